@@ -1,0 +1,189 @@
+/*
+ * vrc.h - C ABI of libvrc, a GB300 (sm_103a) implementation of the
+ * volumetric-ray-casting (VRC) fluence estimator of Sweezy,
+ * "A Monte Carlo Volumetric-Ray-Casting Estimator for Global Fluence
+ * Tallies on GPUs" (arXiv:1706.07476).
+ *
+ * A batch of ray events (position, direction, energy, weight) handed over by
+ * a CPU random walk is traced through a 3-D Cartesian mesh of material
+ * cells.  Every crossed cell i receives the expected track length of Eq. 4,
+ *
+ *     s_i = wt * exp(-tau_in) * (1 - exp(-Sigma_t,i(E) l_i)) / Sigma_t,i(E)
+ *
+ * (wt * exp(-tau_in) * l_i in void), where tau_in is the optical depth from
+ * the ray start to the entry of cell i (the integral of Eq. 2) and wt is the
+ * per-ray weight W/N of Eq. 4.  Scores accumulate in a device-resident
+ * tally that is copied back on request (Sec. 3: the tally stays on the GPU
+ * until the end of the run).
+ *
+ * Conventions shared by every call:
+ *  - Return value: VRC_OK (0) or a negative VRC_ERR_* code.  No C++
+ *    exception crosses this boundary.  vrc_last_error() returns a
+ *    thread-local message describing the last failure on the calling thread.
+ *  - Ownership: a vrc_ctx owns all device memory it allocates and every copy
+ *    of caller data it makes.  The caller keeps ownership of its own arrays.
+ *  - Streams: a `cuda_stream` argument is a cudaStream_t passed as void*;
+ *    NULL selects the context's own stream.
+ *  - Units: lengths in cm, energies in eV, cross sections in 1/cm.
+ *  - Floating point: rays are float32; mesh geometry, energy grids and the
+ *    tally are float64.
+ */
+#ifndef VRC_H
+#define VRC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define VRC_OK 0
+#define VRC_ERR_ARG (-1)       /* invalid argument (null pointer, bad size, bad table) */
+#define VRC_ERR_STATE (-2)     /* call out of order, e.g. cast before a used material has data */
+#define VRC_ERR_CUDA (-3)      /* a CUDA runtime call failed */
+#define VRC_ERR_OOM (-4)       /* device or pinned-host allocation failed */
+#define VRC_ERR_TRAVERSAL (-5) /* a ray needed more grid steps than nx+ny+nz+3 */
+#define VRC_ERR_NONFINITE (-6) /* a ray had a non-finite field, energy <= 0 or a zero direction */
+
+/* ---- precision forms -------------------------------------------------- */
+/* PLAIN: the paper's arithmetic (Sec. 3): single-precision cross sections
+ * and distances, Eq. 4 evaluated in double precision, float64 tally.
+ * Distances are computed with double-float (two float32) arithmetic.
+ * FP32: Eq. 4's exponentials and the optical depth in float32 (optical depth
+ * kept as a compensated float32 pair); the tally sums stay float64. */
+#define VRC_FORM_PLAIN 0
+#define VRC_FORM_FP32 1
+
+/* ---- flags for vrc_read_tally ---------------------------------------- */
+#define VRC_PER_VOLUME 1 /* divide each cell's tally by the cell volume dx*dy*dz */
+
+typedef struct vrc_ctx vrc_ctx;
+
+/* Tuning and behaviour options.  vrc_default_options() fills the defaults;
+ * any field left at its "auto" value is chosen by the library. */
+typedef struct {
+  int32_t form;           /* VRC_FORM_PLAIN (default) or VRC_FORM_FP32 */
+  int32_t sort;           /* ray sorting before the cast: 0 off, 1 on, -1 auto (default) */
+  int32_t sort_cell_bits; /* start-cell block of the sort key is 2^bits cells per axis; -1 auto */
+  int32_t block;          /* threads per block of the cast kernel; 0 auto */
+  int32_t blocks_per_sm;  /* resident blocks per SM for the cast grid; 0 auto */
+  int32_t device;         /* CUDA device ordinal for this context; -1 = current device */
+} vrc_options;
+
+/* A uniform 3-D Cartesian mesh (Sec. 3: 3-D Cartesian mesh geometry).
+ * Cell (ix, iy, iz) spans [x0 + ix*dx, x0 + (ix+1)*dx) x ... ; outside the
+ * box is vacuum (Sec. 5.1).  `material` is a HOST array of nx*ny*nz ids in
+ * [0, n_materials), x fastest ([iz][iy][ix]); it is copied.  n_materials is
+ * at most 64.  Energy groups: n_groups >= 1; group_edges is a HOST array of
+ * n_groups+1 strictly ascending energies (eV), group g = [e_g, e_g+1), last
+ * group closed, rays outside every group score nothing; group_edges == NULL
+ * requires n_groups == 1 and takes every energy.  Tally layout:
+ * [group][iz][iy][ix] float64. */
+typedef struct {
+  int32_t nx, ny, nz;
+  double x0, y0, z0;
+  double dx, dy, dz;
+  const uint8_t *material;
+  int32_t n_materials;
+  int32_t n_groups;
+  const double *group_edges;
+} vrc_mesh_desc;
+
+/* A batch of n rays as eight float32 arrays (structure of arrays).  Each is
+ * a device pointer when on_device != 0, else a host pointer.  (u, v, w) need
+ * not be normalised (only the direction is used); wt already carries the
+ * 1/N of Eq. 4. */
+typedef struct {
+  const float *x, *y, *z;
+  const float *u, *v, *w;
+  const float *E;
+  const float *wt;
+  int64_t n;
+  int32_t on_device;
+} vrc_rays;
+
+/* Counters accumulated on the device since the last reset. */
+typedef struct {
+  int64_t segments;   /* ray-cell segments with positive length that were scored */
+  int64_t rays;       /* rays processed (including those that scored nothing) */
+  int64_t rejected;   /* rays rejected as VRC_ERR_NONFINITE */
+  int64_t overflow;   /* rays stopped by the step bound (VRC_ERR_TRAVERSAL) */
+} vrc_stats;
+
+/* Fills *opt with the defaults.  Never fails. */
+void vrc_default_options(vrc_options *opt);
+
+/* Creates a context for one mesh (Sec. 3: MonteRay holds the mesh geometry
+ * and the cross sections).  Copies the mesh to the device and allocates a
+ * zeroed tally of n_groups*nx*ny*nz float64.  opt may be NULL (defaults).
+ * On failure *out is NULL and nothing is leaked.
+ * Errors: VRC_ERR_ARG (null pointer, non-positive or non-finite size or
+ * spacing, material id >= n_materials, n_materials outside 1..64, bad group
+ * edges), VRC_ERR_OOM, VRC_ERR_CUDA. */
+int vrc_create_mesh(const vrc_mesh_desc *d, const vrc_options *opt, vrc_ctx **out);
+
+/* Loads the total macroscopic cross-section table of one material (Sec. 3:
+ * continuous-energy total cross sections, linearly interpolated between
+ * table points; clamped to the end values outside the table).  E_eV and
+ * sigma_t are HOST arrays of n float64 values, copied.  n == 0 makes the
+ * material void (sigma_t = 0).  Loading a material again replaces its table.
+ * Errors: VRC_ERR_ARG (material out of range, n < 0, null arrays with n > 0,
+ * energies not strictly ascending, non-finite or non-positive energies,
+ * negative or non-finite sigma). */
+int vrc_load_xs(vrc_ctx *c, int32_t material, const double *E_eV, const double *sigma_t,
+                int64_t n);
+
+/* Casts a batch of rays and adds their Eq. 4 scores to the tally (Sec. 3:
+ * per ray, cross-section lookup, ray cast, VRC score).  Asynchronous on the
+ * stream: device arrays must stay valid until the stream passes this point.
+ * Host arrays (on_device == 0) are copied to the device before the call
+ * returns.  Rays with a non-finite field, E <= 0 or a zero direction score
+ * nothing and are reported by the next vrc_sync / vrc_read_tally as
+ * VRC_ERR_NONFINITE.  n == 0 is a no-op.
+ * Errors: VRC_ERR_ARG, VRC_ERR_STATE (a material used by the mesh has no
+ * table), VRC_ERR_OOM, VRC_ERR_CUDA. */
+int vrc_cast_rays(vrc_ctx *c, const vrc_rays *r, void *cuda_stream);
+
+/* Waits for the stream and reports the device status accumulated since the
+ * last reset: VRC_ERR_NONFINITE or VRC_ERR_TRAVERSAL if any ray hit that
+ * case (the tally still holds every other ray's scores), else VRC_OK.
+ * stats may be NULL. */
+int vrc_sync(vrc_ctx *c, void *cuda_stream, vrc_stats *stats);
+
+/* Copies the tally (n must equal n_groups*nx*ny*nz) to the HOST array
+ * out_host, layout [group][iz][iy][ix], optionally divided by the cell
+ * volume (VRC_PER_VOLUME).  Synchronous: waits for all work queued on the
+ * context's stream and on cuda_stream.  Returns the device status like
+ * vrc_sync (the copy is made in every case unless the error is ARG/CUDA). */
+int vrc_read_tally(vrc_ctx *c, double *out_host, int64_t n, int32_t flags, void *cuda_stream);
+
+/* Device pointer of the float64 tally (n_groups*nx*ny*nz entries) for
+ * callers that reduce or post-process it on the device; valid until
+ * vrc_destroy.  NULL if c is NULL. */
+double *vrc_tally_device_ptr(vrc_ctx *c);
+
+/* Zeroes the tally, the counters and the device status (stream-ordered on
+ * cuda_stream). */
+int vrc_reset_tally(vrc_ctx *c, void *cuda_stream);
+
+/* Replaces the context's options (form, sort, launch shape). */
+int vrc_set_options(vrc_ctx *c, const vrc_options *opt);
+
+/* Frees every resource of the context; NULL is a no-op. */
+void vrc_destroy(vrc_ctx *c);
+
+/* Thread-local description of the last error ("" if none). */
+const char *vrc_last_error(void);
+
+/* Number of CUDA devices visible (0 when none or on failure). */
+int vrc_device_count(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int vrc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VRC_H */

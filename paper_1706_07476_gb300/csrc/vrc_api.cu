@@ -1,0 +1,523 @@
+// Host implementation of the libvrc C ABI (include/vrc.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vrc.h"
+#include "vrc_internal.h"
+
+using namespace vrc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(VRC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(VRC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define VRC_CUDA(call, what)                            \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
+  } while (0)
+
+// Sets a device for the scope of an API call and restores the previous one.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Grow-only device buffer.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t want) {
+    if (want <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e == cudaSuccess) bytes = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+df split(double x) {
+  float hi = (float)x;
+  float lo = (float)(x - (double)hi);
+  return {hi, lo};
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+struct vrc_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  vrc_options opt;
+  int32_t n[3] = {0, 0, 0};
+  double org[3] = {0, 0, 0}, h[3] = {0, 0, 0};
+  int64_t ncells = 0;
+  int32_t n_materials = 0, n_groups = 1;
+  std::vector<double> edges;
+  std::vector<uint8_t> used;
+  std::vector<std::vector<double>> tabE, tabS;
+  std::vector<uint8_t> loaded;
+  bool xs_dirty = true;
+
+  uint8_t *d_mat = nullptr;
+  double *d_edges = nullptr;
+  double *d_tally = nullptr;
+  unsigned long long *d_counters = nullptr;
+  unsigned int *d_status = nullptr;
+
+  int32_t n_union = 0, m_pad = 0, n_hash = 0;
+  float l2min = 0.f, inv_bw = 0.f;
+  DevBuf xsE, xsInvdE, xsS, xsHash;
+  DevBuf stage;    // device copy of host rays
+  DevBuf scratch;  // finalize staging
+
+  ~vrc_ctx() {
+    DeviceGuard g(device);
+    if (stream) cudaStreamSynchronize(stream);
+    cudaFree(d_mat);
+    cudaFree(d_edges);
+    cudaFree(d_tally);
+    cudaFree(d_counters);
+    cudaFree(d_status);
+    xsE.release();
+    xsInvdE.release();
+    xsS.release();
+    xsHash.release();
+    stage.release();
+    scratch.release();
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+int check_options(const vrc_options *o) {
+  if (o->form != VRC_FORM_PLAIN && o->form != VRC_FORM_FP32)
+    return fail(VRC_ERR_ARG, "options.form must be VRC_FORM_PLAIN or VRC_FORM_FP32");
+  if (o->block < 0 || o->block > 256 || (o->block % 32) != 0)
+    return fail(VRC_ERR_ARG, "options.block must be 0 or a multiple of 32 up to 256");
+  if (o->blocks_per_sm < 0) return fail(VRC_ERR_ARG, "options.blocks_per_sm must be >= 0");
+  if (o->sort < -1 || o->sort > 1) return fail(VRC_ERR_ARG, "options.sort must be -1, 0 or 1");
+  return VRC_OK;
+}
+
+// Builds the union energy grid, the per-material sigma rows on it, the
+// interval reciprocals and the log2 hash, and uploads them.
+int build_xs(vrc_ctx *c) {
+  for (int m = 0; m < c->n_materials; ++m)
+    if (c->used[m] && !c->loaded[m])
+      return fail(VRC_ERR_STATE, "material %d is used by the mesh but has no cross sections", m);
+  std::vector<double> U;
+  for (int m = 0; m < c->n_materials; ++m)
+    if (c->loaded[m]) U.insert(U.end(), c->tabE[m].begin(), c->tabE[m].end());
+  std::sort(U.begin(), U.end());
+  U.erase(std::unique(U.begin(), U.end()), U.end());
+  const int64_t nu = (int64_t)U.size();
+  if (nu > (int64_t)1 << 30) return fail(VRC_ERR_ARG, "union energy grid too large");
+  c->n_union = (int32_t)nu;
+  c->m_pad = (c->n_materials + 3) & ~3;
+  c->xs_dirty = false;
+  if (nu == 0) return VRC_OK;
+
+  std::vector<float> S((size_t)nu * c->m_pad, 0.f);
+  for (int m = 0; m < c->n_materials; ++m) {
+    const std::vector<double> &E = c->tabE[m], &Sg = c->tabS[m];
+    const size_t n = E.size();
+    if (!c->loaded[m] || n == 0) continue;
+    size_t k = 0;
+    for (int64_t i = 0; i < nu; ++i) {
+      const double e = U[i];
+      double s;
+      if (n == 1 || e <= E[0]) s = Sg[0];
+      else if (e >= E[n - 1]) s = Sg[n - 1];
+      else {
+        while (k + 1 < n && E[k + 1] <= e) ++k;  // E[k] <= e < E[k+1]
+        s = Sg[k] + (e - E[k]) * (Sg[k + 1] - Sg[k]) / (E[k + 1] - E[k]);
+      }
+      S[(size_t)i * c->m_pad + m] = (float)s;
+    }
+  }
+  std::vector<double> inv((size_t)std::max<int64_t>(nu - 1, 1), 0.0);
+  for (int64_t i = 0; i + 1 < nu; ++i) inv[i] = 1.0 / (U[i + 1] - U[i]);
+
+  int nh = 64;
+  while (nh < 4096 && nh * 4 < nu) nh <<= 1;
+  c->n_hash = nh;
+  const double l2a = std::log2(U[0]), l2b = std::log2(U[nu - 1]);
+  c->l2min = (float)l2a;
+  c->inv_bw = l2b > l2a ? (float)(nh / (l2b - l2a)) : 0.f;
+  std::vector<int32_t> hash((size_t)nh + 1);
+  {
+    int64_t i = 0;
+    for (int b = 0; b <= nh; ++b) {
+      double eb = (c->inv_bw > 0.f) ? std::exp2(l2a + b / (double)c->inv_bw) : U[0];
+      while (i + 1 < nu && U[i + 1] <= eb) ++i;
+      hash[b] = (int32_t)std::min<int64_t>(i, std::max<int64_t>(nu - 2, 0));
+    }
+  }
+  VRC_CUDA(c->xsE.ensure(sizeof(double) * nu), "allocating the energy grid");
+  VRC_CUDA(c->xsInvdE.ensure(sizeof(double) * inv.size()), "allocating the energy grid");
+  VRC_CUDA(c->xsS.ensure(sizeof(float) * S.size()), "allocating the cross-section table");
+  VRC_CUDA(c->xsHash.ensure(sizeof(int32_t) * hash.size()), "allocating the energy hash");
+  VRC_CUDA(cudaStreamSynchronize(c->stream), "synchronizing before a table upload");
+  VRC_CUDA(cudaMemcpy(c->xsE.p, U.data(), sizeof(double) * nu, cudaMemcpyHostToDevice), "uploading the energy grid");
+  VRC_CUDA(cudaMemcpy(c->xsInvdE.p, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice), "uploading the energy grid");
+  VRC_CUDA(cudaMemcpy(c->xsS.p, S.data(), sizeof(float) * S.size(), cudaMemcpyHostToDevice), "uploading the cross sections");
+  VRC_CUDA(cudaMemcpy(c->xsHash.p, hash.data(), sizeof(int32_t) * hash.size(), cudaMemcpyHostToDevice), "uploading the energy hash");
+  return VRC_OK;
+}
+
+CastArgs make_args(const vrc_ctx *c, const RayPtrs &rays) {
+  CastArgs a;
+  std::memset(&a, 0, sizeof a);
+  for (int k = 0; k < 3; ++k) {
+    a.mesh.n[k] = c->n[k];
+    a.mesh.org[k] = split(c->org[k]);
+    a.mesh.h[k] = split(c->h[k]);
+    a.mesh.inv_h[k] = split(1.0 / c->h[k]);
+  }
+  a.mesh.stride[0] = 1;
+  a.mesh.stride[1] = c->n[0];
+  a.mesh.stride[2] = (int64_t)c->n[0] * c->n[1];
+  a.mesh.ncells = c->ncells;
+  a.mesh.mat = c->d_mat;
+  a.xs.n_union = c->n_union;
+  a.xs.m_pad = c->m_pad;
+  a.xs.n_mat = c->n_materials;
+  a.xs.n_hash = c->n_hash;
+  a.xs.l2min = c->l2min;
+  a.xs.inv_bw = c->inv_bw;
+  a.xs.E = static_cast<const double *>(c->xsE.p);
+  a.xs.inv_dE = static_cast<const double *>(c->xsInvdE.p);
+  a.xs.S = static_cast<const float *>(c->xsS.p);
+  a.xs.hash = static_cast<const int32_t *>(c->xsHash.p);
+  a.edges = c->edges.empty() ? nullptr : c->d_edges;
+  a.n_groups = c->n_groups;
+  a.rays = rays;
+  a.tally = c->d_tally;
+  a.counters = c->d_counters;
+  a.status = c->d_status;
+  return a;
+}
+
+int status_code(unsigned st) {
+  if (st & kStatusTraversal)
+    return fail(VRC_ERR_TRAVERSAL, "a ray needed more grid steps than the mesh allows");
+  if (st & kStatusNonfinite)
+    return fail(VRC_ERR_NONFINITE,
+                "a ray had a non-finite field, a non-positive energy or a zero direction");
+  return VRC_OK;
+}
+
+int sync_streams(vrc_ctx *c, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (s && s != c->stream) VRC_CUDA(cudaStreamSynchronize(s), "synchronizing the caller's stream");
+  VRC_CUDA(cudaStreamSynchronize(c->stream), "synchronizing the context stream");
+  return VRC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void vrc_default_options(vrc_options *opt) {
+  if (!opt) return;
+  opt->form = VRC_FORM_PLAIN;
+  opt->sort = -1;
+  opt->sort_cell_bits = -1;
+  opt->block = 0;
+  opt->blocks_per_sm = 0;
+  opt->device = -1;
+}
+
+int vrc_create_mesh(const vrc_mesh_desc *d, const vrc_options *opt, vrc_ctx **out) {
+  if (!out) return fail(VRC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(VRC_ERR_ARG, "mesh descriptor is NULL");
+  if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0)
+    return fail(VRC_ERR_ARG, "mesh dimensions must be positive (got %d x %d x %d)", d->nx, d->ny, d->nz);
+  if ((int64_t)d->nx + d->ny + d->nz > (1 << 24))
+    return fail(VRC_ERR_ARG, "mesh too large: nx+ny+nz must stay below 2^24");
+  if (!finite_pos(d->dx) || !finite_pos(d->dy) || !finite_pos(d->dz))
+    return fail(VRC_ERR_ARG, "cell spacings must be finite and positive");
+  if (!std::isfinite(d->x0) || !std::isfinite(d->y0) || !std::isfinite(d->z0))
+    return fail(VRC_ERR_ARG, "mesh origin must be finite");
+  if (!d->material) return fail(VRC_ERR_ARG, "material array is NULL");
+  if (d->n_materials < 1 || d->n_materials > kMaxMaterials)
+    return fail(VRC_ERR_ARG, "n_materials must be in 1..%d", kMaxMaterials);
+  if (d->n_groups < 1 || d->n_groups > kMaxGroups)
+    return fail(VRC_ERR_ARG, "n_groups must be in 1..%d", kMaxGroups);
+  if (!d->group_edges && d->n_groups != 1)
+    return fail(VRC_ERR_ARG, "group_edges is NULL but n_groups is %d", d->n_groups);
+  if (d->group_edges) {
+    for (int g = 0; g <= d->n_groups; ++g) {
+      if (!std::isfinite(d->group_edges[g]))
+        return fail(VRC_ERR_ARG, "group edge %d is not finite", g);
+      if (g > 0 && !(d->group_edges[g] > d->group_edges[g - 1]))
+        return fail(VRC_ERR_ARG, "group edges must be strictly ascending");
+    }
+  }
+  vrc_options o;
+  vrc_default_options(&o);
+  if (opt) o = *opt;
+  int rc = check_options(&o);
+  if (rc) return rc;
+
+  const int64_t ncells = (int64_t)d->nx * d->ny * d->nz;
+  std::vector<uint8_t> used(d->n_materials, 0);
+  for (int64_t i = 0; i < ncells; ++i) {
+    uint8_t m = d->material[i];
+    if (m >= d->n_materials)
+      return fail(VRC_ERR_ARG, "cell %lld has material %d >= n_materials %d", (long long)i, m, d->n_materials);
+    used[m] = 1;
+  }
+
+  int dev = o.device;
+  if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess)
+    return fail(VRC_ERR_CUDA, "no CUDA device available");
+  DeviceGuard g(dev);
+  if (!g.ok) return fail(VRC_ERR_CUDA, "cannot select CUDA device %d", dev);
+
+  vrc_ctx *c = new (std::nothrow) vrc_ctx();
+  if (!c) return fail(VRC_ERR_OOM, "out of host memory");
+  c->device = dev;
+  c->opt = o;
+  c->n[0] = d->nx; c->n[1] = d->ny; c->n[2] = d->nz;
+  c->org[0] = d->x0; c->org[1] = d->y0; c->org[2] = d->z0;
+  c->h[0] = d->dx; c->h[1] = d->dy; c->h[2] = d->dz;
+  c->ncells = ncells;
+  c->n_materials = d->n_materials;
+  c->n_groups = d->n_groups;
+  if (d->group_edges) c->edges.assign(d->group_edges, d->group_edges + d->n_groups + 1);
+  c->used = used;
+  c->tabE.resize(d->n_materials);
+  c->tabS.resize(d->n_materials);
+  c->loaded.assign(d->n_materials, 0);
+
+  auto bail = [&](int code) { delete c; return code; };
+  cudaError_t e;
+  if ((e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return bail(cuda_fail(e, "querying the SM count"));
+  if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(cuda_fail(e, "creating the context stream"));
+  const size_t tally_bytes = sizeof(double) * (size_t)ncells * d->n_groups;
+  if ((e = cudaMalloc((void **)&c->d_mat, (size_t)ncells)) != cudaSuccess ||
+      (e = cudaMalloc((void **)&c->d_tally, tally_bytes)) != cudaSuccess ||
+      (e = cudaMalloc((void **)&c->d_counters, sizeof(unsigned long long) * kNumCounters)) != cudaSuccess ||
+      (e = cudaMalloc((void **)&c->d_status, sizeof(unsigned))) != cudaSuccess)
+    return bail(cuda_fail(e, "allocating the mesh and tally"));
+  if (d->group_edges &&
+      (e = cudaMalloc((void **)&c->d_edges, sizeof(double) * (d->n_groups + 1))) != cudaSuccess)
+    return bail(cuda_fail(e, "allocating the group edges"));
+  if ((e = cudaMemcpy(c->d_mat, d->material, (size_t)ncells, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(cuda_fail(e, "uploading the mesh"));
+  if (d->group_edges &&
+      (e = cudaMemcpy(c->d_edges, d->group_edges, sizeof(double) * (d->n_groups + 1),
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(cuda_fail(e, "uploading the group edges"));
+  if ((e = cudaMemsetAsync(c->d_tally, 0, tally_bytes, c->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * kNumCounters, c->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return bail(cuda_fail(e, "zeroing the tally"));
+  *out = c;
+  return VRC_OK;
+}
+
+int vrc_load_xs(vrc_ctx *c, int32_t material, const double *E_eV, const double *sigma_t, int64_t n) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  if (material < 0 || material >= c->n_materials)
+    return fail(VRC_ERR_ARG, "material %d out of range 0..%d", material, c->n_materials - 1);
+  if (n < 0) return fail(VRC_ERR_ARG, "table length is negative");
+  if (n > 0 && (!E_eV || !sigma_t)) return fail(VRC_ERR_ARG, "table arrays are NULL");
+  if (n > ((int64_t)1 << 28)) return fail(VRC_ERR_ARG, "table too long");
+  for (int64_t i = 0; i < n; ++i) {
+    if (!finite_pos(E_eV[i])) return fail(VRC_ERR_ARG, "energy %lld is not finite and positive", (long long)i);
+    if (i > 0 && !(E_eV[i] > E_eV[i - 1]))
+      return fail(VRC_ERR_ARG, "energies must be strictly ascending (index %lld)", (long long)i);
+    if (!std::isfinite(sigma_t[i]) || sigma_t[i] < 0.0)
+      return fail(VRC_ERR_ARG, "sigma_t %lld is negative or not finite", (long long)i);
+  }
+  c->tabE[material].assign(E_eV, E_eV + n);
+  c->tabS[material].assign(sigma_t, sigma_t + n);
+  c->loaded[material] = 1;
+  c->xs_dirty = true;
+  return VRC_OK;
+}
+
+int vrc_cast_rays(vrc_ctx *c, const vrc_rays *r, void *cuda_stream) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  if (!r) return fail(VRC_ERR_ARG, "rays is NULL");
+  if (r->n < 0) return fail(VRC_ERR_ARG, "ray count is negative");
+  if (r->n == 0) return VRC_OK;
+  if (!r->x || !r->y || !r->z || !r->u || !r->v || !r->w || !r->E || !r->wt)
+    return fail(VRC_ERR_ARG, "a ray array is NULL");
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(VRC_ERR_CUDA, "cannot select CUDA device %d", c->device);
+  if (c->xs_dirty) {
+    int rc = build_xs(c);
+    if (rc) {
+      c->xs_dirty = true;
+      return rc;
+    }
+  }
+  cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+  RayPtrs rp;
+  rp.n = r->n;
+  if (r->on_device) {
+    rp.x = r->x; rp.y = r->y; rp.z = r->z; rp.u = r->u;
+    rp.v = r->v; rp.w = r->w; rp.E = r->E; rp.wt = r->wt;
+  } else {
+    const size_t bytes = sizeof(float) * (size_t)r->n;
+    VRC_CUDA(c->stage.ensure(8 * bytes), "allocating ray staging");
+    float *base = static_cast<float *>(c->stage.p);
+    const float *src[8] = {r->x, r->y, r->z, r->u, r->v, r->w, r->E, r->wt};
+    const float **dst[8] = {&rp.x, &rp.y, &rp.z, &rp.u, &rp.v, &rp.w, &rp.E, &rp.wt};
+    for (int k = 0; k < 8; ++k) {
+      float *dk = base + (size_t)k * r->n;
+      VRC_CUDA(cudaMemcpyAsync(dk, src[k], bytes, cudaMemcpyHostToDevice, s), "copying rays to the device");
+      *dst[k] = dk;
+    }
+  }
+  CastArgs a = make_args(c, rp);
+  const int form = c->opt.form;
+  const int block = c->opt.block > 0 ? c->opt.block : 256;
+  int bps = c->opt.blocks_per_sm;
+  if (bps <= 0) {
+    VRC_CUDA(cast_occupancy(form, a, block, &bps), "querying occupancy");
+    if (bps <= 0) return fail(VRC_ERR_ARG, "cast kernel does not fit on an SM with %d materials", c->n_materials);
+  }
+  const int64_t need = (r->n + block - 1) / block;
+  const int grid = (int)std::min<int64_t>(need, (int64_t)c->num_sms * bps);
+  VRC_CUDA(launch_cast(form, a, grid, block, s), "launching the cast kernel");
+  if (!r->on_device) {
+    // the host arrays may be reused once the copies have completed
+    VRC_CUDA(cudaStreamSynchronize(s), "waiting for the ray upload");
+  }
+  return VRC_OK;
+}
+
+int vrc_sync(vrc_ctx *c, void *cuda_stream, vrc_stats *stats) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  DeviceGuard g(c->device);
+  int rc = sync_streams(c, cuda_stream);
+  if (rc) return rc;
+  unsigned long long cnt[kNumCounters];
+  unsigned st = 0;
+  VRC_CUDA(cudaMemcpy(cnt, c->d_counters, sizeof cnt, cudaMemcpyDeviceToHost), "reading counters");
+  VRC_CUDA(cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost), "reading status");
+  if (stats) {
+    stats->segments = (int64_t)cnt[kCntSegments];
+    stats->rays = (int64_t)cnt[kCntRays];
+    stats->rejected = (int64_t)cnt[kCntRejected];
+    stats->overflow = (int64_t)cnt[kCntOverflow];
+  }
+  return status_code(st);
+}
+
+int vrc_read_tally(vrc_ctx *c, double *out_host, int64_t n, int32_t flags, void *cuda_stream) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  if (!out_host) return fail(VRC_ERR_ARG, "output array is NULL");
+  const int64_t total = c->ncells * c->n_groups;
+  if (n != total) return fail(VRC_ERR_ARG, "tally has %lld entries, caller gave %lld", (long long)total, (long long)n);
+  if (flags & ~VRC_PER_VOLUME) return fail(VRC_ERR_ARG, "unknown flags 0x%x", flags);
+  DeviceGuard g(c->device);
+  int rc = sync_streams(c, cuda_stream);
+  if (rc) return rc;
+  if (flags & VRC_PER_VOLUME) {
+    const double scale = 1.0 / (c->h[0] * c->h[1] * c->h[2]);
+    const int64_t chunk = std::min<int64_t>(total, (int64_t)8 << 20);
+    VRC_CUDA(c->scratch.ensure(sizeof(double) * chunk), "allocating tally staging");
+    for (int64_t off = 0; off < total; off += chunk) {
+      const int64_t m = std::min(chunk, total - off);
+      VRC_CUDA(launch_scale_copy(c->d_tally + off, static_cast<double *>(c->scratch.p), m, scale, c->stream),
+               "launching the tally finalize kernel");
+      VRC_CUDA(cudaMemcpyAsync(out_host + off, c->scratch.p, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream),
+               "copying the tally");
+      VRC_CUDA(cudaStreamSynchronize(c->stream), "copying the tally");
+    }
+  } else {
+    VRC_CUDA(cudaMemcpyAsync(out_host, c->d_tally, sizeof(double) * total, cudaMemcpyDeviceToHost, c->stream),
+             "copying the tally");
+    VRC_CUDA(cudaStreamSynchronize(c->stream), "copying the tally");
+  }
+  unsigned st = 0;
+  VRC_CUDA(cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost), "reading status");
+  return status_code(st);
+}
+
+double *vrc_tally_device_ptr(vrc_ctx *c) { return c ? c->d_tally : nullptr; }
+
+int vrc_reset_tally(vrc_ctx *c, void *cuda_stream) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  DeviceGuard g(c->device);
+  cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+  VRC_CUDA(cudaMemsetAsync(c->d_tally, 0, sizeof(double) * c->ncells * c->n_groups, s), "zeroing the tally");
+  VRC_CUDA(cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * kNumCounters, s), "zeroing counters");
+  VRC_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), s), "zeroing status");
+  return VRC_OK;
+}
+
+int vrc_set_options(vrc_ctx *c, const vrc_options *opt) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  if (!opt) return fail(VRC_ERR_ARG, "options are NULL");
+  int rc = check_options(opt);
+  if (rc) return rc;
+  int dev = c->device;
+  c->opt = *opt;
+  c->opt.device = dev;
+  return VRC_OK;
+}
+
+void vrc_destroy(vrc_ctx *c) { delete c; }
+
+const char *vrc_last_error(void) { return g_last_error.c_str(); }
+
+int vrc_device_count(void) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) return 0;
+  return n;
+}
+
+int vrc_version(void) { return 100; }
+
+}  // extern "C"

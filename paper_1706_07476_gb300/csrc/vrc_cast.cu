@@ -1,0 +1,145 @@
+// The VRC cast kernel (Sec. 3: one GPU thread per ray runs the cross-section
+// lookup, the ray cast and the VRC score of Eq. 4) and the tally finalize
+// kernel.
+#include <algorithm>
+
+#include "vrc_device.cuh"
+
+namespace vrc {
+
+namespace {
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct SmemLayout {
+  size_t hash, edges, sig, inv, total;
+};
+
+SmemLayout smem_layout(int form, const CastArgs &a, int block) {
+  SmemLayout L;
+  size_t off = 0;
+  L.hash = off;
+  off += sizeof(int32_t) * (a.xs.n_union > 0 ? (size_t)a.xs.n_hash + 1 : 1);
+  off = align_up(off, 16);
+  L.edges = off;
+  off += sizeof(double) * (a.edges ? (size_t)a.n_groups + 1 : 1);
+  off = align_up(off, 16);
+  L.sig = off;
+  off += sizeof(float) * (size_t)a.xs.n_mat * block;
+  off = align_up(off, 16);
+  L.inv = off;
+  off += (form == kFormPlain ? sizeof(double) : sizeof(float)) * (size_t)a.xs.n_mat * block;
+  L.total = align_up(off, 16);
+  return L;
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(256) k_cast(CastArgs a, SmemLayout L) {
+  typedef typename Attenuation<FORM>::inv_t inv_t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  int32_t *hash_s = reinterpret_cast<int32_t *>(smem + L.hash);
+  double *edges_s = reinterpret_cast<double *>(smem + L.edges);
+  float *sig_s = reinterpret_cast<float *>(smem + L.sig) + threadIdx.x;
+  inv_t *inv_s = reinterpret_cast<inv_t *>(smem + L.inv) + threadIdx.x;
+
+  if (a.xs.n_union > 0)
+    for (int t = threadIdx.x; t <= a.xs.n_hash; t += blockDim.x) hash_s[t] = a.xs.hash[t];
+  if (a.edges)
+    for (int t = threadIdx.x; t <= a.n_groups; t += blockDim.x) edges_s[t] = a.edges[t];
+  __syncthreads();
+  const double *edges = a.edges ? edges_s : nullptr;
+  const int stride = blockDim.x;
+
+  uint32_t nseg = 0, nrays = 0, nrej = 0, novf = 0;
+  const RayPtrs &R = a.rays;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R.n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const float x = __ldg(R.x + r), y = __ldg(R.y + r), z = __ldg(R.z + r);
+    const float u = __ldg(R.u + r), v = __ldg(R.v + r), w = __ldg(R.w + r);
+    const float E = __ldg(R.E + r), wt = __ldg(R.wt + r);
+    ++nrays;
+    const float dn = sqrtf(u * u + v * v + w * w);
+    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(u) && isfinite(v) &&
+          isfinite(w) && isfinite(E) && isfinite(wt) && E > 0.f && dn > 0.f && isfinite(dn))) {
+      ++nrej;
+      continue;
+    }
+    const int g = group_of(edges, a.n_groups, (double)E);
+    if (g < 0) continue;
+    xs_lookup<inv_t>(a.xs, hash_s, E, sig_s, inv_s, stride);
+    bool ovf = false;
+    nseg += cast_ray<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, a.tally + (int64_t)g * a.mesh.ncells,
+                           sig_s, inv_s, stride, &ovf);
+    novf += ovf;
+  }
+  // one atomic per warp for each counter
+  for (int o = 16; o > 0; o >>= 1) {
+    nseg += __shfl_down_sync(0xffffffffu, nseg, o);
+    nrays += __shfl_down_sync(0xffffffffu, nrays, o);
+    nrej += __shfl_down_sync(0xffffffffu, nrej, o);
+    novf += __shfl_down_sync(0xffffffffu, novf, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (nseg) atomicAdd(a.counters + kCntSegments, (unsigned long long)nseg);
+    if (nrays) atomicAdd(a.counters + kCntRays, (unsigned long long)nrays);
+    if (nrej) {
+      atomicAdd(a.counters + kCntRejected, (unsigned long long)nrej);
+      atomicOr(a.status, kStatusNonfinite);
+    }
+    if (novf) {
+      atomicAdd(a.counters + kCntOverflow, (unsigned long long)novf);
+      atomicOr(a.status, kStatusTraversal);
+    }
+  }
+}
+
+__global__ void k_scale_copy(const double *__restrict__ src, double *__restrict__ dst, int64_t n,
+                             double scale) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i] * scale;
+}
+
+}  // namespace
+
+size_t cast_smem_bytes(int form, const CastArgs &a, int block) {
+  return smem_layout(form, a, block).total;
+}
+
+cudaError_t cast_occupancy(int form, const CastArgs &a, int block, int *blocks_per_sm) {
+  size_t smem = cast_smem_bytes(form, a, block);
+  if (form == kFormPlain) {
+    cudaFuncSetAttribute(k_cast<kFormPlain>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_cast<kFormPlain>, block, smem);
+  }
+  cudaFuncSetAttribute(k_cast<kFormFp32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_cast<kFormFp32>, block, smem);
+}
+
+cudaError_t launch_cast(int form, const CastArgs &a, int grid, int block, cudaStream_t s) {
+  SmemLayout L = smem_layout(form, a, block);
+  if (form == kFormPlain) {
+    cudaError_t e = cudaFuncSetAttribute(k_cast<kFormPlain>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (e != cudaSuccess) return e;
+    k_cast<kFormPlain><<<grid, block, L.total, s>>>(a, L);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_cast<kFormFp32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (e != cudaSuccess) return e;
+    k_cast<kFormFp32><<<grid, block, L.total, s>>>(a, L);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(const double *src, double *dst, int64_t n, double scale,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int block = 256;
+  int64_t want = (n + block - 1) / block;
+  int grid = (int)std::min<int64_t>(want, 152 * 8);
+  k_scale_copy<<<grid, block, 0, s>>>(src, dst, n, scale);
+  return cudaGetLastError();
+}
+
+}  // namespace vrc

@@ -1,0 +1,309 @@
+// Device building blocks of the VRC cast: double-float arithmetic, the
+// hashed union-grid cross-section lookup, and the per-ray grid walk with the
+// Eq. 4 score.  Included by the cast and batched kernels.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include "vrc_internal.h"
+
+namespace vrc {
+
+constexpr int kFormPlain = 0;
+constexpr int kFormFp32 = 1;
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: error-free transformations of Knuth (TwoSum) and
+// Dekker (Fast2Sum), with the product error taken exactly by one fused
+// multiply-add.  The _rn intrinsics keep the compiler from fusing or
+// reassociating these steps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {  // needs |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df df_add_f(df a, float b) {
+  df s = df_two_sum(a.hi, b);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return df_fast_two_sum(p, e);
+}
+
+// 1/d as a double-float: r = rn(1/d); the residual 1 - d r is exact in one
+// fma, and r (1 + residual) carries the quotient to about 2^-46.
+__device__ __forceinline__ df df_rcp(float d) {
+  float r = __frcp_rn(d);
+  float res = __fmaf_rn(-d, r, 1.0f);
+  return df_fast_two_sum(r, __fmul_rn(r, res));
+}
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ bool df_lt(df a, df b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+
+__device__ __forceinline__ bool df_pos(df a) { return a.hi > 0.f || (a.hi == 0.f && a.lo > 0.f); }
+
+// (a - b) rounded to float; exact in the hi parts when a and b are close.
+__device__ __forceinline__ float df_diff(df a, df b) {
+  return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
+}
+
+// floor(a) clamped to [0, n-1].
+__device__ __forceinline__ int df_floor_clamp(df a, int n) {
+  float f = floorf(a.hi);
+  if (f == a.hi && a.lo < 0.f) f -= 1.f;
+  f = fminf(fmaxf(f, 0.f), (float)(n - 1));
+  return (int)f;
+}
+
+// ---------------------------------------------------------------------------
+// Energy group: half-open [e_g, e_g+1), last group closed (edges in smem).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int group_of(const double *edges, int G, double e) {
+  if (edges == nullptr) return 0;
+  if (!(e >= edges[0]) || e > edges[G]) return -1;
+  int lo = 0, hi = G;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (edges[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Cross sections of every material at one energy (Sec. 3: hash-based lookup
+// (Brown) on the union log-energy grid, then linear-linear interpolation).
+// The hash bin of log2(E) gives a short bracket of grid intervals; a bounded
+// fix-up makes the bracket exact whatever the rounding of log2, and a binary
+// search inside it finds E[i] <= e < E[i+1].  The interpolation fraction is
+// formed in double precision once per ray; the per-material interpolation is
+// float32 (the paper's single-precision cross sections).
+// Writes sigma to sg[m*stride] and its reciprocal to inv[m*stride].
+// ---------------------------------------------------------------------------
+template <typename InvT>
+__device__ __forceinline__ void xs_lookup(const XsDev &xs, const int32_t *hash_s, float E,
+                                          float *sg, InvT *inv, int stride) {
+  const int n = xs.n_union;
+  if (n == 0) {
+    for (int m = 0; m < xs.n_mat; ++m) { sg[m * stride] = 0.f; inv[m * stride] = InvT(0); }
+    return;
+  }
+  const double e = (double)E;
+  int i;
+  float f;
+  if (n == 1 || e <= __ldg(xs.E)) {
+    i = 0; f = 0.f;
+  } else if (e >= __ldg(xs.E + n - 1)) {
+    i = n - 1; f = 0.f;
+  } else {
+    int b = (int)((__log2f(E) - xs.l2min) * xs.inv_bw);
+    b = min(max(b, 0), xs.n_hash - 1);
+    int lo = hash_s[b];
+    int hi = min(hash_s[b + 1] + 1, n - 1);
+    while (lo > 0 && __ldg(xs.E + lo) > e) --lo;       // fix-up: E[lo] <= e
+    while (hi < n - 1 && __ldg(xs.E + hi) <= e) ++hi;  // fix-up: e < E[hi]
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (__ldg(xs.E + mid) <= e) lo = mid; else hi = mid;
+    }
+    i = lo;
+    f = (float)((e - __ldg(xs.E + i)) * __ldg(xs.inv_dE + i));
+  }
+  const float *r0 = xs.S + (int64_t)i * xs.m_pad;
+  const float *r1 = (f == 0.f) ? r0 : r0 + xs.m_pad;
+  for (int m = 0; m < xs.n_mat; ++m) {
+    float a = __ldg(r0 + m), b = __ldg(r1 + m);
+    float s = fmaf(f, b - a, a);
+    sg[m * stride] = s;
+    inv[m * stride] = s > 0.f ? InvT(1) / InvT(s) : InvT(0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 4 along one ray, in the two precision forms.
+// ---------------------------------------------------------------------------
+template <int FORM>
+struct Attenuation;
+
+// Plain form: optical depth carried as the transmitted fraction T =
+// exp(-tau_in) in float64; every factor exp(-Sigma l) comes from the same
+// expm1 that gives the path term (exp directly once Sigma l >= 8, where
+// 1 + expm1 would lose digits).
+template <>
+struct Attenuation<kFormPlain> {
+  typedef double inv_t;
+  double T = 1.0;
+  double wt;
+  __device__ __forceinline__ explicit Attenuation(float w) : wt((double)w) {}
+  __device__ __forceinline__ double score(float sig, double inv, float l) {
+    double path, factor;
+    if (sig > 0.f) {
+      double x = (double)sig * (double)l;  // exact: a float product fits a double
+      double em = expm1(-x);
+      path = -em * inv;
+      factor = x < 8.0 ? 1.0 + em : exp(-x);
+    } else {
+      path = (double)l;
+      factor = 1.0;
+    }
+    double s = wt * T * path;
+    T *= factor;
+    return s;
+  }
+};
+
+// FP32 form: optical depth as a compensated float32 pair, exponentials in
+// float32; only the tally accumulation stays float64.
+template <>
+struct Attenuation<kFormFp32> {
+  typedef float inv_t;
+  df tau = {0.f, 0.f};
+  float wt;
+  __device__ __forceinline__ explicit Attenuation(float w) : wt(w) {}
+  __device__ __forceinline__ double score(float sig, float inv, float l) {
+    float T = expf(-tau.hi) * (1.0f - tau.lo);
+    float path;
+    if (sig > 0.f) {
+      float x = sig * l;
+      path = -expm1f(-x) * inv;
+      tau = df_add_f(tau, x);
+    } else {
+      path = l;
+    }
+    return (double)(wt * T * path);
+  }
+};
+
+// Crossing parameter of plane j on one axis: (org + j h - p) / d, evaluated
+// from scratch in double-float (never accumulated) as (D + j h) * inv_d with
+// D = org - p.
+__device__ __forceinline__ df plane_param(df D, df h, int j, df inv_d) {
+  return df_mul(df_add(D, df_mul_f(h, (float)j)), inv_d);
+}
+
+// Walks one ray through the mesh and adds its Eq. 4 score to every crossed
+// cell of `tal` (the ray's group slice).  The ray is the half-line p + s d,
+// s >= 0, with d not necessarily unit: crossing parameters are in units of
+// |d| and lengths are scaled by |d| at the end.  A start outside the box is
+// clipped to it (vacuum outside); the walk ends when the ray leaves the mesh
+// or after max_steps steps (then *overflow is set).  Returns the number of
+// positive-length segments scored.
+template <int FORM>
+__device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float py, float pz,
+                                             float u, float v, float w, float wt, float dn,
+                                             double *__restrict__ tal, const float *sg,
+                                             const typename Attenuation<FORM>::inv_t *inv,
+                                             int stride, bool *overflow) {
+  const float p[3] = {px, py, pz};
+  const float d[3] = {u, v, w};
+  const df inf = {INFINITY, 0.f};
+  df D[3], inv_d[3];
+  df s_in = {0.f, 0.f}, s_out = inf;
+  bool miss = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    D[k] = df_add_f(m.org[k], -p[k]);
+    df Dn = df_add(D[k], df_mul_f(m.h[k], (float)m.n[k]));
+    if (d[k] == 0.f) {
+      inv_d[k] = {0.f, 0.f};
+      if (df_pos(D[k]) || !df_pos(Dn)) miss = true;  // p < lo or p >= hi
+    } else {
+      inv_d[k] = df_rcp(d[k]);
+      df a = df_mul(D[k], inv_d[k]);
+      df b = df_mul(Dn, inv_d[k]);
+      if (d[k] < 0.f) { df t = a; a = b; b = t; }
+      if (df_lt(s_in, a)) s_in = a;
+      if (df_lt(b, s_out)) s_out = b;
+    }
+  }
+  if (miss || !df_lt(s_in, s_out)) return 0;
+
+  int i[3], j[3], stp[3];
+  df S[3];
+  int64_t cell = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    df c = df_neg(D[k]);  // p - org
+    if (s_in.hi > 0.f && d[k] != 0.f) c = df_add(c, df_mul_f(s_in, d[k]));
+    i[k] = df_floor_clamp(df_mul(c, m.inv_h[k]), m.n[k]);
+    cell += (int64_t)i[k] * m.stride[k];
+    if (d[k] == 0.f) {
+      stp[k] = 0; j[k] = 0; S[k] = inf;
+    } else {
+      stp[k] = d[k] > 0.f ? 1 : -1;
+      j[k] = i[k] + (d[k] > 0.f ? 1 : 0);
+      S[k] = plane_param(D[k], m.h[k], j[k], inv_d[k]);
+    }
+  }
+
+  Attenuation<FORM> att(wt);
+  df s_cur = s_in;
+  unsigned mat = __ldg(m.mat + cell);
+  uint32_t nseg = 0;
+  const int max_steps = m.n[0] + m.n[1] + m.n[2] + 3;
+  for (int step = 0;; ++step) {
+    // axis of the nearest crossing (ties resolved x, then y, then z)
+    int k = df_lt(S[1], S[0]) ? 1 : 0;
+    df Sk = k ? S[1] : S[0];
+    if (df_lt(S[2], Sk)) { k = 2; Sk = S[2]; }
+    const int ik = (k == 0 ? i[0] : k == 1 ? i[1] : i[2]);
+    const int sk = (k == 0 ? stp[0] : k == 1 ? stp[1] : stp[2]);
+    const int nk = (k == 0 ? m.n[0] : k == 1 ? m.n[1] : m.n[2]);
+    const int inew = ik + sk;
+    const bool leaving = (unsigned)inew >= (unsigned)nk;
+    const int64_t ncell = cell + (int64_t)sk * (k == 0 ? m.stride[0] : k == 1 ? m.stride[1] : m.stride[2]);
+    const unsigned nmat = leaving ? 0u : __ldg(m.mat + ncell);  // prefetch the next cell
+
+    float l = fmaxf(df_diff(Sk, s_cur), 0.f) * dn;
+    double s = att.score(sg[mat * stride], inv[mat * stride], l);
+    atomicAdd(tal + cell, s);
+    nseg += l > 0.f;
+
+    if (leaving) break;
+    if (step >= max_steps) { *overflow = true; break; }
+    s_cur = Sk;
+    cell = ncell;
+    mat = nmat;
+    // advance the stepped axis and recompute its next crossing from scratch
+    const int jn = (k == 0 ? j[0] : k == 1 ? j[1] : j[2]) + sk;
+    const df Dk = k == 0 ? D[0] : k == 1 ? D[1] : D[2];
+    const df hk = k == 0 ? m.h[0] : k == 1 ? m.h[1] : m.h[2];
+    const df vk = k == 0 ? inv_d[0] : k == 1 ? inv_d[1] : inv_d[2];
+    const df Sn = plane_param(Dk, hk, jn, vk);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a == k) { i[a] = inew; j[a] = jn; S[a] = Sn; }
+    }
+  }
+  return nseg;
+}
+
+}  // namespace vrc

@@ -1,0 +1,74 @@
+// Internal declarations shared by the libvrc translation units (host and
+// device).  Not part of the public ABI; see include/vrc.h for that.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vrc {
+
+constexpr int kMaxMaterials = 64;  // material ids are uint8; per-thread sigma lives in smem
+constexpr int kMaxGroups = 1024;
+
+// Status bits written by kernels (read by vrc_sync / vrc_read_tally).
+constexpr unsigned kStatusNonfinite = 1u;
+constexpr unsigned kStatusTraversal = 2u;
+
+// Device counters (unsigned long long each).
+enum Counter { kCntSegments = 0, kCntRays = 1, kCntRejected = 2, kCntOverflow = 3, kNumCounters = 4 };
+
+// A value held as an unevaluated sum hi + lo of two float32 ("double-float").
+struct df {
+  float hi, lo;
+};
+
+// Uniform Cartesian mesh, geometry split into double-float pairs on the host.
+struct MeshDev {
+  int32_t n[3];
+  int64_t ncells;
+  int64_t stride[3];  // 1, nx, nx*ny
+  df org[3];          // x0, y0, z0
+  df h[3];            // dx, dy, dz
+  df inv_h[3];        // 1/dx, 1/dy, 1/dz
+  const uint8_t *mat; // [nz][ny][nx]
+};
+
+// Cross sections on the union energy grid of all materials.
+struct XsDev {
+  int32_t n_union;   // points on the union grid (0 = every material void)
+  int32_t m_pad;     // row stride (floats) of S
+  int32_t n_mat;     // materials
+  int32_t n_hash;    // hash bins over log2(E)
+  float l2min;       // log2 of the first grid energy
+  float inv_bw;      // bins per unit of log2(E)
+  const double *E;      // [n_union] union grid energies (eV)
+  const double *inv_dE; // [n_union-1] 1/(E[i+1]-E[i])
+  const float *S;       // [n_union][m_pad] sigma_t at the union points
+  const int32_t *hash;  // [n_hash+1] interval index at each bin's lower energy
+};
+
+struct RayPtrs {
+  const float *x, *y, *z, *u, *v, *w, *E, *wt;
+  int64_t n;
+};
+
+struct CastArgs {
+  MeshDev mesh;
+  XsDev xs;
+  const double *edges;  // [n_groups+1] or nullptr (single group, every energy)
+  int32_t n_groups;
+  RayPtrs rays;
+  double *tally;        // [n_groups][ncells]
+  unsigned long long *counters;
+  unsigned int *status;
+};
+
+// Launchers (vrc_cast.cu).  smem_bytes() gives the dynamic shared memory a
+// cast launch of the given block size needs.
+size_t cast_smem_bytes(int form, const CastArgs &a, int block);
+cudaError_t launch_cast(int form, const CastArgs &a, int grid, int block, cudaStream_t s);
+cudaError_t cast_occupancy(int form, const CastArgs &a, int block, int *blocks_per_sm);
+cudaError_t launch_scale_copy(const double *src, double *dst, int64_t n, double scale,
+                              cudaStream_t s);
+
+}  // namespace vrc

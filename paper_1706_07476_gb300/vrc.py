@@ -1,0 +1,273 @@
+"""Python binding of libvrc (include/vrc.h): the same calls, argument marshalling only.
+
+Every step of the cast runs in the library's CUDA kernels.  There is no
+Python or CPU fallback: importing this module fails loudly when libvrc.so has
+not been built, and every call raises :class:`VrcError` with the library's
+message on failure.
+
+Arrays may be numpy arrays (host), torch CPU tensors (host, pinned or not) or
+torch CUDA tensors (device).  Streams may be ``None`` (the context's stream),
+a ``torch.cuda.Stream`` or a raw ``cudaStream_t`` integer.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvrc.so")
+
+VRC_OK = 0
+VRC_ERR_ARG = -1
+VRC_ERR_STATE = -2
+VRC_ERR_CUDA = -3
+VRC_ERR_OOM = -4
+VRC_ERR_TRAVERSAL = -5
+VRC_ERR_NONFINITE = -6
+VRC_FORM_PLAIN = 0
+VRC_FORM_FP32 = 1
+VRC_PER_VOLUME = 1
+
+RAY_FIELDS = ("x", "y", "z", "u", "v", "w", "E", "wt")
+
+
+class VrcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libvrc error {code}: {msg}")
+        self.code = code
+
+
+class vrc_options(C.Structure):
+    _fields_ = [("form", C.c_int32), ("sort", C.c_int32), ("sort_cell_bits", C.c_int32),
+                ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("device", C.c_int32)]
+
+
+class vrc_mesh_desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("material", C.c_void_p), ("n_materials", C.c_int32), ("n_groups", C.c_int32),
+                ("group_edges", C.c_void_p)]
+
+
+class vrc_rays(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in RAY_FIELDS] + [("n", C.c_int64), ("on_device", C.c_int32)]
+
+
+class vrc_stats(C.Structure):
+    _fields_ = [("segments", C.c_int64), ("rays", C.c_int64), ("rejected", C.c_int64),
+                ("overflow", C.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    lib = C.CDLL(LIB_PATH)
+    P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "vrc_default_options": ([P], None),
+        "vrc_create_mesh": ([P, P, P], C.c_int),
+        "vrc_load_xs": ([P, I32, P, P, I64], C.c_int),
+        "vrc_cast_rays": ([P, P, P], C.c_int),
+        "vrc_sync": ([P, P, P], C.c_int),
+        "vrc_read_tally": ([P, P, I64, I32, P], C.c_int),
+        "vrc_tally_device_ptr": ([P], C.c_void_p),
+        "vrc_reset_tally": ([P, P], C.c_int),
+        "vrc_set_options": ([P, P], C.c_int),
+        "vrc_destroy": ([P], None),
+        "vrc_last_error": ([], C.c_char_p),
+        "vrc_device_count": ([], C.c_int),
+        "vrc_version": ([], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    """The loaded ctypes library (for callers that need a symbol directly)."""
+    return _lib
+
+
+def vrc_last_error() -> str:
+    return (_lib.vrc_last_error() or b"").decode()
+
+
+def _check(rc: int, ok=(VRC_OK,)) -> int:
+    if rc not in ok:
+        raise VrcError(rc, vrc_last_error())
+    return rc
+
+
+def vrc_device_count() -> int:
+    return int(_lib.vrc_device_count())
+
+
+def vrc_version() -> int:
+    return int(_lib.vrc_version())
+
+
+def require_device():
+    if vrc_device_count() < 1:
+        raise RuntimeError("libvrc found no CUDA device")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return int(stream.cuda_stream) or None
+
+
+def vrc_default_options(**kw) -> vrc_options:
+    o = vrc_options()
+    _lib.vrc_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, int(v))
+    return o
+
+
+class Context:
+    """Owns one vrc_ctx handle; destroyed explicitly or when collected."""
+
+    def __init__(self, handle, ncells, n_groups, spacing):
+        self.handle = handle
+        self.ncells = ncells
+        self.n_groups = n_groups
+        self.spacing = spacing
+        self._keep = []
+
+    @property
+    def tally_size(self):
+        return self.ncells * self.n_groups
+
+    def close(self):
+        if self.handle:
+            _lib.vrc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def vrc_create_mesh(mesh, n_materials: int, group_edges=None, options: vrc_options | None = None) -> Context:
+    """mesh: object with nx, ny, nz, x0..z0, dx..dz and uint8 material [nz][ny][nx]."""
+    mat = np.ascontiguousarray(mesh.material, dtype=np.uint8).reshape(-1)
+    edges = None if group_edges is None else np.ascontiguousarray(group_edges, np.float64)
+    d = vrc_mesh_desc(mesh.nx, mesh.ny, mesh.nz, mesh.x0, mesh.y0, mesh.z0, mesh.dx, mesh.dy,
+                      mesh.dz, mat.ctypes.data, int(n_materials),
+                      1 if edges is None else len(edges) - 1,
+                      None if edges is None else edges.ctypes.data)
+    h = C.c_void_p()
+    _check(_lib.vrc_create_mesh(C.byref(d), None if options is None else C.byref(options),
+                                C.byref(h)))
+    return Context(h, mesh.nx * mesh.ny * mesh.nz, d.n_groups, (mesh.dx, mesh.dy, mesh.dz))
+
+
+def vrc_load_xs(ctx: Context, material: int, E, sigma):
+    if E is None:
+        _check(_lib.vrc_load_xs(ctx.handle, int(material), None, None, 0))
+        return
+    E = np.ascontiguousarray(E, np.float64)
+    S = np.ascontiguousarray(sigma, np.float64)
+    if E.shape != S.shape:
+        raise ValueError("E and sigma must have the same length")
+    _check(_lib.vrc_load_xs(ctx.handle, int(material), E.ctypes.data, S.ctypes.data, len(E)))
+
+
+def _ray_struct(rays: dict):
+    arrs = [rays[k] for k in RAY_FIELDS]
+    keep = []
+    ptrs = []
+    on_dev = None
+    n = None
+    for a in arrs:
+        if isinstance(a, np.ndarray):
+            a = np.ascontiguousarray(a, np.float32)
+            dev = False
+            ptr, cnt = a.ctypes.data, a.shape[0]
+        else:  # torch tensor
+            if a.dtype != __import__("torch").float32 or not a.is_contiguous():
+                raise TypeError("ray tensors must be contiguous float32")
+            dev = a.is_cuda
+            ptr, cnt = a.data_ptr(), a.shape[0]
+        keep.append(a)
+        if on_dev is None:
+            on_dev, n = dev, cnt
+        elif dev != on_dev or cnt != n:
+            raise ValueError("ray arrays must all be on the same side and of the same length")
+        ptrs.append(ptr)
+    r = vrc_rays(*ptrs, int(n), int(bool(on_dev)))
+    return r, keep
+
+
+def vrc_cast_rays(ctx: Context, rays: dict, stream=None):
+    r, keep = _ray_struct(rays)
+    _check(_lib.vrc_cast_rays(ctx.handle, C.byref(r), _stream_handle(stream)))
+    ctx._keep = keep  # device arrays stay referenced until the next cast
+
+
+def vrc_sync(ctx: Context, stream=None):
+    """Waits; returns (status code, stats dict).  Raises only for ARG/CUDA errors."""
+    st = vrc_stats()
+    rc = _lib.vrc_sync(ctx.handle, _stream_handle(stream), C.byref(st))
+    _check(rc, ok=(VRC_OK, VRC_ERR_NONFINITE, VRC_ERR_TRAVERSAL))
+    return rc, dict(segments=st.segments, rays=st.rays, rejected=st.rejected, overflow=st.overflow)
+
+
+def vrc_read_tally(ctx: Context, out: np.ndarray | None = None, flags: int = 0, stream=None):
+    """Copies the tally to host float64 [n_groups*ncells]; returns (array, status code)."""
+    if out is None:
+        out = np.empty(ctx.tally_size, np.float64)
+    if out.dtype != np.float64 or not out.flags.c_contiguous or out.size != ctx.tally_size:
+        raise ValueError("out must be a contiguous float64 array of the tally size")
+    rc = _lib.vrc_read_tally(ctx.handle, out.ctypes.data, out.size, int(flags), _stream_handle(stream))
+    _check(rc, ok=(VRC_OK, VRC_ERR_NONFINITE, VRC_ERR_TRAVERSAL))
+    return out, rc
+
+
+def vrc_tally_device_ptr(ctx: Context) -> int:
+    return int(_lib.vrc_tally_device_ptr(ctx.handle) or 0)
+
+
+def vrc_reset_tally(ctx: Context, stream=None):
+    _check(_lib.vrc_reset_tally(ctx.handle, _stream_handle(stream)))
+
+
+def vrc_set_options(ctx: Context, options: vrc_options):
+    _check(_lib.vrc_set_options(ctx.handle, C.byref(options)))
+
+
+def vrc_destroy(ctx: Context):
+    ctx.close()
+
+
+def context_for(problem, options: vrc_options | None = None) -> Context:
+    """vrc_create_mesh + vrc_load_xs for a vrc_workloads.Problem."""
+    ctx = vrc_create_mesh(problem.mesh, problem.n_materials, problem.group_edges, options)
+    for m, t in enumerate(problem.tables):
+        if t is None:
+            vrc_load_xs(ctx, m, None, None)
+        else:
+            vrc_load_xs(ctx, m, t[0], t[1])
+    return ctx

@@ -1,0 +1,268 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerance: the plain form and the FP32 form must both match the oracle to
+<= 1e-4 relative per (group, cell) wherever the oracle tally is >= 1e-30
+(the Eq. 7 relative difference; cells below that floor are held to an
+absolute 1e-28).  The floating-point budget behind 1e-4: float32 cross
+sections and path lengths (2^-24 each), float32 exponentials (a few ulp) and,
+in the FP32 form, a compensated float32 optical depth: a few 1e-7 per score,
+far below 1e-4; the margin covers cells whose only contributions are short
+corner clips, where the double-float crossing parameters (about 2^-46
+relative) dominate.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import vrc_workloads as W
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+ABS_BELOW = 1e-28
+FORMS = {"plain": 0, "fp32": 1}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _device_rays(torch, rays):
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in rays.items()}
+
+
+def run_gpu(vrc, torch, prob, form, rays=None, on_device=True, options=None, batches=1):
+    opts = options or vrc.vrc_default_options(form=form)
+    ctx = vrc.context_for(prob, opts)
+    try:
+        rays = prob.rays if rays is None else rays
+        n = len(rays["x"])
+        for b in range(batches):
+            sl = slice(n * b // batches, n * (b + 1) // batches)
+            part = {k: v[sl] for k, v in rays.items()}
+            if on_device:
+                part = _device_rays(torch, part)
+            stream = torch.cuda.current_stream()
+            vrc.vrc_cast_rays(ctx, part, stream=stream)
+        rc, stats = vrc.vrc_sync(ctx, torch.cuda.current_stream())
+        tally, rc2 = vrc.vrc_read_tally(ctx)
+        assert rc == rc2
+        return tally, rc, stats
+    finally:
+        ctx.close()
+
+
+def assert_parity(want, got, tol=REL_TOL):
+    rep = H.rel_err_report(want, got)
+    assert rep["max_rel"] <= tol, rep
+    assert rep["max_abs_below"] <= ABS_BELOW, rep
+    return rep
+
+
+# ---------------------------------------------------------------- golden cases
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+@pytest.mark.parametrize("case", H.golden_cases(), ids=lambda c: c["name"])
+def test_golden_closed_forms_gpu(vrc, torch_cuda, case, form):
+    prob = H.golden_problem(case)
+    want = H.golden_expected(case, prob)
+    got, rc, _ = run_gpu(vrc, torch_cuda, prob, FORMS[form])
+    assert rc == vrc.VRC_OK
+    nz = want != 0
+    np.testing.assert_allclose(got[nz], want[nz], rtol=1e-6)
+    assert np.all(np.abs(got[~nz]) <= 1e-12)
+
+
+# ---------------------------------------------------------------- workloads
+
+@pytest.fixture(scope="module")
+def uniform32():
+    prob = W.uniform_small()  # 32^3, 2 materials, 2^17 rays, seed 0 (full size)
+    want, st = oracle.cast(prob)
+    return prob, want, st
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_uniform32_full_vs_oracle(vrc, torch_cuda, uniform32, form):
+    prob, want, st = uniform32
+    got, rc, stats = run_gpu(vrc, torch_cuda, prob, FORMS[form])
+    assert rc == vrc.VRC_OK
+    assert stats["rays"] == prob.n_rays and stats["rejected"] == 0 and stats["overflow"] == 0
+    assert stats["segments"] == st["segments"]
+    rep = assert_parity(want, got)
+    assert rep["n_cells"] == prob.tally_size
+
+
+@pytest.fixture(scope="module")
+def slab_small():
+    prob = W.slab_room(seed=1, n=48, n_rays=1 << 16, n_points=2000, n_resonances=40)
+    want, st = oracle.cast(prob)
+    return prob, want, st
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_slab_groups_vs_oracle(vrc, torch_cuda, slab_small, form):
+    prob, want, st = slab_small
+    got, rc, stats = run_gpu(vrc, torch_cuda, prob, FORMS[form])
+    assert rc == vrc.VRC_OK
+    assert stats["segments"] == st["segments"]
+    assert_parity(want, got)
+
+
+@pytest.fixture(scope="module")
+def lattice_small():
+    prob = W.pin_lattice(seed=2, pins=3, cells_per_pin=32, nz=6, n_rays=1 << 15, n_points=2000,
+                         n_resonances=40)
+    want, st = oracle.cast(prob)
+    return prob, want, st
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_pin_lattice_vs_oracle(vrc, torch_cuda, lattice_small, form):
+    prob, want, st = lattice_small
+    got, rc, stats = run_gpu(vrc, torch_cuda, prob, FORMS[form])
+    assert rc == vrc.VRC_OK
+    assert stats["segments"] == st["segments"]
+    assert_parity(want, got)
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_ragged_mesh_and_offsets(vrc, torch_cuda, form):
+    """Non-cubic mesh, non-unit and unequal spacings, shifted origin, rays
+    starting inside and outside the box, a ragged ray count."""
+    rng = np.random.default_rng(21)
+    nx, ny, nz = 37, 5, 19
+    mat = rng.integers(0, 5, size=(nz, ny, nx)).astype(np.uint8)
+    mesh = W.Mesh(nx, ny, nz, -3.25, 11.0, 0.125, 0.3, 2.5, 0.0625, mat)
+    tables = [W.xs_table(rng, 300, 4, peak_lo=0.1, peak_hi=30.0) for _ in range(5)]
+    tables[2] = None
+    n = 10007
+    lo, hi = np.array(mesh.lo), np.array(mesh.hi)
+    pos = lo - 0.3 * (hi - lo) + 1.6 * (hi - lo) * rng.random((n, 3))
+    d = rng.normal(size=(n, 3))
+    rays = W.make_rays(*(pos[:, k].astype(np.float32) for k in range(3)),
+                       *(d[:, k].astype(np.float32) for k in range(3)), W.log_uniform(rng, n),
+                       rng.lognormal(0, 0.5, n).astype(np.float32))
+    prob = W.Problem("ragged", mesh, tables, W.log_group_edges(3, 1e-3, 1e6), rays)
+    want, st = oracle.cast(prob)
+    got, rc, stats = run_gpu(vrc, torch_cuda, prob, FORMS[form])
+    assert rc == vrc.VRC_OK
+    assert stats["segments"] == st["segments"]
+    assert_parity(want, got)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def _tiny():
+    rng = np.random.default_rng(3)
+    mat = rng.integers(0, 2, size=(4, 4, 4)).astype(np.uint8)
+    mesh = W.Mesh(4, 4, 4, 0.0, 0.0, 0.0, 1.0, 1.0, 1.0, mat)
+    return mesh, [W.xs_table(rng, 50, 2), None]
+
+
+def test_empty_batch_is_noop(vrc, torch_cuda):
+    mesh, tables = _tiny()
+    prob = W.Problem("e", mesh, tables, None, W.make_rays(*([np.zeros(0, np.float32)] * 8)))
+    got, rc, stats = run_gpu(vrc, torch_cuda, prob, 0)
+    assert rc == vrc.VRC_OK and stats["rays"] == 0 and not got.any()
+
+
+def test_bad_rays_are_reported_and_skipped(vrc, torch_cuda):
+    mesh, tables = _tiny()
+    rng = np.random.default_rng(4)
+    n = 64
+    pos = (4 * rng.random((n, 3))).astype(np.float32)
+    d = rng.normal(size=(n, 3)).astype(np.float32)
+    E = W.log_uniform(rng, n)
+    wt = np.ones(n, np.float32)
+    rays = W.make_rays(pos[:, 0], pos[:, 1], pos[:, 2], d[:, 0], d[:, 1], d[:, 2], E, wt)
+    rays["x"][3] = np.nan
+    rays["u"][5] = rays["v"][5] = rays["w"][5] = 0.0
+    rays["E"][7] = -1.0
+    rays["wt"][9] = np.inf
+    prob = W.Problem("bad", mesh, tables, None, rays)
+    want, st = oracle.cast(prob)
+    assert st["rejected"] == 4
+    got, rc, stats = run_gpu(vrc, torch_cuda, prob, 0)
+    assert rc == vrc.VRC_ERR_NONFINITE
+    assert stats["rejected"] == 4 and stats["rays"] == n
+    assert_parity(want, got)
+
+
+def test_host_rays_equal_device_rays_and_batches_accumulate(vrc, torch_cuda, uniform32):
+    prob, want, _ = uniform32
+    a, _, sa = run_gpu(vrc, torch_cuda, prob, 0, on_device=False)
+    b, _, sb = run_gpu(vrc, torch_cuda, prob, 0, on_device=True, batches=7)
+    assert sa["segments"] == sb["segments"]
+    np.testing.assert_allclose(a, b, rtol=1e-12)
+
+
+def test_reset_per_volume_and_device_pointer(vrc, torch_cuda):
+    torch = torch_cuda
+    rng = np.random.default_rng(8)
+    mat = np.zeros((3, 3, 3), np.uint8)
+    mesh = W.Mesh(3, 3, 3, 0.0, 0.0, 0.0, 0.5, 2.0, 0.25, mat)
+    prob = W.Problem("v", mesh, [W.xs_table(rng, 30, 1)], None,
+                     W.make_rays(*(np.full(5, c, np.float32) for c in (0.7, 3.1, 0.3)),
+                                 *(np.full(5, c, np.float32) for c in (0.3, -0.2, 1.0)),
+                                 np.full(5, 2.0, np.float32), np.full(5, 1.5, np.float32)))
+    want, _ = oracle.cast(prob)
+    ctx = vrc.context_for(prob)
+    try:
+        vrc.vrc_cast_rays(ctx, _device_rays(torch, prob.rays))
+        raw, rc = vrc.vrc_read_tally(ctx)
+        pv, rc2 = vrc.vrc_read_tally(ctx, flags=vrc.VRC_PER_VOLUME)
+        assert rc == rc2 == vrc.VRC_OK
+        np.testing.assert_allclose(raw, want, rtol=1e-6)
+        np.testing.assert_allclose(pv, want / (0.5 * 2.0 * 0.25), rtol=1e-6)
+        ptr = vrc.vrc_tally_device_ptr(ctx)
+        assert ptr != 0
+        vrc.vrc_reset_tally(ctx)
+        again, _ = vrc.vrc_read_tally(ctx)
+        assert not again.any()
+        _, stats = vrc.vrc_sync(ctx)
+        assert stats["segments"] == 0
+    finally:
+        ctx.close()
+
+
+def test_missing_table_is_state_error(vrc, torch_cuda):
+    mesh, tables = _tiny()
+    ctx = vrc.vrc_create_mesh(mesh, 2)
+    try:
+        vrc.vrc_load_xs(ctx, 0, *tables[0])  # material 1 is used but never loaded
+        rays = W.make_rays(*(np.full(1, 0.5, np.float32) for _ in range(3)),
+                           np.ones(1, np.float32), np.zeros(1, np.float32),
+                           np.zeros(1, np.float32), np.ones(1, np.float32), np.ones(1, np.float32))
+        with pytest.raises(vrc.VrcError) as ei:
+            vrc.vrc_cast_rays(ctx, rays)
+        assert ei.value.code == vrc.VRC_ERR_STATE
+    finally:
+        ctx.close()
+
+
+def test_ray_starting_on_faces_and_parallel_to_planes(vrc, torch_cuda):
+    """Starts exactly on grid planes, directions with zero components, a ray
+    sliding along a face, and rays that only clip a corner."""
+    mesh, tables = _tiny()
+    P = [(1.0, 2.0, 3.0), (0.0, 0.5, 0.5), (4.0, 0.5, 0.5), (2.0, 2.0, 0.25), (0.5, 0.5, 0.5),
+         (1.0, 1.0, 1.0), (3.999, 0.001, 2.5)]
+    D = [(1, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 0, 1), (0, 1, 1), (1, 1, 1), (1, -1, 0.001)]
+    n = len(P)
+    rays = W.make_rays(*(np.array([p[k] for p in P], np.float32) for k in range(3)),
+                       *(np.array([d[k] for d in D], np.float32) for k in range(3)),
+                       np.full(n, 3.0, np.float32), np.ones(n, np.float32))
+    prob = W.Problem("faces", mesh, tables, None, rays)
+    want, st = oracle.cast(prob)
+    for form in (0, 1):
+        got, rc, stats = run_gpu(vrc, torch_cuda, prob, form)
+        assert rc == vrc.VRC_OK
+        assert_parity(want, got, tol=1e-5)
