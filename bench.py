@@ -1,0 +1,417 @@
+#!/usr/bin/env python3
+"""Throughput of the VRC cast on GB300: ray-cell segments per second.
+
+One step casts one batch of 2^24 synthetic rays through the 256^3 slab mesh
+(8 materials with 20,000-point tables, 16 energy groups) into the
+device-resident tally: the whole hot path (cross-section lookup, grid walk,
+Eq. 4 score, tally update) in libvrc's kernels, called through the C ABI.
+
+Default: N=1, both precision forms timed side by side; the headline line is
+the FP32 form.  Under torchrun every rank casts its own replica batch into its
+own tally (weak scaling, no collective in the timed region).
+
+--impl reference times the FP64 CPU oracle on the host cores instead, on
+bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import vrc_workloads as W  # noqa: E402
+
+WORKLOAD = ("slab256: 256^3 mesh of 1 cm cells, 8 materials with 20,000-point tables "
+            "(200 Lorentzian resonances each), 16 random axis-aligned slabs, 2^24 rays "
+            "(uniform positions, isotropic directions, log-uniform energies, lognormal(0,0.5) "
+            "weights), 16 log-uniform energy groups, seed 1")
+METRIC = "ray-cell segments/s at <=1e-4 tally rel. err vs FP64 oracle; % HBM roofline"
+UNIT = "segments/s"
+# Algorithmic bytes: per segment 8 B tally read + 8 B tally write + 1 B material
+# id; per ray 32 B of ray data (x, y, z, u, v, w, E, wt as float32).
+BYTES_PER_SEGMENT = 17
+BYTES_PER_RAY = 32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["vrc", "reference"], default="vrc")
+    ap.add_argument("--forms", default="plain,fp32", help="forms to time; the last is the headline")
+    ap.add_argument("--sort", type=int, default=-1, help="ray sorting: -1 auto, 0 off, 1 on")
+    ap.add_argument("--n-rays", type=int, default=1 << 24)
+    ap.add_argument("--mesh", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parity-sample", action="store_true")
+    ap.add_argument("--no-micro", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="target wall time of the CPU-baseline oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args):
+    return W.slab_room(seed=1, n=args.mesh, n_rays=args.n_rays)
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- helpers
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def profiled_traffic(kernel_tag: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current cast kernel source (matched by the recorded source hash)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}_slab256.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    h = hashlib.sha256()
+    for f in ("vrc_device.cuh", "vrc_cast.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1706_07476_gb300", "csrc", f), "rb").read())
+    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("source_sha256:", "traffic_bytes_per_launch:")))
+    if fields.get("source_sha256", "").strip() != h.hexdigest():
+        return None
+    try:
+        return float(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(prob, target_s: float, oracle):
+    """The FP64 oracle as it stands on all host cores, on the first rays of
+    the same workload, sized to take about target_s seconds."""
+    threads = oracle.hardware_threads()
+    tally = np.zeros(prob.tally_size, np.float64)
+    n = 1 << 14
+    for _ in range(4):  # grow the sample until it takes about target_s
+        tally[:] = 0.0
+        sample = W.take_rays(prob, slice(0, n)).rays
+        t0 = time.perf_counter()
+        _, st = oracle.cast(prob, nthreads=threads, rays=sample, tally=tally)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * target_s or n >= prob.n_rays:
+            break
+        n = int(min(prob.n_rays, n * min(64.0, 0.9 * target_s / max(dt, 1e-3))))
+    return dict(value=st["segments"] / dt, unit=UNIT, cores=st["threads"], kind="oracle",
+                sample=f"first {n} of the {prob.n_rays} rays of the slab256 workload "
+                       f"({st['segments']} segments, {dt:.1f} s)"), tally, n
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    prob = workload(args)
+    threads = oracle.hardware_threads()
+    per_step = max(1 << 12, min(prob.n_rays, 1 << 18))
+    tally = np.zeros(prob.tally_size, np.float64)
+    segs, times = [], []
+    for s in range(args.warmup + args.steps):
+        lo = (s * per_step) % prob.n_rays
+        sample = W.take_rays(prob, slice(lo, lo + per_step)).rays
+        t0 = time.perf_counter()
+        _, st = oracle.cast(prob, nthreads=threads, rays=sample, tally=tally)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            segs.append(st["segments"])
+            times.append(dt)
+    value = sum(segs) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rays_per_step": per_step,
+                   "note": "each step is a bounded sample of the workload's rays"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step} consecutive rays of the slab256 workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1706_07476_gb300 import micro, vrc
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    prob = workload(args)
+    dev_rays = {k: torch.from_numpy(v).cuda() for k, v in prob.rays.items()}
+    # a dedicated stream: the legacy default stream has handle 0, which the C
+    # ABI reads as "the context's own stream"
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    form_id = {"plain": vrc.VRC_FORM_PLAIN, "fp32": vrc.VRC_FORM_FP32}
+
+    results = {}
+    ctxs = {}
+    clocks = None
+    launches = 0
+    for fi, form in enumerate(forms):
+        headline = fi == len(forms) - 1
+        ctx = vrc.context_for(prob, vrc.vrc_default_options(form=form_id[form], sort=args.sort,
+                                                            device=local))
+        ctxs[form] = ctx
+        for _ in range(args.warmup):
+            vrc.vrc_cast_rays(ctx, dev_rays, stream=stream)
+        rc, _ = vrc.vrc_sync(ctx, stream)
+        assert rc == vrc.VRC_OK, rc
+        vrc.vrc_reset_tally(ctx, stream)
+        vrc.vrc_enable_timing(ctx, True)
+        vrc.vrc_get_timing(ctx, stream, reset=True)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if headline else None
+        if sampler:
+            sampler.__enter__()
+        l0 = vrc.vrc_launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            vrc.vrc_cast_rays(ctx, dev_rays, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        n_launch = vrc.vrc_launch_count() - l0
+        if sampler:
+            sampler.__exit__(None, None, None)
+            clocks = sampler.summary()
+            launches = n_launch
+        barrier()
+        elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+        rc, stats = vrc.vrc_sync(ctx, stream)
+        timing = vrc.vrc_get_timing(ctx, stream)
+        assert rc == vrc.VRC_OK and stats["overflow"] == 0 and stats["rejected"] == 0, (rc, stats)
+        seg_per_step = stats["segments"] / args.steps
+        total = sum_over_ranks(stats["segments"])
+        kernel_s = timing["cast_ms"] / 1e3 / max(timing["cast_launches"], 1)
+        alg_bytes = seg_per_step * BYTES_PER_SEGMENT + prob.n_rays * BYTES_PER_RAY
+        results[form] = dict(value=total / elapsed, ms_per_step=1e3 * elapsed / args.steps,
+                             segments_per_step=seg_per_step, kernel_ms=1e3 * kernel_s,
+                             alg_gbs=alg_bytes / kernel_s / 1e9, launches=n_launch)
+
+    head = forms[-1]
+    R = results[head]
+
+    # end to end: host rays from pinned memory through the C ABI, per-step
+    # device->host read of the step's status and counters
+    e2e = None
+    ctx = ctxs[head]
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in prob.rays.items()}
+    vrc.vrc_enable_timing(ctx, False)
+    for _ in range(max(1, args.warmup)):
+        vrc.vrc_cast_rays(ctx, pinned, stream=stream)
+        vrc.vrc_sync(ctx, stream)
+    vrc.vrc_reset_tally(ctx, stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    seg = 0
+    for _ in range(e2e_steps):
+        vrc.vrc_cast_rays(ctx, pinned, stream=stream)
+        rc, st = vrc.vrc_sync(ctx, stream)
+    t1 = time.perf_counter()
+    seg = st["segments"]
+    barrier()
+    e2e_t = max_over_ranks(t1 - t0)
+    e2e = {"value": sum_over_ranks(seg) / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": BYTES_PER_RAY * prob.n_rays,
+           "d2h_bytes_per_step": 4 * 8 + 4,
+           "note": "vrc_cast_rays on pinned host rays (upload inside) + vrc_sync reading the "
+                   "step's counters and status; the tally stays on the device"}
+
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    roof = {"bound": "hbm", "achieved": R["alg_gbs"], "peak": hbm, "unit": "GB/s",
+            "frac": R["alg_gbs"] / hbm, "traffic": profiled_traffic(f"k_cast_{head}"),
+            "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)",
+            "algorithmic_bytes": f"{BYTES_PER_SEGMENT} B/segment + {BYTES_PER_RAY} B/ray",
+            "kernel": f"k_cast<{head}>", "kernel_ms": R["kernel_ms"]}
+
+    extra = {}
+    if not args.no_micro and rank == 0:
+        try:
+            red_hbm = micro.red_f64_rate(torch, 1 << 28, 1 << 28)
+            red_l2 = micro.red_f64_rate(torch, 1 << 22, 1 << 28)
+            extra["micro"] = {
+                "red_f64_hbm_per_s": red_hbm, "red_f64_l2_per_s": red_l2,
+                "fma_f64_flops": micro.arith_rate(torch, "fma_f64"),
+                "fma_f32_flops": micro.arith_rate(torch, "fma_f32"),
+                "expm1_f64_per_s": micro.arith_rate(torch, "expm1_f64", iters=500),
+                "expm1_f32_per_s": micro.arith_rate(torch, "expm1_f32", iters=500),
+            }
+            roof["atomic_roof_segments_per_s"] = red_hbm
+            roof["frac_of_atomic_roof"] = R["value"] / world / red_hbm
+        except Exception as e:  # measurement aid only
+            extra["micro"] = {"error": str(e)}
+
+    line = {
+        "metric": METRIC, "value": R["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": R["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if head == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rays_per_step": prob.n_rays,
+                   "segments_per_step": R["segments_per_step"], "form": head,
+                   "sort": args.sort, "tally": "float64 [16][256^3] (2 GiB)",
+                   "l2": "inputs larger than L2 (512 MiB rays, 2 GiB tally, 16 MiB mesh); no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "forms": results,
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches,
+    }
+    line.update(extra)
+
+    if rank == 0 and world == 1:
+        import oracle
+        if not args.no_cpu_baseline:
+            cb, otally, n_sample = cpu_baseline(prob, args.cpu_seconds, oracle)
+            line["cpu_baseline"] = cb
+            if not args.no_parity_sample:
+                # the timed configuration, on the sampled rays, against the oracle
+                par = {}
+                for form in forms:
+                    c = ctxs[form]
+                    vrc.vrc_reset_tally(c, stream)
+                    sub = {k: v[:n_sample] for k, v in dev_rays.items()}
+                    vrc.vrc_cast_rays(c, sub, stream=stream)
+                    got, rc = vrc.vrc_read_tally(c, stream=stream)
+                    sel = otally >= 1e-30
+                    rel = np.abs(got[sel] - otally[sel]) / otally[sel]
+                    par[form] = {"rays": n_sample, "max_rel_err": float(rel.max()),
+                                 "mean_rel_err": float(rel.mean()), "cells": int(sel.sum())}
+                line["parity_sample"] = par
+    for c in ctxs.values():
+        c.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

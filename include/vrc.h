@@ -176,6 +176,18 @@ void vrc_destroy(vrc_ctx *c);
 /* Thread-local description of the last error ("" if none). */
 const char *vrc_last_error(void);
 
+/* Kernel timing.  When enabled, every cast records CUDA events on the
+ * launching stream around its kernels; vrc_get_timing waits for the stream
+ * and returns the summed device time (ms) of the cast kernels and of the ray
+ * sort kernels, and the number of cast-kernel launches, since timing was
+ * enabled or last read with reset != 0. */
+int vrc_enable_timing(vrc_ctx *c, int32_t on);
+int vrc_get_timing(vrc_ctx *c, void *cuda_stream, double *cast_ms, double *sort_ms,
+                   int64_t *cast_launches, int32_t reset);
+
+/* Number of kernels libvrc has launched in this process (all contexts). */
+int64_t vrc_launch_count(void);
+
 /* Number of CUDA devices visible (0 when none or on failure). */
 int vrc_device_count(void);
 

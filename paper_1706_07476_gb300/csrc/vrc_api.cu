@@ -1,5 +1,6 @@
 // Host implementation of the libvrc C ABI (include/vrc.h).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,6 +17,7 @@ using namespace vrc;
 namespace {
 
 thread_local std::string g_last_error;
+std::atomic<long long> g_launches{0};
 
 int fail(int code, const char *fmt, ...) {
   char buf[512];
@@ -83,6 +85,14 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 }  // namespace
 
+void vrc::note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// A pair of events bracketing one group of kernel launches.
+struct TimedSpan {
+  cudaEvent_t start, stop;
+  int kind;  // 0 cast, 1 sort
+};
+
 struct vrc_ctx {
   int device = 0;
   int num_sms = 0;
@@ -110,9 +120,30 @@ struct vrc_ctx {
   DevBuf stage;    // device copy of host rays
   DevBuf scratch;  // finalize staging
 
+  bool timing = false;
+  std::vector<TimedSpan> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double cast_ms = 0.0, sort_ms = 0.0;
+  int64_t cast_launches = 0;
+
+  cudaError_t get_event(cudaEvent_t *e) {
+    if (!event_pool.empty()) {
+      *e = event_pool.back();
+      event_pool.pop_back();
+      return cudaSuccess;
+    }
+    return cudaEventCreate(e);
+  }
+
   ~vrc_ctx() {
     DeviceGuard g(device);
     if (stream) cudaStreamSynchronize(stream);
+    for (auto &t : pending) {
+      cudaEventSynchronize(t.stop);
+      cudaEventDestroy(t.start);
+      cudaEventDestroy(t.stop);
+    }
+    for (auto e : event_pool) cudaEventDestroy(e);
     cudaFree(d_mat);
     cudaFree(d_edges);
     cudaFree(d_tally);
@@ -418,6 +449,11 @@ int vrc_cast_rays(vrc_ctx *c, const vrc_rays *r, void *cuda_stream) {
       *dst[k] = dk;
     }
   }
+  cudaEvent_t uploaded = nullptr;
+  if (!r->on_device) {
+    VRC_CUDA(c->get_event(&uploaded), "creating the upload event");
+    VRC_CUDA(cudaEventRecord(uploaded, s), "recording the upload event");
+  }
   CastArgs a = make_args(c, rp);
   const int form = c->opt.form;
   const int block = c->opt.block > 0 ? c->opt.block : 256;
@@ -428,10 +464,22 @@ int vrc_cast_rays(vrc_ctx *c, const vrc_rays *r, void *cuda_stream) {
   }
   const int64_t need = (r->n + block - 1) / block;
   const int grid = (int)std::min<int64_t>(need, (int64_t)c->num_sms * bps);
+  TimedSpan span{nullptr, nullptr, 0};
+  if (c->timing) {
+    VRC_CUDA(c->get_event(&span.start), "creating a timing event");
+    VRC_CUDA(c->get_event(&span.stop), "creating a timing event");
+    VRC_CUDA(cudaEventRecord(span.start, s), "recording a timing event");
+  }
   VRC_CUDA(launch_cast(form, a, grid, block, s), "launching the cast kernel");
-  if (!r->on_device) {
-    // the host arrays may be reused once the copies have completed
-    VRC_CUDA(cudaStreamSynchronize(s), "waiting for the ray upload");
+  if (c->timing) {
+    VRC_CUDA(cudaEventRecord(span.stop, s), "recording a timing event");
+    c->pending.push_back(span);
+    c->cast_launches += 1;
+  }
+  if (uploaded) {
+    // the caller may reuse its host arrays once the copies have completed
+    VRC_CUDA(cudaEventSynchronize(uploaded), "waiting for the ray upload");
+    c->event_pool.push_back(uploaded);
   }
   return VRC_OK;
 }
@@ -511,6 +559,39 @@ int vrc_set_options(vrc_ctx *c, const vrc_options *opt) {
 void vrc_destroy(vrc_ctx *c) { delete c; }
 
 const char *vrc_last_error(void) { return g_last_error.c_str(); }
+
+int vrc_enable_timing(vrc_ctx *c, int32_t on) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  c->timing = on != 0;
+  return VRC_OK;
+}
+
+int vrc_get_timing(vrc_ctx *c, void *cuda_stream, double *cast_ms, double *sort_ms,
+                   int64_t *cast_launches, int32_t reset) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  DeviceGuard g(c->device);
+  int rc = sync_streams(c, cuda_stream);
+  if (rc) return rc;
+  for (auto &t : c->pending) {
+    float ms = 0.f;
+    VRC_CUDA(cudaEventSynchronize(t.stop), "waiting for a timing event");
+    VRC_CUDA(cudaEventElapsedTime(&ms, t.start, t.stop), "reading a timing event");
+    (t.kind == 0 ? c->cast_ms : c->sort_ms) += ms;
+    c->event_pool.push_back(t.start);
+    c->event_pool.push_back(t.stop);
+  }
+  c->pending.clear();
+  if (cast_ms) *cast_ms = c->cast_ms;
+  if (sort_ms) *sort_ms = c->sort_ms;
+  if (cast_launches) *cast_launches = c->cast_launches;
+  if (reset) {
+    c->cast_ms = c->sort_ms = 0.0;
+    c->cast_launches = 0;
+  }
+  return VRC_OK;
+}
+
+int64_t vrc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int vrc_device_count(void) {
   int n = 0;

@@ -123,11 +123,13 @@ cudaError_t launch_cast(int form, const CastArgs &a, int grid, int block, cudaSt
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
     k_cast<kFormPlain><<<grid, block, L.total, s>>>(a, L);
+    note_launches(1);
   } else {
     cudaError_t e = cudaFuncSetAttribute(k_cast<kFormFp32>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
     k_cast<kFormFp32><<<grid, block, L.total, s>>>(a, L);
+    note_launches(1);
   }
   return cudaGetLastError();
 }
@@ -139,6 +141,7 @@ cudaError_t launch_scale_copy(const double *src, double *dst, int64_t n, double 
   int64_t want = (n + block - 1) / block;
   int grid = (int)std::min<int64_t>(want, 152 * 8);
   k_scale_copy<<<grid, block, 0, s>>>(src, dst, n, scale);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -63,6 +63,9 @@ struct CastArgs {
   unsigned int *status;
 };
 
+// Process-wide count of kernels launched by libvrc (vrc_launch_count).
+void note_launches(int n);
+
 // Launchers (vrc_cast.cu).  smem_bytes() gives the dynamic shared memory a
 // cast launch of the given block size needs.
 size_t cast_smem_bytes(int form, const CastArgs &a, int block);

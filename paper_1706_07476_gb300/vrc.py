@@ -80,6 +80,9 @@ def _load():
         "vrc_destroy": ([P], None),
         "vrc_last_error": ([], C.c_char_p),
         "vrc_device_count": ([], C.c_int),
+        "vrc_enable_timing": ([P, I32], C.c_int),
+        "vrc_get_timing": ([P, P, P, P, P, I32], C.c_int),
+        "vrc_launch_count": ([], C.c_int64),
         "vrc_version": ([], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -256,6 +259,22 @@ def vrc_reset_tally(ctx: Context, stream=None):
 
 def vrc_set_options(ctx: Context, options: vrc_options):
     _check(_lib.vrc_set_options(ctx.handle, C.byref(options)))
+
+
+def vrc_enable_timing(ctx: Context, on: bool = True):
+    _check(_lib.vrc_enable_timing(ctx.handle, int(bool(on))))
+
+
+def vrc_get_timing(ctx: Context, stream=None, reset: bool = False):
+    """Returns dict(cast_ms, sort_ms, cast_launches) summed since enable/reset."""
+    cast_ms, sort_ms, n = C.c_double(), C.c_double(), C.c_int64()
+    _check(_lib.vrc_get_timing(ctx.handle, _stream_handle(stream), C.byref(cast_ms),
+                               C.byref(sort_ms), C.byref(n), int(bool(reset))))
+    return dict(cast_ms=cast_ms.value, sort_ms=sort_ms.value, cast_launches=n.value)
+
+
+def vrc_launch_count() -> int:
+    return int(_lib.vrc_launch_count())
 
 
 def vrc_destroy(ctx: Context):
