@@ -64,8 +64,11 @@ typedef struct vrc_ctx vrc_ctx;
  * any field left at its "auto" value is chosen by the library. */
 typedef struct {
   int32_t form;           /* VRC_FORM_PLAIN (default) or VRC_FORM_FP32 */
-  int32_t sort;           /* ray sorting before the cast: 0 off, 1 on, -1 auto (default) */
-  int32_t sort_cell_bits; /* start-cell block of the sort key is 2^bits cells per axis; -1 auto */
+  int32_t sort;           /* counting sort of the rays by (energy group, number of cells
+                             crossed) before the cast: 0 off, 1 on, -1 auto (on for batches
+                             of 65,536 rays or more; default) */
+  int32_t sort_len_buckets; /* crossed-cell buckets per group in the sort key, 1..256;
+                               -1 auto (64, fewer when groups x buckets would pass 16,384) */
   int32_t block;          /* threads per block of the cast kernel; 0 auto */
   int32_t blocks_per_sm;  /* resident blocks per SM for the cast grid; 0 auto */
   int32_t device;         /* CUDA device ordinal for this context; -1 = current device */
@@ -137,6 +140,9 @@ int vrc_load_xs(vrc_ctx *c, int32_t material, const double *E_eV, const double *
 /* Casts a batch of rays and adds their Eq. 4 scores to the tally (Sec. 3:
  * per ray, cross-section lookup, ray cast, VRC score).  Asynchronous on the
  * stream: device arrays must stay valid until the stream passes this point.
+ * With sorting on, the rays are first copied, in sorted order, into
+ * context-owned scratch (36 B per ray plus a small table); the tally is the
+ * same up to float64 summation order.
  * Host arrays (on_device == 0) are copied to the device before the call
  * returns.  Rays with a non-finite field, E <= 0 or a zero direction score
  * nothing and are reported by the next vrc_sync / vrc_read_tally as

@@ -11,6 +11,7 @@
 
 #include "vrc.h"
 #include "vrc_internal.h"
+#include "vrc_sort.h"
 
 using namespace vrc;
 
@@ -119,6 +120,7 @@ struct vrc_ctx {
   DevBuf xsE, xsInvdE, xsS, xsHash;
   DevBuf stage;    // device copy of host rays
   DevBuf scratch;  // finalize staging
+  DevBuf sortKeys, sortTable, sortOffsets, sortTiles, sortRays;  // ray-sort scratch
 
   bool timing = false;
   std::vector<TimedSpan> pending;
@@ -155,6 +157,11 @@ struct vrc_ctx {
     xsHash.release();
     stage.release();
     scratch.release();
+    sortKeys.release();
+    sortTable.release();
+    sortOffsets.release();
+    sortTiles.release();
+    sortRays.release();
     if (stream) cudaStreamDestroy(stream);
   }
 };
@@ -168,6 +175,8 @@ int check_options(const vrc_options *o) {
     return fail(VRC_ERR_ARG, "options.block must be 0 or a multiple of 32 up to 256");
   if (o->blocks_per_sm < 0) return fail(VRC_ERR_ARG, "options.blocks_per_sm must be >= 0");
   if (o->sort < -1 || o->sort > 1) return fail(VRC_ERR_ARG, "options.sort must be -1, 0 or 1");
+  if (o->sort_len_buckets != -1 && (o->sort_len_buckets < 1 || o->sort_len_buckets > 256))
+    return fail(VRC_ERR_ARG, "options.sort_len_buckets must be -1 or 1..256");
   return VRC_OK;
 }
 
@@ -286,6 +295,55 @@ int sync_streams(vrc_ctx *c, void *stream) {
   return VRC_OK;
 }
 
+constexpr int64_t kAutoSortMin = 65536;
+
+// Sorts the batch into context scratch and points rp at the sorted copy.
+int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s) {
+  SortKeyArgs P;
+  std::memset(&P, 0, sizeof P);
+  for (int k = 0; k < 3; ++k) {
+    P.lo[k] = (float)c->org[k];
+    P.hi[k] = (float)(c->org[k] + c->n[k] * c->h[k]);
+    P.inv_h[k] = (float)(1.0 / c->h[k]);
+    P.n[k] = c->n[k];
+  }
+  P.n_groups = c->n_groups;
+  int nl = c->opt.sort_len_buckets > 0 ? c->opt.sort_len_buckets : 64;
+  while (nl > 1 && (int64_t)c->n_groups * nl + 1 > 16384) nl >>= 1;
+  P.n_len = nl;
+  const int max_cells = c->n[0] + c->n[1] + c->n[2] + 1;
+  P.len_width = std::max(1, (max_cells + nl - 1) / nl);
+  P.n_keys = c->n_groups * nl + 1;
+  SortPlan plan = make_sort_plan(rp.n, P.n_keys);
+  VRC_CUDA(c->sortKeys.ensure(plan.bytes_keys), "allocating sort scratch");
+  VRC_CUDA(c->sortTable.ensure(plan.bytes_table), "allocating sort scratch");
+  VRC_CUDA(c->sortOffsets.ensure(plan.bytes_table), "allocating sort scratch");
+  VRC_CUDA(c->sortTiles.ensure(plan.bytes_tiles), "allocating sort scratch");
+  VRC_CUDA(c->sortRays.ensure(plan.bytes_rays), "allocating sort scratch");
+  float *base = static_cast<float *>(c->sortRays.p);
+  RayOut out;
+  float **f[8] = {&out.x, &out.y, &out.z, &out.u, &out.v, &out.w, &out.E, &out.wt};
+  for (int k = 0; k < 8; ++k) *f[k] = base + (size_t)k * rp.n;
+  TimedSpan span{nullptr, nullptr, 1};
+  if (c->timing) {
+    VRC_CUDA(c->get_event(&span.start), "creating a timing event");
+    VRC_CUDA(c->get_event(&span.stop), "creating a timing event");
+    VRC_CUDA(cudaEventRecord(span.start, s), "recording a timing event");
+  }
+  VRC_CUDA(launch_sort(rp, P, c->edges.empty() ? nullptr : c->d_edges, plan,
+                       static_cast<uint32_t *>(c->sortKeys.p), static_cast<uint32_t *>(c->sortTable.p),
+                       static_cast<uint32_t *>(c->sortOffsets.p), static_cast<uint32_t *>(c->sortTiles.p),
+                       out, s),
+           "launching the ray sort");
+  if (c->timing) {
+    VRC_CUDA(cudaEventRecord(span.stop, s), "recording a timing event");
+    c->pending.push_back(span);
+  }
+  rp.x = out.x; rp.y = out.y; rp.z = out.z; rp.u = out.u;
+  rp.v = out.v; rp.w = out.w; rp.E = out.E; rp.wt = out.wt;
+  return VRC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -294,7 +352,7 @@ void vrc_default_options(vrc_options *opt) {
   if (!opt) return;
   opt->form = VRC_FORM_PLAIN;
   opt->sort = -1;
-  opt->sort_cell_bits = -1;
+  opt->sort_len_buckets = -1;
   opt->block = 0;
   opt->blocks_per_sm = 0;
   opt->device = -1;
@@ -453,6 +511,11 @@ int vrc_cast_rays(vrc_ctx *c, const vrc_rays *r, void *cuda_stream) {
   if (!r->on_device) {
     VRC_CUDA(c->get_event(&uploaded), "creating the upload event");
     VRC_CUDA(cudaEventRecord(uploaded, s), "recording the upload event");
+  }
+  const bool do_sort = c->opt.sort == 1 || (c->opt.sort == -1 && r->n >= kAutoSortMin);
+  if (do_sort) {
+    int rc = sort_rays(c, rp, s);
+    if (rc) return rc;
   }
   CastArgs a = make_args(c, rp);
   const int form = c->opt.form;

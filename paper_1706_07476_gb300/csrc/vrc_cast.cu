@@ -34,7 +34,7 @@ SmemLayout smem_layout(int form, const CastArgs &a, int block) {
 }
 
 template <int FORM>
-__global__ void __launch_bounds__(256) k_cast(CastArgs a, SmemLayout L) {
+__global__ void __launch_bounds__(256, 4) k_cast(CastArgs a, SmemLayout L) {
   typedef typename Attenuation<FORM>::inv_t inv_t;
   extern __shared__ __align__(16) unsigned char smem[];
   int32_t *hash_s = reinterpret_cast<int32_t *>(smem + L.hash);

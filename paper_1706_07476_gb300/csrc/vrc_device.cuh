@@ -148,7 +148,24 @@ __device__ __forceinline__ void xs_lookup(const XsDev &xs, const int32_t *hash_s
 }
 
 // ---------------------------------------------------------------------------
-// Eq. 4 along one ray, in the two precision forms.
+// float -> double without the FP64 pipe (GB300's FP64 rate is 1/64 of FP32):
+// a normal float's sign, exponent (rebiased by 1023 - 127 = 896) and
+// mantissa are moved into the double's fields with integer operations.
+// Zero maps to +0; subnormal inputs (rare: a score below 1.2e-38) take the
+// hardware conversion.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  if (e == 0u) return (b & 0x7fffffffu) ? (double)f : 0.0;
+  const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xfffffu);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 4 along one ray, in the two precision forms.  score() returns the
+// segment's contribution as a double; an exact +0 (the transmitted fraction
+// has underflowed) needs no tally update, since adding +0 changes no bit.
 // ---------------------------------------------------------------------------
 template <int FORM>
 struct Attenuation;
@@ -198,24 +215,22 @@ struct Attenuation<kFormFp32> {
     } else {
       path = l;
     }
-    return (double)(wt * T * path);
+    return f2d_bits(wt * T * path);
   }
 };
-
-// Crossing parameter of plane j on one axis: (org + j h - p) / d, evaluated
-// from scratch in double-float (never accumulated) as (D + j h) * inv_d with
-// D = org - p.
-__device__ __forceinline__ df plane_param(df D, df h, int j, df inv_d) {
-  return df_mul(df_add(D, df_mul_f(h, (float)j)), inv_d);
-}
 
 // Walks one ray through the mesh and adds its Eq. 4 score to every crossed
 // cell of `tal` (the ray's group slice).  The ray is the half-line p + s d,
 // s >= 0, with d not necessarily unit: crossing parameters are in units of
-// |d| and lengths are scaled by |d| at the end.  A start outside the box is
-// clipped to it (vacuum outside); the walk ends when the ray leaves the mesh
-// or after max_steps steps (then *overflow is set).  Returns the number of
-// positive-length segments scored.
+// |d| and lengths are scaled by |d| at the end.  The crossing parameter of
+// plane j on axis k, ((org_k - p_k) + j h_k) * (1/d_k), is re-evaluated in
+// double-float from the integer plane index at every step (never
+// accumulated).  The sum is formed before the product, so a start exactly
+// on a plane gives an exactly zero first segment, as in exact arithmetic.
+// A start
+// outside the box is clipped to it (vacuum outside); the walk ends when the
+// ray leaves the mesh or after max_steps steps (then *overflow is set).
+// Returns the number of positive-length segments scored.
 template <int FORM>
 __device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float py, float pz,
                                              float u, float v, float w, float wt, float dn,
@@ -225,20 +240,20 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float p
   const float p[3] = {px, py, pz};
   const float d[3] = {u, v, w};
   const df inf = {INFINITY, 0.f};
-  df D[3], inv_d[3];
+  df D[3], R[3];  // org - p and 1/d per axis
   df s_in = {0.f, 0.f}, s_out = inf;
   bool miss = false;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     D[k] = df_add_f(m.org[k], -p[k]);
-    df Dn = df_add(D[k], df_mul_f(m.h[k], (float)m.n[k]));
+    const df Dn = df_add(D[k], df_mul_f(m.h[k], (float)m.n[k]));
     if (d[k] == 0.f) {
-      inv_d[k] = {0.f, 0.f};
+      R[k] = {0.f, 0.f};
       if (df_pos(D[k]) || !df_pos(Dn)) miss = true;  // p < lo or p >= hi
     } else {
-      inv_d[k] = df_rcp(d[k]);
-      df a = df_mul(D[k], inv_d[k]);
-      df b = df_mul(Dn, inv_d[k]);
+      R[k] = df_rcp(d[k]);
+      df a = df_mul(D[k], R[k]);
+      df b = df_mul(Dn, R[k]);
       if (d[k] < 0.f) { df t = a; a = b; b = t; }
       if (df_lt(s_in, a)) s_in = a;
       if (df_lt(b, s_out)) s_out = b;
@@ -246,22 +261,20 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float p
   }
   if (miss || !df_lt(s_in, s_out)) return 0;
 
-  int i[3], j[3], stp[3];
+  int i[3], stp[3], off[3], cst[3];
   df S[3];
-  int64_t cell = 0;
+  int cell = 0;
+  const int cstride[3] = {1, m.n[0], m.n[0] * m.n[1]};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    df c = df_neg(D[k]);  // p - org
+    df c = df_add_f(df_neg(m.org[k]), p[k]);  // p - org
     if (s_in.hi > 0.f && d[k] != 0.f) c = df_add(c, df_mul_f(s_in, d[k]));
     i[k] = df_floor_clamp(df_mul(c, m.inv_h[k]), m.n[k]);
-    cell += (int64_t)i[k] * m.stride[k];
-    if (d[k] == 0.f) {
-      stp[k] = 0; j[k] = 0; S[k] = inf;
-    } else {
-      stp[k] = d[k] > 0.f ? 1 : -1;
-      j[k] = i[k] + (d[k] > 0.f ? 1 : 0);
-      S[k] = plane_param(D[k], m.h[k], j[k], inv_d[k]);
-    }
+    cell += i[k] * cstride[k];
+    stp[k] = d[k] > 0.f ? 1 : -1;
+    off[k] = d[k] > 0.f ? 1 : 0;
+    cst[k] = stp[k] * cstride[k];
+    S[k] = d[k] == 0.f ? inf : df_mul(df_add(D[k], df_mul_f(m.h[k], (float)(i[k] + off[k]))), R[k]);
   }
 
   Attenuation<FORM> att(wt);
@@ -271,20 +284,19 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float p
   const int max_steps = m.n[0] + m.n[1] + m.n[2] + 3;
   for (int step = 0;; ++step) {
     // axis of the nearest crossing (ties resolved x, then y, then z)
-    int k = df_lt(S[1], S[0]) ? 1 : 0;
-    df Sk = k ? S[1] : S[0];
-    if (df_lt(S[2], Sk)) { k = 2; Sk = S[2]; }
-    const int ik = (k == 0 ? i[0] : k == 1 ? i[1] : i[2]);
-    const int sk = (k == 0 ? stp[0] : k == 1 ? stp[1] : stp[2]);
-    const int nk = (k == 0 ? m.n[0] : k == 1 ? m.n[1] : m.n[2]);
-    const int inew = ik + sk;
-    const bool leaving = (unsigned)inew >= (unsigned)nk;
-    const int64_t ncell = cell + (int64_t)sk * (k == 0 ? m.stride[0] : k == 1 ? m.stride[1] : m.stride[2]);
+    const bool y_first = df_lt(S[1], S[0]);
+    df Sk = y_first ? S[1] : S[0];
+    const bool z_first = df_lt(S[2], Sk);
+    if (z_first) Sk = S[2];
+    const int k = z_first ? 2 : (y_first ? 1 : 0);
+    const int inew = (k == 0 ? i[0] : k == 1 ? i[1] : i[2]) + (k == 0 ? stp[0] : k == 1 ? stp[1] : stp[2]);
+    const bool leaving = (unsigned)inew >= (unsigned)(k == 0 ? m.n[0] : k == 1 ? m.n[1] : m.n[2]);
+    const int ncell = cell + (k == 0 ? cst[0] : k == 1 ? cst[1] : cst[2]);
     const unsigned nmat = leaving ? 0u : __ldg(m.mat + ncell);  // prefetch the next cell
 
-    float l = fmaxf(df_diff(Sk, s_cur), 0.f) * dn;
-    double s = att.score(sg[mat * stride], inv[mat * stride], l);
-    atomicAdd(tal + cell, s);
+    const float l = fmaxf(df_diff(Sk, s_cur), 0.f) * dn;
+    const double s = att.score(sg[mat * stride], inv[mat * stride], l);
+    if (s != 0.0) atomicAdd(tal + cell, s);
     nseg += l > 0.f;
 
     if (leaving) break;
@@ -292,15 +304,15 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float p
     s_cur = Sk;
     cell = ncell;
     mat = nmat;
-    // advance the stepped axis and recompute its next crossing from scratch
-    const int jn = (k == 0 ? j[0] : k == 1 ? j[1] : j[2]) + sk;
+    // next crossing on the stepped axis, from its integer plane index
     const df Dk = k == 0 ? D[0] : k == 1 ? D[1] : D[2];
     const df hk = k == 0 ? m.h[0] : k == 1 ? m.h[1] : m.h[2];
-    const df vk = k == 0 ? inv_d[0] : k == 1 ? inv_d[1] : inv_d[2];
-    const df Sn = plane_param(Dk, hk, jn, vk);
+    const df Rk = k == 0 ? R[0] : k == 1 ? R[1] : R[2];
+    const int ok = k == 0 ? off[0] : k == 1 ? off[1] : off[2];
+    const df Sn = df_mul(df_add(Dk, df_mul_f(hk, (float)(inew + ok))), Rk);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      if (a == k) { i[a] = inew; j[a] = jn; S[a] = Sn; }
+      if (a == k) { i[a] = inew; S[a] = Sn; }
     }
   }
   return nseg;

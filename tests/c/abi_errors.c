@@ -55,6 +55,12 @@ int main(void) {
   EXPECT(vrc_create_mesh(&d, &bad, &c) == VRC_ERR_ARG);
   bad = o; bad.block = 512;
   EXPECT(vrc_create_mesh(&d, &bad, &c) == VRC_ERR_ARG);
+  bad = o; bad.sort = 2;
+  EXPECT(vrc_create_mesh(&d, &bad, &c) == VRC_ERR_ARG);
+  bad = o; bad.sort_len_buckets = 0;
+  EXPECT(vrc_create_mesh(&d, &bad, &c) == VRC_ERR_ARG);
+  bad = o; bad.sort_len_buckets = 300;
+  EXPECT(vrc_create_mesh(&d, &bad, &c) == VRC_ERR_ARG);
 
   /* calls on a NULL context */
   double E[2] = {1.0, 2.0}, S[2] = {1.0, 1.0};

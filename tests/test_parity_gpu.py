@@ -266,3 +266,50 @@ def test_ray_starting_on_faces_and_parallel_to_planes(vrc, torch_cuda):
         got, rc, stats = run_gpu(vrc, torch_cuda, prob, form)
         assert rc == vrc.VRC_OK
         assert_parity(want, got, tol=1e-5)
+
+
+# ---------------------------------------------------------------- ray sort
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_sort_on_off_same_tally(vrc, torch_cuda, slab_small, form):
+    """Sorting by (group, crossed cells) changes only the float64 summation
+    order of the tally."""
+    prob, want, st = slab_small
+    a, rc_a, sa = run_gpu(vrc, torch_cuda, prob, FORMS[form],
+                          options=vrc.vrc_default_options(form=FORMS[form], sort=0))
+    b, rc_b, sb = run_gpu(vrc, torch_cuda, prob, FORMS[form],
+                          options=vrc.vrc_default_options(form=FORMS[form], sort=1,
+                                                          sort_len_buckets=17))
+    assert rc_a == rc_b == vrc.VRC_OK
+    assert sa["segments"] == sb["segments"] == st["segments"]
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-300)
+    assert_parity(want, b)
+
+
+def test_sort_with_rejected_and_out_of_group_rays(vrc, torch_cuda):
+    """Rejected rays and rays outside every group land in the last key and are
+    still reported; a ragged count that is not a multiple of the chunk."""
+    rng = np.random.default_rng(31)
+    mat = rng.integers(0, 3, size=(9, 7, 11)).astype(np.uint8)
+    mesh = W.Mesh(11, 7, 9, 0.5, -2.0, 1.0, 0.9, 1.7, 0.6, mat)
+    tables = [W.xs_table(rng, 200, 3), None, W.xs_table(rng, 150, 2)]
+    n = 20011
+    lo, hi = np.array(mesh.lo), np.array(mesh.hi)
+    pos = lo - 0.2 * (hi - lo) + 1.4 * (hi - lo) * rng.random((n, 3))
+    d = rng.normal(size=(n, 3))
+    rays = W.make_rays(*(pos[:, k].astype(np.float32) for k in range(3)),
+                       *(d[:, k].astype(np.float32) for k in range(3)),
+                       W.log_uniform(rng, n, 1e-6, 1e8), np.ones(n, np.float32))
+    bad = rng.choice(n, 50, replace=False)
+    rays["w"][bad[:25]] = np.nan
+    rays["E"][bad[25:]] = 0.0
+    edges = W.log_group_edges(5, 1e-4, 1e7)  # some energies fall outside
+    prob = W.Problem("sortmix", mesh, tables, edges, rays)
+    want, st = oracle.cast(prob)
+    for sort in (0, 1):
+        got, rc, stats = run_gpu(vrc, torch_cuda, prob, 1,
+                                 options=vrc.vrc_default_options(form=1, sort=sort))
+        assert rc == vrc.VRC_ERR_NONFINITE
+        assert stats["rejected"] == 50 and stats["rays"] == n
+        assert stats["segments"] == st["segments"]
+        assert_parity(want, got)
