@@ -151,6 +151,31 @@ int vrc_load_xs(vrc_ctx *c, int32_t material, const double *E_eV, const double *
  * table), VRC_ERR_OOM, VRC_ERR_CUDA. */
 int vrc_cast_rays(vrc_ctx *c, const vrc_rays *r, void *cuda_stream);
 
+/* Sorts a device batch of rays the way vrc_cast_rays does before its cast
+ * (by energy group, then by the number of cells crossed) without allocating
+ * any memory.  The paper has no counterpart: it is for callers that may not
+ * call cudaMalloc once their run has started, e.g. a transport code that
+ * gives all free device memory to its own pool at start-up, or one whose
+ * batch loop must not pay the device-wide synchronisation of cudaMalloc /
+ * cudaFree while the CPU random walk keeps running.  Cast the result with
+ * sorting off (options.sort = 0) to get vrc_cast_rays' sorted cast.
+ *  - in: device rays (on_device != 0), at most 262,144 per call; larger
+ *    batches are rejected with VRC_ERR_ARG (split them).
+ *  - out: caller-owned device array of 8*n floats receiving the sorted rays
+ *    as x, y, z, u, v, w, E, wt blocks of n each.
+ *  - the key uses the context's mesh box, groups and sort_len_buckets.
+ *  - scratch: one fixed device array of about 5 MiB inside libvrc, held by
+ *    every GPU that loads the library until exit and shared by every call;
+ *    each call writes all of it that it reads, so nothing needs clearing.
+ *    Calls that overlap on the GPU (other streams, other threads, other
+ *    contexts on the same device) race on it: serialise them.
+ *  - the first call on each device looks up the scratch's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - asynchronous on cuda_stream (NULL = the context's stream).
+ * Errors: VRC_ERR_ARG (NULL pointers, host rays, too many rays or keys),
+ * VRC_ERR_CUDA. */
+int vrc_sort_rays_static(vrc_ctx *c, const vrc_rays *in, float *out, void *cuda_stream);
+
 /* Waits for the stream and reports the device status accumulated since the
  * last reset: VRC_ERR_NONFINITE or VRC_ERR_TRAVERSAL if any ray hit that
  * case (the tally still holds every other ray's scores), else VRC_OK.

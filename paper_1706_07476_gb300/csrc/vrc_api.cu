@@ -656,6 +656,35 @@ int vrc_get_timing(vrc_ctx *c, void *cuda_stream, double *cast_ms, double *sort_
 
 int64_t vrc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+}  // extern "C"
+
+// Internal accessors for vrc_static.cu (the no-allocation sort).
+int vrc::set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+int vrc::ctx_sort_args(const vrc_ctx *c, SortKeyArgs *P, const double **edges, int *device,
+                       cudaStream_t *stream) {
+  std::memset(P, 0, sizeof *P);
+  for (int k = 0; k < 3; ++k) {
+    P->lo[k] = (float)c->org[k];
+    P->hi[k] = (float)(c->org[k] + c->n[k] * c->h[k]);
+    P->inv_h[k] = (float)(1.0 / c->h[k]);
+    P->n[k] = c->n[k];
+  }
+  P->n_groups = c->n_groups;
+  int nl = c->opt.sort_len_buckets > 0 ? c->opt.sort_len_buckets : 64;
+  while (nl > 1 && (int64_t)c->n_groups * nl + 1 > 16384) nl >>= 1;
+  P->n_len = nl;
+  const int max_cells = c->n[0] + c->n[1] + c->n[2] + 1;
+  P->len_width = std::max(1, (max_cells + nl - 1) / nl);
+  P->n_keys = c->n_groups * nl + 1;
+  *edges = c->edges.empty() ? nullptr : c->d_edges;
+  *device = c->device;
+  *stream = c->stream;
+  return VRC_OK;
+}
+
+extern "C" {
+
 int vrc_device_count(void) {
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess) return 0;

@@ -7,6 +7,8 @@
 
 #include "vrc_internal.h"
 
+struct vrc_ctx;
+
 namespace vrc {
 
 struct SortKeyArgs {
@@ -37,5 +39,12 @@ SortPlan make_sort_plan(int64_t n, int n_keys);
 cudaError_t launch_sort(const RayPtrs &in, SortKeyArgs P, const double *edges, const SortPlan &plan,
                         uint32_t *keys, uint32_t *table, uint32_t *offsets, uint32_t *tiles,
                         const RayOut &out, cudaStream_t s);
+
+// Sort-key arguments, group edges (device), device and stream of a context.
+int ctx_sort_args(const vrc_ctx *c, SortKeyArgs *P, const double **edges, int *device,
+                  cudaStream_t *stream);
+
+// Records a message for vrc_last_error() and returns code.
+int set_last_error(int code, const char *msg);
 
 }  // namespace vrc

@@ -83,6 +83,7 @@ def _load():
         "vrc_enable_timing": ([P, I32], C.c_int),
         "vrc_get_timing": ([P, P, P, P, P, I32], C.c_int),
         "vrc_launch_count": ([], C.c_int64),
+        "vrc_sort_rays_static": ([P, P, P, P], C.c_int),
         "vrc_version": ([], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -228,6 +229,14 @@ def vrc_cast_rays(ctx: Context, rays: dict, stream=None):
     r, keep = _ray_struct(rays)
     _check(_lib.vrc_cast_rays(ctx.handle, C.byref(r), _stream_handle(stream)))
     ctx._keep = keep  # device arrays stay referenced until the next cast
+
+
+def vrc_sort_rays_static(ctx: Context, rays: dict, out, stream=None):
+    """No-allocation ray sort: device rays in; `out` is a caller-owned device
+    float32 tensor of 8*n elements receiving x, y, z, u, v, w, E, wt blocks."""
+    r, keep = _ray_struct(rays)
+    ptr = None if out is None else out.data_ptr()
+    _check(_lib.vrc_sort_rays_static(ctx.handle, C.byref(r), ptr, _stream_handle(stream)))
 
 
 def vrc_sync(ctx: Context, stream=None):
