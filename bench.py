@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--sort", type=int, default=-1, help="ray sorting: -1 auto, 0 off, 1 on")
     ap.add_argument("--n-rays", type=int, default=1 << 24)
     ap.add_argument("--mesh", type=int, default=256)
+    ap.add_argument("--workload", choices=["slab256", "batched"], default="slab256")
+    ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity-sample", action="store_true")
     ap.add_argument("--no-micro", action="store_true")
@@ -221,6 +223,89 @@ def run_reference(args, rank, world):
     return 0
 
 
+# --------------------------------------------------------------------------- batched form
+
+BATCHED = ("batched1024: 1,024 independent problems, cubic meshes of 1 cm cells with side "
+           "log-uniform in 16-128, 2-8 materials each from the 1,000-point table generator, "
+           "uniform-random layout, ray counts log-uniform in 1e3-1e6 (1.4e8 rays), one group, "
+           "seed 3; one persistent graph-captured launch per step")
+
+
+def run_batched(args, rank, world, local):
+    """The batched form: every step is one launch of the batch plan (all
+    problems), timed with CUDA events; the plan's options come from the
+    project's autotuner (sweep outside the timed region, cached per GPU)."""
+    import torch
+    from paper_1706_07476_gb300 import autotune, vrc
+    torch.cuda.set_device(local)
+    form = vrc.VRC_FORM_FP32 if args.forms.split(",")[-1].strip() == "fp32" else vrc.VRC_FORM_PLAIN
+    probs = W.batched_problems(seed=3)
+    ctxs = [vrc.context_for(p, vrc.vrc_default_options(form=form, device=local)) for p in probs]
+    rays = [{k: torch.from_numpy(p.rays[k]).cuda() for k in W.RAY_FIELDS} for p in probs]
+    best, tuned_ms, table = autotune.tune_batched(torch, probs, ctxs, rays, form,
+                                                  use_cache=not args.retune)
+    batch = vrc.vrc_batch_create(ctxs, rays, vrc.vrc_default_batch_options(**best))
+    stream = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        vrc.vrc_batch_launch(batch, stream=stream)
+    stream.synchronize()
+    for c in ctxs:
+        vrc.vrc_reset_tally(c)
+        vrc.vrc_sync(c)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.__enter__()
+    l0 = vrc.vrc_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        vrc.vrc_batch_launch(batch, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    launches = vrc.vrc_launch_count() - l0
+    sampler.__exit__(None, None, None)
+    elapsed = e0.elapsed_time(e1) / 1e3
+    seg = 0
+    for c in ctxs:
+        rc, st = vrc.vrc_sync(c)
+        assert rc == vrc.VRC_OK and st["overflow"] == 0, (rc, st)
+        seg += st["segments"]
+    n_rays = sum(p.n_rays for p in probs)
+    value = seg / elapsed
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    alg = (seg / args.steps * BYTES_PER_SEGMENT + n_rays * BYTES_PER_RAY) / (elapsed / args.steps) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if form else "f64",
+        "data": "synthetic",
+        "config": {"workload": BATCHED, "rays_per_step": n_rays,
+                   "segments_per_step": seg / args.steps, "form": "fp32" if form else "plain",
+                   "autotuned_options": best, "tuned_ms": tuned_ms,
+                   "l2": "inputs larger than L2 (4.5 GB rays, 2.6 GB tallies); no flush"},
+        "roofline": {"bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
+                     "frac": alg / hbm, "traffic": None,
+                     "peak_source": f"{src} hbm_gbs", "kernel": "whole step (sort + k_cast_batched)"},
+        "clocks": sampler.summary(), "gpu_launches": launches,
+        "autotune_sweep": [{"options": o, "ms": ms} for o, ms in table],
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        idx = np.linspace(0, len(probs) - 1, 64).astype(int)
+        t0 = time.perf_counter()
+        segs = sum(oracle.cast(probs[i])[1]["segments"] for i in idx)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": segs / dt, "unit": UNIT, "cores": oracle.hardware_threads(),
+                                "kind": "oracle",
+                                "sample": f"64 of the 1,024 problems, evenly spaced ({segs} segments, {dt:.1f} s)"}
+    batch.close()
+    for c in ctxs:
+        c.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -228,6 +313,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batched":
+        return run_batched(args, rank, world, local)
 
     import torch
     import torch.distributed as dist

@@ -207,6 +207,51 @@ void vrc_destroy(vrc_ctx *c);
 /* Thread-local description of the last error ("" if none). */
 const char *vrc_last_error(void);
 
+/* ---- batched form ------------------------------------------------------
+ * Many independent tally problems (each a context with its own mesh, cross
+ * sections and tally, and its own device ray batch) cast by ONE persistent
+ * kernel that takes chunks of rays ("work items") from a device counter, the
+ * whole launch sequence captured once in a CUDA graph.  This generalises the
+ * paper's one-problem GPU step (Sec. 3) to serving many problems at once; the
+ * per-ray arithmetic is that of vrc_cast_rays (Eq. 4). */
+typedef struct vrc_batch vrc_batch;
+
+typedef struct {
+  int32_t block;            /* threads per block: 0 auto (256), else 32..256 step 32 */
+  int32_t blocks_per_sm;    /* resident blocks per SM: 0 auto (occupancy) */
+  int32_t chunk;            /* rays per work item: 0 auto (2048), else 64..65536 */
+  int32_t sort_len_buckets; /* 0: no sort; 1..256: sort each problem's rays by (group,
+                               crossed cells) into this many buckets first; -1 auto (16) */
+  int32_t use_graph;        /* 1 (default): capture the sequence in a CUDA graph once */
+} vrc_batch_options;
+
+void vrc_default_batch_options(vrc_batch_options *opt);
+
+/* Builds a batch plan over n_problems contexts.  rays[p] is problem p's
+ * DEVICE ray batch (on_device != 0); the arrays must stay valid and
+ * unchanged in size for the plan's lifetime (their contents may change
+ * between launches).  All contexts must live on one device and use the same
+ * precision form.  Uploads any pending cross sections, allocates the plan's
+ * device state (work list, problem table, optional sort scratch of 36 B per
+ * ray) and, with use_graph, captures the sequence.
+ * Errors: VRC_ERR_ARG (NULL, host rays, mixed devices or forms, more than
+ * 2^31 work items or 2^32 rays), VRC_ERR_STATE (missing cross sections),
+ * VRC_ERR_OOM, VRC_ERR_CUDA. */
+int vrc_batch_create(vrc_ctx *const *ctxs, const vrc_rays *rays, int32_t n_problems,
+                     const vrc_batch_options *opt, vrc_batch **out);
+
+/* Casts every problem's rays into its own context's tally: one graph launch
+ * (or the plain launch sequence) on cuda_stream (NULL = the first context's
+ * stream).  Asynchronous; use vrc_sync / vrc_read_tally on each context. */
+int vrc_batch_launch(vrc_batch *b, void *cuda_stream);
+
+/* Frees the plan (waits for its launches); NULL is a no-op. */
+void vrc_batch_destroy(vrc_batch *b);
+
+/* One-shot: create a plan with default options, launch it, wait, destroy. */
+int vrc_cast_batched(vrc_ctx *const *ctxs, const vrc_rays *rays, int32_t n_problems,
+                     void *cuda_stream);
+
 /* Kernel timing.  When enabled, every cast records CUDA events on the
  * launching stream around its kernels; vrc_get_timing waits for the stream
  * and returns the summed device time (ms) of the cast kernels and of the ray

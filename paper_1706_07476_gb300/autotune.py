@@ -1,0 +1,149 @@
+"""Launch-shape autotuner for the cast and the batched form.
+
+Sweeps the options that set the launch shape (threads per block, rays per
+work item, sort granularity), times each candidate with CUDA events on the
+launching stream, and caches the best choice per GPU name and configuration
+class in a JSON file (``$VRC_AUTOTUNE_CACHE``, default
+``~/.cache/vrc_autotune.json``).  The sweep is a coordinate descent: one
+option at a time, holding the best values found so far.
+
+Tuning only changes how the same work is scheduled: every candidate casts
+every ray and produces the same tally up to float64 summation order.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+from paper_1706_07476_gb300 import vrc
+
+CACHE = os.environ.get("VRC_AUTOTUNE_CACHE",
+                       os.path.join(os.path.expanduser("~"), ".cache", "vrc_autotune.json"))
+
+BATCH_SPACE = {
+    "sort_len_buckets": [0, 8, 16, 32],
+    "chunk": [1024, 2048, 4096, 8192],
+    "block": [128, 256],
+}
+CAST_SPACE = {
+    "sort_len_buckets": [8, 32, 64, 128],
+    "block": [128, 256],
+}
+
+
+def _gpu_name(torch) -> str:
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def _load_cache():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key, value):
+    data = _load_cache()
+    data[key] = value
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    tmp = CACHE + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, CACHE)
+
+
+def _pow2_bucket(x: float) -> int:
+    return int(round(math.log2(max(x, 1.0))))
+
+
+def batched_class(problems, form: int) -> str:
+    n = len(problems)
+    rays = sum(p.n_rays for p in problems)
+    side = sum(p.mesh.nx + p.mesh.ny + p.mesh.nz for p in problems) / max(n, 1) / 3
+    return f"batched|form{form}|p{_pow2_bucket(n)}|r{_pow2_bucket(rays)}|s{_pow2_bucket(side)}"
+
+
+def cast_class(problem, form: int) -> str:
+    m = problem.mesh
+    return (f"cast|form{form}|c{_pow2_bucket(m.ncells)}|g{problem.n_groups}|"
+            f"r{_pow2_bucket(problem.n_rays)}")
+
+
+def _time_events(torch, fn, stream, reps):
+    fn()  # warm-up
+    stream.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    return best
+
+
+def _descend(space, default, measure):
+    best = dict(default)
+    table = []
+    best_ms = measure(best)
+    table.append((dict(best), best_ms))
+    for key, values in space.items():
+        for v in values:
+            if v == best.get(key):
+                continue
+            cand = dict(best)
+            cand[key] = v
+            ms = measure(cand)
+            table.append((dict(cand), ms))
+            if ms < best_ms:
+                best, best_ms = cand, ms
+    return best, best_ms, table
+
+
+def tune_batched(torch, problems, ctxs, rays_list, form: int, reps: int = 2, use_cache=True):
+    """Best vrc_batch_options fields for this batch (dict), ms, and the sweep table."""
+    key = f"{_gpu_name(torch)}|{batched_class(problems, form)}"
+    if use_cache:
+        hit = _load_cache().get(key)
+        if hit:
+            return hit["options"], hit["ms"], []
+    stream = torch.cuda.Stream()
+
+    def measure(opts):
+        o = vrc.vrc_default_batch_options(**opts)
+        batch = vrc.vrc_batch_create(ctxs, rays_list, o)
+        try:
+            return _time_events(torch, lambda: vrc.vrc_batch_launch(batch, stream=stream), stream, reps)
+        finally:
+            stream.synchronize()
+            batch.close()
+
+    best, ms, table = _descend(BATCH_SPACE, {"sort_len_buckets": 16, "chunk": 2048, "block": 256},
+                               measure)
+    _store(key, {"options": best, "ms": ms, "when": time.time()})
+    return best, ms, table
+
+
+def tune_cast(torch, problem, ctx, dev_rays, form: int, reps: int = 2, use_cache=True):
+    """Best vrc_options fields (sort buckets, block) for one problem's casts."""
+    key = f"{_gpu_name(torch)}|{cast_class(problem, form)}"
+    if use_cache:
+        hit = _load_cache().get(key)
+        if hit:
+            return hit["options"], hit["ms"], []
+    stream = torch.cuda.Stream()
+
+    def measure(opts):
+        o = vrc.vrc_default_options(form=form, sort=1, **opts)
+        vrc.vrc_set_options(ctx, o)
+        return _time_events(torch, lambda: vrc.vrc_cast_rays(ctx, dev_rays, stream=stream), stream, reps)
+
+    best, ms, table = _descend(CAST_SPACE, {"sort_len_buckets": 64, "block": 256}, measure)
+    vrc.vrc_set_options(ctx, vrc.vrc_default_options(form=form, sort=1, **best))
+    _store(key, {"options": best, "ms": ms, "when": time.time()})
+    return best, ms, table

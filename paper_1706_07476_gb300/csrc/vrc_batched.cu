@@ -1,0 +1,105 @@
+// Batched form: many independent tally problems (each its own mesh, cross
+// sections, rays and tally) cast by one persistent kernel.  Work items are
+// chunks of one problem's rays; every block takes the next item from a
+// global counter until the list is exhausted.  The per-ray code is the same
+// cast_one as the single-problem kernel (Sec. 3: lookup, cast, Eq. 4 score).
+#include <algorithm>
+
+#include "vrc_device.cuh"
+
+namespace vrc {
+
+namespace {
+
+inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+
+struct BatchSmem {
+  size_t hash, edges, sig, inv, total;
+};
+
+BatchSmem batch_smem(int form, const BatchShape &sh, int block) {
+  BatchSmem L;
+  size_t off = 0;
+  L.hash = off;
+  off = align16(off + sizeof(int32_t) * ((size_t)sh.max_hash + 1));
+  L.edges = off;
+  off = align16(off + sizeof(double) * ((size_t)sh.max_groups + 1));
+  L.sig = off;
+  off = align16(off + sizeof(float) * (size_t)sh.max_mat * block);
+  L.inv = off;
+  off = align16(off + (form == kFormPlain ? sizeof(double) : sizeof(float)) * (size_t)sh.max_mat * block);
+  L.total = off;
+  return L;
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(256, 4)
+    k_cast_batched(const CastArgs *__restrict__ probs, const BatchItem *__restrict__ items, int n_items,
+                   unsigned int *queue, BatchSmem L) {
+  typedef typename Attenuation<FORM>::inv_t inv_t;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CastArgs A;
+  __shared__ int s_item;
+  int32_t *hash_s = reinterpret_cast<int32_t *>(smem + L.hash);
+  double *edges_s = reinterpret_cast<double *>(smem + L.edges);
+  float *sig_s = reinterpret_cast<float *>(smem + L.sig) + threadIdx.x;
+  inv_t *inv_s = reinterpret_cast<inv_t *>(smem + L.inv) + threadIdx.x;
+  const int stride = blockDim.x;
+  int cur = -1;
+  // Each pass takes one item index; indices only grow, so at most n_items passes.
+  for (int pass = 0; pass < n_items; ++pass) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const BatchItem item = items[it];
+    if (item.problem != cur) {  // block-uniform
+      if (threadIdx.x == 0) A = probs[item.problem];
+      __syncthreads();
+      if (A.xs.n_union > 0)
+        for (int t = threadIdx.x; t <= A.xs.n_hash; t += blockDim.x) hash_s[t] = A.xs.hash[t];
+      if (A.edges)
+        for (int t = threadIdx.x; t <= A.n_groups; t += blockDim.x) edges_s[t] = A.edges[t];
+      __syncthreads();
+      cur = item.problem;
+    }
+    const double *edges = A.edges ? edges_s : nullptr;
+    RayCounts cnt;
+    const int64_t end = item.start + item.count;
+    for (int64_t r = item.start + threadIdx.x; r < end; r += blockDim.x)
+      cast_one<FORM>(A, r, hash_s, edges, sig_s, inv_s, stride, cnt);
+    flush_counts(cnt, A.counters, A.status);
+    __syncthreads();  // s_item, A and the staged tables are reused next pass
+  }
+}
+
+}  // namespace
+
+size_t batched_smem_bytes(int form, const BatchShape &sh, int block) {
+  return batch_smem(form, sh, block).total;
+}
+
+cudaError_t batched_occupancy(int form, const BatchShape &sh, int block, int *blocks_per_sm) {
+  const size_t smem = batched_smem_bytes(form, sh, block);
+  cudaError_t e;
+  if (form == kFormPlain) {
+    if ((e = cudaFuncSetAttribute(k_cast_batched<kFormPlain>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_cast_batched<kFormPlain>, block, smem);
+  }
+  if ((e = cudaFuncSetAttribute(k_cast_batched<kFormFp32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_cast_batched<kFormFp32>, block, smem);
+}
+
+cudaError_t launch_batched_cast(int form, const CastArgs *probs, const BatchItem *items, int n_items,
+                                unsigned int *queue, const BatchShape &sh, int grid, int block,
+                                cudaStream_t s) {
+  const BatchSmem L = batch_smem(form, sh, block);
+  if (form == kFormPlain)
+    k_cast_batched<kFormPlain><<<grid, block, L.total, s>>>(probs, items, n_items, queue, L);
+  else
+    k_cast_batched<kFormFp32><<<grid, block, L.total, s>>>(probs, items, n_items, queue, L);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace vrc

@@ -50,47 +50,11 @@ __global__ void __launch_bounds__(256, 4) k_cast(CastArgs a, SmemLayout L) {
   const double *edges = a.edges ? edges_s : nullptr;
   const int stride = blockDim.x;
 
-  uint32_t nseg = 0, nrays = 0, nrej = 0, novf = 0;
-  const RayPtrs &R = a.rays;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R.n;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    const float x = __ldg(R.x + r), y = __ldg(R.y + r), z = __ldg(R.z + r);
-    const float u = __ldg(R.u + r), v = __ldg(R.v + r), w = __ldg(R.w + r);
-    const float E = __ldg(R.E + r), wt = __ldg(R.wt + r);
-    ++nrays;
-    const float dn = sqrtf(u * u + v * v + w * w);
-    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(u) && isfinite(v) &&
-          isfinite(w) && isfinite(E) && isfinite(wt) && E > 0.f && dn > 0.f && isfinite(dn))) {
-      ++nrej;
-      continue;
-    }
-    const int g = group_of(edges, a.n_groups, (double)E);
-    if (g < 0) continue;
-    xs_lookup<inv_t>(a.xs, hash_s, E, sig_s, inv_s, stride);
-    bool ovf = false;
-    nseg += cast_ray<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, a.tally + (int64_t)g * a.mesh.ncells,
-                           sig_s, inv_s, stride, &ovf);
-    novf += ovf;
-  }
-  // one atomic per warp for each counter
-  for (int o = 16; o > 0; o >>= 1) {
-    nseg += __shfl_down_sync(0xffffffffu, nseg, o);
-    nrays += __shfl_down_sync(0xffffffffu, nrays, o);
-    nrej += __shfl_down_sync(0xffffffffu, nrej, o);
-    novf += __shfl_down_sync(0xffffffffu, novf, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (nseg) atomicAdd(a.counters + kCntSegments, (unsigned long long)nseg);
-    if (nrays) atomicAdd(a.counters + kCntRays, (unsigned long long)nrays);
-    if (nrej) {
-      atomicAdd(a.counters + kCntRejected, (unsigned long long)nrej);
-      atomicOr(a.status, kStatusNonfinite);
-    }
-    if (novf) {
-      atomicAdd(a.counters + kCntOverflow, (unsigned long long)novf);
-      atomicOr(a.status, kStatusTraversal);
-    }
-  }
+  RayCounts cnt;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.rays.n;
+       r += (int64_t)gridDim.x * blockDim.x)
+    cast_one<FORM>(a, r, hash_s, edges, sig_s, inv_s, stride, cnt);
+  flush_counts(cnt, a.counters, a.status);
 }
 
 __global__ void k_scale_copy(const double *__restrict__ src, double *__restrict__ dst, int64_t n,

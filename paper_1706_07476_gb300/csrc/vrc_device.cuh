@@ -318,4 +318,58 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float p
   return nseg;
 }
 
+// Per-thread counters of one cast, flushed with one atomic per warp.
+struct RayCounts {
+  uint32_t seg = 0, rays = 0, rej = 0, ovf = 0;
+};
+
+// One ray of a cast: validation, group, cross sections, walk and score.
+template <int FORM>
+__device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int32_t *hash_s,
+                                         const double *edges, float *sig_s,
+                                         typename Attenuation<FORM>::inv_t *inv_s, int stride,
+                                         RayCounts &c) {
+  const RayPtrs &R = a.rays;
+  const float x = __ldg(R.x + r), y = __ldg(R.y + r), z = __ldg(R.z + r);
+  const float u = __ldg(R.u + r), v = __ldg(R.v + r), w = __ldg(R.w + r);
+  const float E = __ldg(R.E + r), wt = __ldg(R.wt + r);
+  ++c.rays;
+  const float dn = sqrtf(u * u + v * v + w * w);
+  if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(u) && isfinite(v) && isfinite(w) &&
+        isfinite(E) && isfinite(wt) && E > 0.f && dn > 0.f && isfinite(dn))) {
+    ++c.rej;
+    return;
+  }
+  const int g = group_of(edges, a.n_groups, (double)E);
+  if (g < 0) return;
+  xs_lookup(a.xs, hash_s, E, sig_s, inv_s, stride);
+  bool ovf = false;
+  c.seg += cast_ray<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, a.tally + (int64_t)g * a.mesh.ncells,
+                          sig_s, inv_s, stride, &ovf);
+  c.ovf += ovf;
+}
+
+// Adds a warp's counters to the device counters (all 32 lanes must call).
+__device__ __forceinline__ void flush_counts(RayCounts c, unsigned long long *counters,
+                                             unsigned int *status) {
+  for (int o = 16; o > 0; o >>= 1) {
+    c.seg += __shfl_down_sync(0xffffffffu, c.seg, o);
+    c.rays += __shfl_down_sync(0xffffffffu, c.rays, o);
+    c.rej += __shfl_down_sync(0xffffffffu, c.rej, o);
+    c.ovf += __shfl_down_sync(0xffffffffu, c.ovf, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (c.seg) atomicAdd(counters + kCntSegments, (unsigned long long)c.seg);
+    if (c.rays) atomicAdd(counters + kCntRays, (unsigned long long)c.rays);
+    if (c.rej) {
+      atomicAdd(counters + kCntRejected, (unsigned long long)c.rej);
+      atomicOr(status, kStatusNonfinite);
+    }
+    if (c.ovf) {
+      atomicAdd(counters + kCntOverflow, (unsigned long long)c.ovf);
+      atomicOr(status, kStatusTraversal);
+    }
+  }
+}
+
 }  // namespace vrc

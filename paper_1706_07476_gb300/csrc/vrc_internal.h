@@ -63,6 +63,24 @@ struct CastArgs {
   unsigned int *status;
 };
 
+// Batched form (vrc_batched.cu): a work item is a chunk of one problem's rays.
+struct BatchItem {
+  int32_t problem;
+  int32_t count;
+  int64_t start;
+};
+
+// Largest per-problem table sizes in a batch (shared memory is sized by them).
+struct BatchShape {
+  int32_t max_hash, max_groups, max_mat;
+};
+
+size_t batched_smem_bytes(int form, const BatchShape &sh, int block);
+cudaError_t batched_occupancy(int form, const BatchShape &sh, int block, int *blocks_per_sm);
+cudaError_t launch_batched_cast(int form, const CastArgs *probs, const BatchItem *items, int n_items,
+                                unsigned int *queue, const BatchShape &sh, int grid, int block,
+                                cudaStream_t s);
+
 // Process-wide count of kernels launched by libvrc (vrc_launch_count).
 void note_launches(int n);
 

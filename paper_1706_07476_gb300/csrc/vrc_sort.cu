@@ -202,6 +202,59 @@ __global__ void __launch_bounds__(kSortBlock) k_sort_scatter(RayPtrs R, SortKeyA
   }
 }
 
+// ---- batched form -----------------------------------------------------------
+__global__ void __launch_bounds__(kSortBlock) k_bsort_count(const BSortProblem *__restrict__ probs,
+                                                            const int32_t *__restrict__ chunk_problem,
+                                                            int chunk, uint32_t *keys, uint32_t *table) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *hist = reinterpret_cast<uint32_t *>(smem);
+  const int p = chunk_problem[blockIdx.x];
+  const BSortProblem &B = probs[p];
+  const SortKeyArgs P = B.P;
+  const int c = blockIdx.x - B.first_chunk;
+  for (int t = threadIdx.x; t < P.n_keys; t += blockDim.x) hist[t] = 0;
+  __syncthreads();
+  const int64_t begin = (int64_t)c * chunk;
+  const int64_t end = min(begin + chunk, B.src.n);
+  for (int64_t r = begin + threadIdx.x; r < end; r += blockDim.x) {
+    uint32_t k = ray_key(P, B.edges, B.src, r);
+    keys[B.ray_base + r] = k;
+    atomicAdd(&hist[k], 1u);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < P.n_keys; t += blockDim.x)
+    table[B.table_base + (int64_t)t * B.n_chunks + c] = hist[t];
+}
+
+__global__ void __launch_bounds__(kSortBlock) k_bsort_scatter(const BSortProblem *__restrict__ probs,
+                                                              const int32_t *__restrict__ chunk_problem,
+                                                              int chunk, const uint32_t *keys,
+                                                              const uint32_t *offsets, RayOut O) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *cursor = reinterpret_cast<uint32_t *>(smem);
+  const int p = chunk_problem[blockIdx.x];
+  const BSortProblem &B = probs[p];
+  const int n_keys = B.P.n_keys;
+  const int c = blockIdx.x - B.first_chunk;
+  for (int t = threadIdx.x; t < n_keys; t += blockDim.x)
+    cursor[t] = offsets[B.table_base + (int64_t)t * B.n_chunks + c];
+  __syncthreads();
+  const int64_t begin = (int64_t)c * chunk;
+  const int64_t end = min(begin + chunk, B.src.n);
+  const RayPtrs R = B.src;
+  for (int64_t r = begin + threadIdx.x; r < end; r += blockDim.x) {
+    const uint32_t pos = atomicAdd(&cursor[keys[B.ray_base + r]], 1u);
+    O.x[pos] = __ldg(R.x + r);
+    O.y[pos] = __ldg(R.y + r);
+    O.z[pos] = __ldg(R.z + r);
+    O.u[pos] = __ldg(R.u + r);
+    O.v[pos] = __ldg(R.v + r);
+    O.w[pos] = __ldg(R.w + r);
+    O.E[pos] = __ldg(R.E + r);
+    O.wt[pos] = __ldg(R.wt + r);
+  }
+}
+
 size_t count_smem(const SortKeyArgs &P) {
   return (size_t)P.edges_off + sizeof(double) * (size_t)(P.n_groups + 1);
 }
@@ -240,5 +293,29 @@ cudaError_t launch_sort(const RayPtrs &in, SortKeyArgs P, const double *edges, c
   note_launches(5);
   return cudaGetLastError();
 }
+
+cudaError_t prepare_batched_sort(const BSortPlan &plan) {
+  const int smem = (int)(sizeof(uint32_t) * (size_t)plan.max_keys);
+  cudaError_t e = cudaFuncSetAttribute(k_bsort_count, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_bsort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_batched_sort(const BSortProblem *probs_dev, const int32_t *chunk_problem_dev,
+                                const BSortPlan &plan, uint32_t *keys, uint32_t *table,
+                                uint32_t *offsets, uint32_t *tiles, const RayOut &out,
+                                cudaStream_t s) {
+  if (plan.n_chunks == 0) return cudaSuccess;
+  const size_t smem = sizeof(uint32_t) * (size_t)plan.max_keys;
+  k_bsort_count<<<plan.n_chunks, kSortBlock, smem, s>>>(probs_dev, chunk_problem_dev, plan.chunk, keys, table);
+  k_scan_tiles<<<plan.n_tiles, kScanBlock, 0, s>>>(table, plan.table_len, tiles);
+  k_scan_sums<<<1, kScanBlock, 0, s>>>(tiles, plan.n_tiles);
+  k_scan_apply<<<plan.n_tiles, kScanBlock, 0, s>>>(table, plan.table_len, tiles, offsets);
+  k_bsort_scatter<<<plan.n_chunks, kSortBlock, smem, s>>>(probs_dev, chunk_problem_dev, plan.chunk, keys, offsets, out);
+  note_launches(5);
+  return cudaGetLastError();
+}
+
+int scan_tile_elems() { return kScanTile; }
 
 }  // namespace vrc

@@ -40,6 +40,35 @@ cudaError_t launch_sort(const RayPtrs &in, SortKeyArgs P, const double *edges, c
                         uint32_t *keys, uint32_t *table, uint32_t *offsets, uint32_t *tiles,
                         const RayOut &out, cudaStream_t s);
 
+// ---- batched form: many problems sorted in one pass -------------------------
+// Problem p's rays (its own arrays) are sorted by p's key into the
+// concatenated output at [ray_base, ray_base + n); the (key, chunk) count
+// table holds every problem's block at table_base.
+struct BSortProblem {
+  SortKeyArgs P;        // key arguments of the problem (chunk field unused)
+  const double *edges;  // device group edges or nullptr
+  RayPtrs src;          // the problem's rays
+  int64_t ray_base;     // first slot in the concatenated output
+  int64_t table_base;   // first entry of the problem's (key, chunk) block
+  int32_t n_chunks;     // chunks of this problem
+  int32_t first_chunk;  // global index of its first chunk
+};
+
+struct BSortPlan {
+  int chunk = 8192;
+  int n_chunks = 0, n_tiles = 0, max_keys = 0;
+  int64_t table_len = 0, total_rays = 0;
+};
+
+// Launches count / scan / scatter over every problem (5 kernels).
+// chunk_problem[c] is the problem of global chunk c.
+cudaError_t launch_batched_sort(const BSortProblem *probs_dev, const int32_t *chunk_problem_dev,
+                                const BSortPlan &plan, uint32_t *keys, uint32_t *table,
+                                uint32_t *offsets, uint32_t *tiles, const RayOut &out,
+                                cudaStream_t s);
+cudaError_t prepare_batched_sort(const BSortPlan &plan);
+int scan_tile_elems();
+
 // Sort-key arguments, group edges (device), device and stream of a context.
 int ctx_sort_args(const vrc_ctx *c, SortKeyArgs *P, const double **edges, int *device,
                   cudaStream_t *stream);

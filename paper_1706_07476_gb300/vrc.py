@@ -84,6 +84,11 @@ def _load():
         "vrc_get_timing": ([P, P, P, P, P, I32], C.c_int),
         "vrc_launch_count": ([], C.c_int64),
         "vrc_sort_rays_static": ([P, P, P, P], C.c_int),
+        "vrc_default_batch_options": ([P], None),
+        "vrc_batch_create": ([P, P, I32, P, P], C.c_int),
+        "vrc_batch_launch": ([P, P], C.c_int),
+        "vrc_batch_destroy": ([P], None),
+        "vrc_cast_batched": ([P, P, I32, P], C.c_int),
         "vrc_version": ([], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -237,6 +242,81 @@ def vrc_sort_rays_static(ctx: Context, rays: dict, out, stream=None):
     r, keep = _ray_struct(rays)
     ptr = None if out is None else out.data_ptr()
     _check(_lib.vrc_sort_rays_static(ctx.handle, C.byref(r), ptr, _stream_handle(stream)))
+
+
+class vrc_batch_options(C.Structure):
+    _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("chunk", C.c_int32),
+                ("sort_len_buckets", C.c_int32), ("use_graph", C.c_int32)]
+
+
+def vrc_default_batch_options(**kw) -> vrc_batch_options:
+    o = vrc_batch_options()
+    _lib.vrc_default_batch_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown batch option {k}")
+        setattr(o, k, int(v))
+    return o
+
+
+class Batch:
+    """Owns one vrc_batch plan (and keeps its contexts and rays referenced)."""
+
+    def __init__(self, handle, ctxs, keep):
+        self.handle = handle
+        self.ctxs = ctxs
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            _lib.vrc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ctx_array(ctxs):
+    arr = (C.c_void_p * len(ctxs))(*[c.handle.value if isinstance(c.handle, C.c_void_p) else c.handle
+                                     for c in ctxs])
+    return arr
+
+
+def _rays_array(rays_list):
+    structs, keep = [], []
+    for rays in rays_list:
+        r, k = _ray_struct(rays)
+        structs.append(r)
+        keep.append(k)
+    arr = (vrc_rays * len(structs))(*structs)
+    return arr, keep
+
+
+def vrc_batch_create(ctxs, rays_list, options: vrc_batch_options | None = None) -> Batch:
+    """ctxs: list of Context; rays_list: list of dicts of device tensors."""
+    carr = _ctx_array(ctxs)
+    rarr, keep = _rays_array(rays_list)
+    h = C.c_void_p()
+    _check(_lib.vrc_batch_create(carr, rarr, len(ctxs),
+                                 None if options is None else C.byref(options), C.byref(h)))
+    return Batch(h, list(ctxs), (carr, rarr, keep))
+
+
+def vrc_batch_launch(batch: Batch, stream=None):
+    _check(_lib.vrc_batch_launch(batch.handle, _stream_handle(stream)))
+
+
+def vrc_batch_destroy(batch: Batch):
+    batch.close()
+
+
+def vrc_cast_batched(ctxs, rays_list, stream=None):
+    carr = _ctx_array(ctxs)
+    rarr, keep = _rays_array(rays_list)
+    _check(_lib.vrc_cast_batched(carr, rarr, len(ctxs), _stream_handle(stream)))
 
 
 def vrc_sync(ctx: Context, stream=None):

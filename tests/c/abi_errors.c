@@ -75,6 +75,24 @@ int main(void) {
   EXPECT(vrc_set_options(NULL, &o) == VRC_ERR_ARG);
   EXPECT(vrc_tally_device_ptr(NULL) == NULL);
   vrc_destroy(NULL); /* no-op */
+
+  /* batched form */
+  vrc_batch_options bo;
+  vrc_default_batch_options(&bo);
+  EXPECT(bo.use_graph == 1 && bo.sort_len_buckets == -1 && bo.chunk == 0);
+  vrc_batch *bt = (vrc_batch *)0x1;
+  EXPECT(vrc_batch_create(NULL, &r, 1, NULL, &bt) == VRC_ERR_ARG && bt == NULL);
+  vrc_ctx *none[1] = {NULL};
+  EXPECT(vrc_batch_create(none, &r, 1, NULL, &bt) == VRC_ERR_ARG);
+  EXPECT(vrc_batch_create(none, &r, 0, NULL, &bt) == VRC_ERR_ARG);
+  vrc_batch_options bb = bo; bb.chunk = 10;
+  EXPECT(vrc_batch_create(none, &r, 1, &bb, &bt) == VRC_ERR_ARG);
+  bb = bo; bb.block = 48;
+  EXPECT(vrc_batch_create(none, &r, 1, &bb, &bt) == VRC_ERR_ARG);
+  EXPECT(vrc_batch_launch(NULL, NULL) == VRC_ERR_ARG);
+  vrc_batch_destroy(NULL);
+  EXPECT(vrc_cast_batched(NULL, &r, 1, NULL) == VRC_ERR_ARG);
+  EXPECT(vrc_sort_rays_static(NULL, &r, NULL, NULL) == VRC_ERR_ARG);
   EXPECT(vrc_version() >= 100);
   EXPECT(vrc_device_count() >= 0);
 
