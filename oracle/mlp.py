@@ -9,7 +9,7 @@ evaluation per ray serves every cell it crosses, Eq. 4):
 
     x      = (log10 E - log10 e_lo) / (log10 e_hi - log10 e_lo)
     emb(E) = [sin(pi f_0 x), cos(pi f_0 x), ..., sin(pi f_31 x), cos(pi f_31 x)],
-             f_k = 2^(15 k / 31)  (32 frequencies, 1 to 32768)
+             f_k = 2^(11 k / 31)  (32 frequencies, 1 to 2048)
     h1 = silu(W1 emb + b1)   (64 -> 128)
     h2 = silu(W2 h1 + b2)    (128 -> 128)
     y  = W3 h2 + b3          (128 -> 16), y_m = log Sigma_m(E)
@@ -24,6 +24,7 @@ from __future__ import annotations
 import numpy as np
 
 N_FREQ = 32
+FREQ_MAX_LOG2 = 11  # highest frequency 2^11; a fit study over 2^10 .. 2^15 found 2^11 best
 EMB = 2 * N_FREQ
 HID = 128
 OUT = 16
@@ -33,7 +34,7 @@ N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
 
 
 def frequencies() -> np.ndarray:
-    return 2.0 ** (15.0 * np.arange(N_FREQ) / (N_FREQ - 1))
+    return 2.0 ** (FREQ_MAX_LOG2 * np.arange(N_FREQ) / (N_FREQ - 1))
 
 
 def unpack(params):

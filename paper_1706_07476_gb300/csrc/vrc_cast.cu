@@ -33,7 +33,7 @@ SmemLayout smem_layout(int form, const CastArgs &a, int block) {
   return L;
 }
 
-template <int FORM>
+template <int FORM, bool SURR>
 __global__ void __launch_bounds__(256, 4) k_cast(CastArgs a, SmemLayout L) {
   typedef typename Attenuation<FORM>::inv_t inv_t;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256, 4) k_cast(CastArgs a, SmemLayout L) {
   RayCounts cnt;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.rays.n;
        r += (int64_t)gridDim.x * blockDim.x)
-    cast_one<FORM>(a, r, hash_s, edges, sig_s, inv_s, stride, cnt);
+    cast_one<FORM, SURR>(a, r, hash_s, edges, sig_s, inv_s, stride, cnt);
   flush_counts(cnt, a.counters, a.status);
 }
 
@@ -70,32 +70,36 @@ size_t cast_smem_bytes(int form, const CastArgs &a, int block) {
   return smem_layout(form, a, block).total;
 }
 
+template <int FORM, bool SURR>
+cudaError_t occupancy_t(const CastArgs &a, int block, int *bps) {
+  const size_t smem = cast_smem_bytes(FORM, a, block);
+  cudaError_t e = cudaFuncSetAttribute(k_cast<FORM, SURR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_cast<FORM, SURR>, block, smem);
+}
+
+template <int FORM, bool SURR>
+cudaError_t launch_t(const CastArgs &a, int grid, int block, cudaStream_t s) {
+  const SmemLayout L = smem_layout(FORM, a, block);
+  cudaError_t e = cudaFuncSetAttribute(k_cast<FORM, SURR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  if (e != cudaSuccess) return e;
+  k_cast<FORM, SURR><<<grid, block, L.total, s>>>(a, L);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t cast_occupancy(int form, const CastArgs &a, int block, int *blocks_per_sm) {
-  size_t smem = cast_smem_bytes(form, a, block);
-  if (form == kFormPlain) {
-    cudaFuncSetAttribute(k_cast<kFormPlain>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_cast<kFormPlain>, block, smem);
-  }
-  cudaFuncSetAttribute(k_cast<kFormFp32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_cast<kFormFp32>, block, smem);
+  const bool surr = a.sig_ray != nullptr;
+  if (form == kFormPlain)
+    return surr ? occupancy_t<kFormPlain, true>(a, block, blocks_per_sm) : occupancy_t<kFormPlain, false>(a, block, blocks_per_sm);
+  return surr ? occupancy_t<kFormFp32, true>(a, block, blocks_per_sm) : occupancy_t<kFormFp32, false>(a, block, blocks_per_sm);
 }
 
 cudaError_t launch_cast(int form, const CastArgs &a, int grid, int block, cudaStream_t s) {
-  SmemLayout L = smem_layout(form, a, block);
-  if (form == kFormPlain) {
-    cudaError_t e = cudaFuncSetAttribute(k_cast<kFormPlain>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-    if (e != cudaSuccess) return e;
-    k_cast<kFormPlain><<<grid, block, L.total, s>>>(a, L);
-    note_launches(1);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(k_cast<kFormFp32>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-    if (e != cudaSuccess) return e;
-    k_cast<kFormFp32><<<grid, block, L.total, s>>>(a, L);
-    note_launches(1);
-  }
-  return cudaGetLastError();
+  const bool surr = a.sig_ray != nullptr;
+  if (form == kFormPlain)
+    return surr ? launch_t<kFormPlain, true>(a, grid, block, s) : launch_t<kFormPlain, false>(a, grid, block, s);
+  return surr ? launch_t<kFormFp32, true>(a, grid, block, s) : launch_t<kFormFp32, false>(a, grid, block, s);
 }
 
 cudaError_t launch_scale_copy(const double *src, double *dst, int64_t n, double scale,

@@ -324,7 +324,7 @@ struct RayCounts {
 };
 
 // One ray of a cast: validation, group, cross sections, walk and score.
-template <int FORM>
+template <int FORM, bool SURR = false>
 __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int32_t *hash_s,
                                          const double *edges, float *sig_s,
                                          typename Attenuation<FORM>::inv_t *inv_s, int stride,
@@ -342,7 +342,29 @@ __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int
   }
   const int g = group_of(edges, a.n_groups, (double)E);
   if (g < 0) return;
-  xs_lookup(a.xs, hash_s, E, sig_s, inv_s, stride);
+  bool from_table = true;
+  if (SURR) {  // surrogate sigma, unless this ray's energy bin is flagged
+    const float4 *q = reinterpret_cast<const float4 *>(a.sig_ray + r * 16);
+    const float4 v0 = __ldg(q);
+    if (!isnan(v0.x)) {
+      from_table = false;
+      for (int m4 = 0; m4 < (a.xs.n_mat + 3) / 4; ++m4) {
+        const float4 v = m4 == 0 ? v0 : __ldg(q + m4);
+        const float s4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int m = 4 * m4 + e;
+          if (m < a.xs.n_mat) {
+            sig_s[m * stride] = s4[e];
+            inv_s[m * stride] = s4[e] > 0.f ? typename Attenuation<FORM>::inv_t(1) /
+                                                  typename Attenuation<FORM>::inv_t(s4[e])
+                                            : typename Attenuation<FORM>::inv_t(0);
+          }
+        }
+      }
+    }
+  }
+  if (from_table) xs_lookup(a.xs, hash_s, E, sig_s, inv_s, stride);
   bool ovf = false;
   c.seg += cast_ray<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, a.tally + (int64_t)g * a.mesh.ncells,
                           sig_s, inv_s, stride, &ovf);

@@ -58,6 +58,7 @@ struct CastArgs {
   const double *edges;  // [n_groups+1] or nullptr (single group, every energy)
   int32_t n_groups;
   RayPtrs rays;
+  const float *sig_ray; // [n][16] per-ray sigma from the surrogate (NaN in [0] = use the table), or nullptr
   double *tally;        // [n_groups][ncells]
   unsigned long long *counters;
   unsigned int *status;

@@ -1,0 +1,91 @@
+// Learned cross-section surrogate: network shape, parameter layout and
+// kernel launchers (implementation in vrc_mlp.cu).
+//
+// The network maps one energy to log Sigma_t of up to 16 materials:
+//   x = (log10 E - l0) * inv_range,  features sin(pi f_k x), cos(pi f_k x),
+//   f_k = 2^(11k/31), k = 0..31 (64 features, interleaved sin/cos);
+//   h1 = silu(W1 x + b1) (64 -> 128), h2 = silu(W2 h1 + b2) (128 -> 128),
+//   y = W3 h2 + b3 (128 -> 16).
+// Parameters are float32 masters in one array: W1 [128][64], b1, W2
+// [128][128], b2, W3 [16][128], b3.  Kernels round every weight to bfloat16.
+// The two 128-wide layers run on the tensor cores (bfloat16 operands,
+// float32 accumulation); the 128 -> 16 output layer runs in float32 on the
+// CUDA cores from float32 h2 (2,048 FMAs per ray), because rounding h2 to
+// bfloat16 would put about 1e-2 of noise on log sigma, ten times the
+// accepted error of the surrogate.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vrc {
+namespace mlp {
+
+constexpr int kFreq = 32;
+constexpr double kFreqMaxLog2 = 11.0;  // highest embedding frequency 2^11
+constexpr int kEmb = 64;
+constexpr int kHid = 128;
+constexpr int kOut = 16;
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kHid * kEmb;
+constexpr int kOffW2 = kOffB1 + kHid;
+constexpr int kOffB2 = kOffW2 + kHid * kHid;
+constexpr int kOffW3 = kOffB2 + kHid;
+constexpr int kOffB3 = kOffW3 + kOut * kHid;
+constexpr int kParams = kOffB3 + kOut;  // 26,896
+
+struct Embed {
+  float l0, inv_range;   // x = (log10 E - l0) * inv_range
+  float freq[kFreq];     // f_k
+};
+
+Embed make_embed(double e_lo, double e_hi);
+
+// Training step on rows of (E, target): forward, loss, backward; adds the
+// gradient of the mean squared error (over unmasked (row, material) pairs,
+// normalised by inv_count) to grad and the summed squared error times
+// inv_count to *loss.  With set_n > 0 the rows are drawn from a training
+// set instead: row i uses set entry splitmix64(seed + i) mod set_n.
+struct TrainArgs {
+  const float *params;
+  const float *E;        // [m] (or the training set's energies)
+  const float *target;   // [m][16] log sigma (or the training set's)
+  const uint8_t *mask;   // [m][16] or nullptr (then mat_mask applies)
+  uint32_t mat_mask;     // bit j: output j is trained
+  int64_t m;             // rows in this step
+  int64_t set_n;         // 0, or the training-set size to sample from
+  uint64_t seed;
+  float inv_count;
+  float *grad;           // [kParams], accumulated
+  float *loss;           // scalar, accumulated
+  Embed emb;
+};
+
+cudaError_t launch_train(const TrainArgs &a, cudaStream_t s);
+
+// Adam (Kingma & Ba) on the float32 masters with bias correction.
+cudaError_t launch_adam(float *params, const float *grad, float *m1, float *m2, int n, float lr,
+                        float beta1, float beta2, float eps, int step, cudaStream_t s);
+
+// Forward pass for n energies.  mode 0: y = log sigma to out[n][16].
+// mode 1: sigma = exp(y) to out[n][16], with out[i][0] = NaN when the ray's
+// hash bin is flagged (flags[bin] != 0) or its energy lies outside
+// [e_first, e_last]; outputs with bit j clear in mat_mask are written as 0.
+struct ApplyArgs {
+  const float *params;
+  const float *E;
+  int64_t n;
+  float *out;
+  int mode;
+  uint32_t mat_mask;
+  const uint8_t *flags;
+  int n_hash;
+  float l2min, inv_bw;
+  double e_first, e_last;
+  Embed emb;
+};
+
+cudaError_t launch_apply(const ApplyArgs &a, int num_sms, cudaStream_t s);
+
+}  // namespace mlp
+}  // namespace vrc

@@ -84,6 +84,12 @@ def _load():
         "vrc_get_timing": ([P, P, P, P, P, I32], C.c_int),
         "vrc_launch_count": ([], C.c_int64),
         "vrc_sort_rays_static": ([P, P, P, P], C.c_int),
+        "vrc_default_surrogate_options": ([P], None),
+        "vrc_mlp_forward": ([P, P, I64, C.c_double, C.c_double, P, P], C.c_int),
+        "vrc_mlp_loss_grad": ([P, P, P, P, I64, I64, C.c_double, C.c_double, P, P, P], C.c_int),
+        "vrc_train_surrogate": ([P, P, P], C.c_int),
+        "vrc_set_xs_mode": ([P, I32], C.c_int),
+        "vrc_get_surrogate_params": ([P, P], C.c_int),
         "vrc_default_batch_options": ([P], None),
         "vrc_batch_create": ([P, P, I32, P, P], C.c_int),
         "vrc_batch_launch": ([P, P], C.c_int),
@@ -242,6 +248,65 @@ def vrc_sort_rays_static(ctx: Context, rays: dict, out, stream=None):
     r, keep = _ray_struct(rays)
     ptr = None if out is None else out.data_ptr()
     _check(_lib.vrc_sort_rays_static(ctx.handle, C.byref(r), ptr, _stream_handle(stream)))
+
+
+VRC_MLP_PARAMS = 26896
+VRC_XS_TABLE = 0
+VRC_XS_SURROGATE = 1
+
+
+class vrc_surrogate_options(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("tol", C.c_float),
+                ("seed", C.c_uint64)]
+
+
+class vrc_surrogate_report(C.Structure):
+    _fields_ = [("final_loss", C.c_float), ("bins", C.c_int32), ("bins_accepted", C.c_int32),
+                ("coverage", C.c_float), ("max_rel_err_accepted", C.c_float),
+                ("median_rel_err", C.c_float), ("train_points", C.c_int64),
+                ("validation_points", C.c_int64)]
+
+
+def vrc_default_surrogate_options(**kw) -> vrc_surrogate_options:
+    o = vrc_surrogate_options()
+    _lib.vrc_default_surrogate_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown surrogate option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def vrc_mlp_forward(params, E, e_lo: float, e_hi: float, out, stream=None):
+    """Device tensors: params [VRC_MLP_PARAMS] f32, E [n] f32, out [n, 16] f32."""
+    _check(_lib.vrc_mlp_forward(params.data_ptr(), E.data_ptr(), E.shape[0], float(e_lo),
+                                float(e_hi), out.data_ptr(), _stream_handle(stream)))
+
+
+def vrc_mlp_loss_grad(params, E, target, mask, count: int, e_lo: float, e_hi: float, grad, loss,
+                      stream=None):
+    """Device tensors; mask uint8 [n, 16] or None.  grad and loss are overwritten."""
+    _check(_lib.vrc_mlp_loss_grad(params.data_ptr(), E.data_ptr(), target.data_ptr(),
+                                  None if mask is None else mask.data_ptr(), E.shape[0],
+                                  int(count), float(e_lo), float(e_hi), grad.data_ptr(),
+                                  loss.data_ptr(), _stream_handle(stream)))
+
+
+def vrc_train_surrogate(ctx: Context, options: vrc_surrogate_options | None = None) -> dict:
+    rep = vrc_surrogate_report()
+    _check(_lib.vrc_train_surrogate(ctx.handle, None if options is None else C.byref(options),
+                                    C.byref(rep)))
+    return {k: getattr(rep, k) for k, _ in rep._fields_}
+
+
+def vrc_set_xs_mode(ctx: Context, mode: int):
+    _check(_lib.vrc_set_xs_mode(ctx.handle, int(mode)))
+
+
+def vrc_get_surrogate_params(ctx: Context) -> np.ndarray:
+    out = np.empty(VRC_MLP_PARAMS, np.float32)
+    _check(_lib.vrc_get_surrogate_params(ctx.handle, out.ctypes.data))
+    return out
 
 
 class vrc_batch_options(C.Structure):

@@ -54,10 +54,10 @@ def test_forward_matches_torch_float64():
         for layer, (w, b) in zip([net[0], net[2], net[4]], [("W1", "b1"), ("W2", "b2"), ("W3", "b3")]):
             layer.weight.copy_(torch.from_numpy(P[w]))
             layer.bias.copy_(torch.from_numpy(P[b]))
-        # embedding written independently: angle = pi * 2^(15k/31) * x
+        # embedding written independently: angle = pi * 2^(11k/31) * x
         x = (np.log10(E) + 5.0) / (np.log10(2e7) + 5.0)
         k = np.arange(32)
-        ang = np.pi * np.exp2(15.0 * k / 31.0)[None, :] * x[:, None]
+        ang = np.pi * np.exp2(11.0 * k / 31.0)[None, :] * x[:, None]
         emb = np.stack([np.sin(ang), np.cos(ang)], axis=2).reshape(len(E), 64)
         want = net(torch.from_numpy(emb)).numpy()
     np.testing.assert_allclose(y, want, rtol=1e-12, atol=1e-12)
@@ -68,7 +68,7 @@ def test_embedding_end_values():
     np.testing.assert_allclose(e[0, 0::2], 0.0, atol=1e-15)
     np.testing.assert_allclose(e[0, 1::2], 1.0, atol=1e-15)
     f = M.frequencies()
-    assert f[0] == 1.0 and f[-1] == pytest.approx(32768.0, rel=1e-14)
+    assert f[0] == 1.0 and f[-1] == pytest.approx(2048.0, rel=1e-14)
     np.testing.assert_allclose(e[1, 0::2], np.sin(np.pi * f), atol=1e-9)
 
 
