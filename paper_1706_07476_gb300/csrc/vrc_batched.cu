@@ -25,9 +25,14 @@ BatchSmem batch_smem(int form, const BatchShape &sh, int block) {
   L.edges = off;
   off = align16(off + sizeof(double) * ((size_t)sh.max_groups + 1));
   L.sig = off;
-  off = align16(off + sizeof(float) * (size_t)sh.max_mat * block);
-  L.inv = off;
-  off = align16(off + (form == kFormPlain ? sizeof(double) : sizeof(float)) * (size_t)sh.max_mat * block);
+  if (form == kFormPlain) {
+    off = align16(off + sizeof(float) * (size_t)sh.max_mat * block);
+    L.inv = off;
+    off = align16(off + sizeof(double) * (size_t)sh.max_mat * block);
+  } else {  // (sigma, 1/sigma) float pairs
+    L.inv = off + sizeof(float);
+    off = align16(off + 2 * sizeof(float) * (size_t)sh.max_mat * block);
+  }
   L.total = off;
   return L;
 }
@@ -42,9 +47,10 @@ __global__ void __launch_bounds__(256, 4)
   __shared__ int s_item;
   int32_t *hash_s = reinterpret_cast<int32_t *>(smem + L.hash);
   double *edges_s = reinterpret_cast<double *>(smem + L.edges);
-  float *sig_s = reinterpret_cast<float *>(smem + L.sig) + threadIdx.x;
-  inv_t *inv_s = reinterpret_cast<inv_t *>(smem + L.inv) + threadIdx.x;
-  const int stride = blockDim.x;
+  const int lanes = FORM == kFormPlain ? 1 : 2;  // FP32: (sigma, 1/sigma) pairs
+  float *sig_s = reinterpret_cast<float *>(smem + L.sig) + lanes * threadIdx.x;
+  inv_t *inv_s = reinterpret_cast<inv_t *>(smem + L.inv) + lanes * threadIdx.x;
+  const int stride = lanes * blockDim.x;
   int cur = -1;
   // Each pass takes one item index; indices only grow, so at most n_items passes.
   for (int pass = 0; pass < n_items; ++pass) {

@@ -25,10 +25,15 @@ SmemLayout smem_layout(int form, const CastArgs &a, int block) {
   off += sizeof(double) * (a.edges ? (size_t)a.n_groups + 1 : 1);
   off = align_up(off, 16);
   L.sig = off;
-  off += sizeof(float) * (size_t)a.xs.n_mat * block;
-  off = align_up(off, 16);
-  L.inv = off;
-  off += (form == kFormPlain ? sizeof(double) : sizeof(float)) * (size_t)a.xs.n_mat * block;
+  if (form == kFormPlain) {  // float sigma [M][B], then double 1/sigma [M][B]
+    off += sizeof(float) * (size_t)a.xs.n_mat * block;
+    off = align_up(off, 16);
+    L.inv = off;
+    off += sizeof(double) * (size_t)a.xs.n_mat * block;
+  } else {  // (sigma, 1/sigma) float pairs [M][B]
+    L.inv = off + sizeof(float);
+    off += 2 * sizeof(float) * (size_t)a.xs.n_mat * block;
+  }
   L.total = align_up(off, 16);
   return L;
 }
@@ -39,8 +44,9 @@ __global__ void __launch_bounds__(256, 4) k_cast(CastArgs a, SmemLayout L) {
   extern __shared__ __align__(16) unsigned char smem[];
   int32_t *hash_s = reinterpret_cast<int32_t *>(smem + L.hash);
   double *edges_s = reinterpret_cast<double *>(smem + L.edges);
-  float *sig_s = reinterpret_cast<float *>(smem + L.sig) + threadIdx.x;
-  inv_t *inv_s = reinterpret_cast<inv_t *>(smem + L.inv) + threadIdx.x;
+  const int lanes = FORM == kFormPlain ? 1 : 2;  // FP32: (sigma, 1/sigma) pairs
+  float *sig_s = reinterpret_cast<float *>(smem + L.sig) + lanes * threadIdx.x;
+  inv_t *inv_s = reinterpret_cast<inv_t *>(smem + L.inv) + lanes * threadIdx.x;
 
   if (a.xs.n_union > 0)
     for (int t = threadIdx.x; t <= a.xs.n_hash; t += blockDim.x) hash_s[t] = a.xs.hash[t];
@@ -48,7 +54,7 @@ __global__ void __launch_bounds__(256, 4) k_cast(CastArgs a, SmemLayout L) {
     for (int t = threadIdx.x; t <= a.n_groups; t += blockDim.x) edges_s[t] = a.edges[t];
   __syncthreads();
   const double *edges = a.edges ? edges_s : nullptr;
-  const int stride = blockDim.x;
+  const int stride = lanes * blockDim.x;
 
   RayCounts cnt;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.rays.n;
