@@ -329,10 +329,9 @@ int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s) {
   VRC_CUDA(c->sortOffsets.ensure(plan.bytes_table), "allocating sort scratch");
   VRC_CUDA(c->sortTiles.ensure(plan.bytes_tiles), "allocating sort scratch");
   VRC_CUDA(c->sortRays.ensure(plan.bytes_rays), "allocating sort scratch");
-  float *base = static_cast<float *>(c->sortRays.p);
   RayOut out;
-  float **f[8] = {&out.x, &out.y, &out.z, &out.u, &out.v, &out.w, &out.E, &out.wt};
-  for (int k = 0; k < 8; ++k) *f[k] = base + (size_t)k * rp.n;
+  std::memset(&out, 0, sizeof out);
+  out.aos = static_cast<float4 *>(c->sortRays.p);  // sorted copy as 32-byte records
   TimedSpan span{nullptr, nullptr, 1};
   if (c->timing) {
     VRC_CUDA(c->get_event(&span.start), "creating a timing event");
@@ -348,8 +347,8 @@ int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s) {
     VRC_CUDA(cudaEventRecord(span.stop, s), "recording a timing event");
     c->pending.push_back(span);
   }
-  rp.x = out.x; rp.y = out.y; rp.z = out.z; rp.u = out.u;
-  rp.v = out.v; rp.w = out.w; rp.E = out.E; rp.wt = out.wt;
+  rp.x = rp.y = rp.z = rp.u = rp.v = rp.w = rp.E = rp.wt = nullptr;
+  rp.aos = out.aos;
   return VRC_OK;
 }
 
@@ -500,6 +499,7 @@ int vrc_cast_rays(vrc_ctx *c, const vrc_rays *r, void *cuda_stream) {
   }
   cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
   RayPtrs rp;
+  rp.aos = nullptr;
   rp.n = r->n;
   if (r->on_device) {
     rp.x = r->x; rp.y = r->y; rp.z = r->z; rp.u = r->u;
@@ -533,6 +533,7 @@ int vrc_cast_rays(vrc_ctx *c, const vrc_rays *r, void *cuda_stream) {
     std::memset(&aa, 0, sizeof aa);
     aa.params = static_cast<const float *>(c->mlpParams.p);
     aa.E = rp.E;
+    aa.aos = rp.aos;
     aa.n = rp.n;
     aa.out = static_cast<float *>(c->sigBuf.p);
     aa.mode = 1;
@@ -790,9 +791,9 @@ cudaError_t enqueue_batch(vrc_batch *b, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   if (b->sorted) {
-    const int64_t T = b->total_rays;
-    RayOut o = {b->d_sorted, b->d_sorted + T, b->d_sorted + 2 * T, b->d_sorted + 3 * T,
-                b->d_sorted + 4 * T, b->d_sorted + 5 * T, b->d_sorted + 6 * T, b->d_sorted + 7 * T};
+    RayOut o;
+    std::memset(&o, 0, sizeof o);
+    o.aos = reinterpret_cast<float4 *>(b->d_sorted);  // sorted copy as 32-byte records
     e = launch_batched_sort(b->d_bprobs, b->d_chunk_problem, b->bplan, b->d_keys, b->d_table,
                             b->d_offsets, b->d_tiles, o, s);
     if (e != cudaSuccess) return e;
@@ -940,10 +941,9 @@ int vrc_batch_create(vrc_ctx *const *ctxs, const vrc_rays *rays, int32_t n_probl
   BatchShape sh{0, 0, 0};
   for (int p = 0; p < n_problems; ++p) {
     RayPtrs rp;
+    std::memset(&rp, 0, sizeof rp);
     if (b->sorted) {
-      float *s = b->d_sorted;
-      rp.x = s; rp.y = s + total; rp.z = s + 2 * total; rp.u = s + 3 * total;
-      rp.v = s + 4 * total; rp.w = s + 5 * total; rp.E = s + 6 * total; rp.wt = s + 7 * total;
+      rp.aos = reinterpret_cast<const float4 *>(b->d_sorted);
       rp.n = total;
     } else {
       const vrc_rays &r = rays[p];

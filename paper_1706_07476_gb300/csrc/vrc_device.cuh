@@ -345,6 +345,18 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float p
   return nseg;
 }
 
+// The eight fields of ray r (SoA or 32-byte records).
+__device__ __forceinline__ void load_ray(const RayPtrs &R, int64_t r, float (&f)[8]) {
+  if (R.aos) {
+    const float4 a = __ldg(R.aos + 2 * r), b = __ldg(R.aos + 2 * r + 1);
+    f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+    f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
+  } else {
+    f[0] = __ldg(R.x + r); f[1] = __ldg(R.y + r); f[2] = __ldg(R.z + r); f[3] = __ldg(R.u + r);
+    f[4] = __ldg(R.v + r); f[5] = __ldg(R.w + r); f[6] = __ldg(R.E + r); f[7] = __ldg(R.wt + r);
+  }
+}
+
 // Per-thread counters of one cast, flushed with one atomic per warp.
 struct RayCounts {
   uint32_t seg = 0, rays = 0, rej = 0, ovf = 0;
@@ -356,10 +368,9 @@ __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int
                                          const double *edges, float *sig_s,
                                          typename Attenuation<FORM>::inv_t *inv_s, int stride,
                                          RayCounts &c) {
-  const RayPtrs &R = a.rays;
-  const float x = __ldg(R.x + r), y = __ldg(R.y + r), z = __ldg(R.z + r);
-  const float u = __ldg(R.u + r), v = __ldg(R.v + r), w = __ldg(R.w + r);
-  const float E = __ldg(R.E + r), wt = __ldg(R.wt + r);
+  float f[8];
+  load_ray(a.rays, r, f);
+  const float x = f[0], y = f[1], z = f[2], u = f[3], v = f[4], w = f[5], E = f[6], wt = f[7];
   ++c.rays;
   const float dn = sqrtf(u * u + v * v + w * w);
   if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(u) && isfinite(v) && isfinite(w) &&

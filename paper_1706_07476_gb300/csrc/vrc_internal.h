@@ -47,8 +47,11 @@ struct XsDev {
   const int32_t *hash;  // [n_hash+1] interval index at each bin's lower energy
 };
 
+// A ray batch: eight float32 arrays (SoA), or, when aos is set, one array
+// of 32-byte records (x, y, z, u | v, w, E, wt) as two float4 per ray.
 struct RayPtrs {
   const float *x, *y, *z, *u, *v, *w, *E, *wt;
+  const float4 *aos;
   int64_t n;
 };
 

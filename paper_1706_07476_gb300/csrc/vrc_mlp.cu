@@ -415,8 +415,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_mlp_apply(ApplyArgs a) {
   const int64_t tiles = (a.n + 15) / 16;
   for (int64_t tile = (int64_t)blockIdx.x * 4 + warp; tile < tiles; tile += (int64_t)gridDim.x * 4) {
     const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
-    const float E0 = r0 < a.n ? a.E[r0] : 1.0f;
-    const float E1 = r1 < a.n ? a.E[r1] : 1.0f;
+    const float E0 = r0 < a.n ? (a.aos ? __ldg(a.aos + 2 * r0 + 1).z : a.E[r0]) : 1.0f;
+    const float E1 = r1 < a.n ? (a.aos ? __ldg(a.aos + 2 * r1 + 1).z : a.E[r1]) : 1.0f;
     // layer 1 A operand: features k = 16j + 2t (+1) and 16j + 8 + 2t (+1),
     // i.e. frequencies 8j + t and 8j + 4 + t, for rows g and g + 8
     uint32_t x[4][4];

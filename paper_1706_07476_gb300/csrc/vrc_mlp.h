@@ -73,7 +73,8 @@ cudaError_t launch_adam(float *params, const float *grad, float *m1, float *m2, 
 // [e_first, e_last]; outputs with bit j clear in mat_mask are written as 0.
 struct ApplyArgs {
   const float *params;
-  const float *E;
+  const float *E;          // energies, or nullptr when aos is set
+  const float4 *aos;       // 32-byte ray records (E is the third field of the second float4)
   int64_t n;
   float *out;
   int mode;

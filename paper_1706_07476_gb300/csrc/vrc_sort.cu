@@ -60,9 +60,9 @@ __device__ __forceinline__ int crossing_estimate(const SortKeyArgs &P, float px,
 
 __device__ __forceinline__ uint32_t ray_key(const SortKeyArgs &P, const double *edges, const RayPtrs &R,
                                             int64_t r) {
-  const float x = __ldg(R.x + r), y = __ldg(R.y + r), z = __ldg(R.z + r);
-  const float u = __ldg(R.u + r), v = __ldg(R.v + r), w = __ldg(R.w + r);
-  const float E = __ldg(R.E + r), wt = __ldg(R.wt + r);
+  float f[8];
+  load_ray(R, r, f);
+  const float x = f[0], y = f[1], z = f[2], u = f[3], v = f[4], w = f[5], E = f[6], wt = f[7];
   const float dn = sqrtf(u * u + v * v + w * w);
   const uint32_t reject = (uint32_t)(P.n_keys - 1);
   if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(u) && isfinite(v) && isfinite(w) &&
@@ -191,14 +191,15 @@ __global__ void __launch_bounds__(kSortBlock) k_sort_scatter(RayPtrs R, SortKeyA
   const int64_t end = min(begin + P.chunk, R.n);
   for (int64_t r = begin + threadIdx.x; r < end; r += blockDim.x) {
     const uint32_t pos = atomicAdd(&cursor[keys[r]], 1u);
-    O.x[pos] = __ldg(R.x + r);
-    O.y[pos] = __ldg(R.y + r);
-    O.z[pos] = __ldg(R.z + r);
-    O.u[pos] = __ldg(R.u + r);
-    O.v[pos] = __ldg(R.v + r);
-    O.w[pos] = __ldg(R.w + r);
-    O.E[pos] = __ldg(R.E + r);
-    O.wt[pos] = __ldg(R.wt + r);
+    float f[8];
+    load_ray(R, r, f);
+    if (O.aos) {
+      O.aos[2 * (int64_t)pos] = make_float4(f[0], f[1], f[2], f[3]);
+      O.aos[2 * (int64_t)pos + 1] = make_float4(f[4], f[5], f[6], f[7]);
+    } else {
+      O.x[pos] = f[0]; O.y[pos] = f[1]; O.z[pos] = f[2]; O.u[pos] = f[3];
+      O.v[pos] = f[4]; O.w[pos] = f[5]; O.E[pos] = f[6]; O.wt[pos] = f[7];
+    }
   }
 }
 
@@ -244,14 +245,15 @@ __global__ void __launch_bounds__(kSortBlock) k_bsort_scatter(const BSortProblem
   const RayPtrs R = B.src;
   for (int64_t r = begin + threadIdx.x; r < end; r += blockDim.x) {
     const uint32_t pos = atomicAdd(&cursor[keys[B.ray_base + r]], 1u);
-    O.x[pos] = __ldg(R.x + r);
-    O.y[pos] = __ldg(R.y + r);
-    O.z[pos] = __ldg(R.z + r);
-    O.u[pos] = __ldg(R.u + r);
-    O.v[pos] = __ldg(R.v + r);
-    O.w[pos] = __ldg(R.w + r);
-    O.E[pos] = __ldg(R.E + r);
-    O.wt[pos] = __ldg(R.wt + r);
+    float f[8];
+    load_ray(R, r, f);
+    if (O.aos) {
+      O.aos[2 * (int64_t)pos] = make_float4(f[0], f[1], f[2], f[3]);
+      O.aos[2 * (int64_t)pos + 1] = make_float4(f[4], f[5], f[6], f[7]);
+    } else {
+      O.x[pos] = f[0]; O.y[pos] = f[1]; O.z[pos] = f[2]; O.u[pos] = f[3];
+      O.v[pos] = f[4]; O.w[pos] = f[5]; O.E[pos] = f[6]; O.wt[pos] = f[7];
+    }
   }
 }
 

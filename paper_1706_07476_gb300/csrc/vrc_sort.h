@@ -24,6 +24,7 @@ struct SortKeyArgs {
 
 struct RayOut {
   float *x, *y, *z, *u, *v, *w, *E, *wt;
+  float4 *aos;  // when set, the sorted rays are written as 32-byte records here
 };
 
 struct SortPlan {

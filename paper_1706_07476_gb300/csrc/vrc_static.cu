@@ -98,6 +98,7 @@ extern "C" int vrc_sort_rays_static(vrc_ctx *c, const vrc_rays *in, float *out, 
       const int64_t n = in->n;
       RayOut o = {out, out + n, out + 2 * n, out + 3 * n, out + 4 * n, out + 5 * n, out + 6 * n, out + 7 * n};
       RayPtrs rp;
+      rp.aos = nullptr;
       rp.x = in->x; rp.y = in->y; rp.z = in->z; rp.u = in->u;
       rp.v = in->v; rp.w = in->w; rp.E = in->E; rp.wt = in->wt;
       rp.n = n;
