@@ -253,7 +253,7 @@ struct Attenuation<kFormFp32> {
 // ray leaves the mesh or after max_steps steps (then *overflow is set).
 // Returns the number of positive-length segments scored.
 template <int FORM>
-__device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float py, float pz,
+__device__ __forceinline__ uint32_t cast_ray(const MeshDev &M, float px, float py, float pz,
                                              float u, float v, float w, float wt, float dn,
                                              double *__restrict__ tal, const float *sg,
                                              const typename Attenuation<FORM>::inv_t *inv,
@@ -266,8 +266,8 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float p
   bool miss = false;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    D[k] = df_add_f(m.org[k], -p[k]);
-    const df Dn = df_add(D[k], df_mul_f(m.h[k], (float)m.n[k]));
+    D[k] = df_add_f(M.org[k], -p[k]);
+    const df Dn = df_add(D[k], df_mul_f(M.h[k], (float)M.n[k]));
     if (d[k] == 0.f) {
       R[k] = {0.f, 0.f};
       if (df_pos(D[k]) || !df_pos(Dn)) miss = true;  // p < lo or p >= hi
@@ -282,27 +282,40 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float p
   }
   if (miss || !df_lt(s_in, s_out)) return 0;
 
-  int i[3], stp[3], off[3], cst[3];
-  df S[3];
+  // Per axis: S0 = first crossing ahead of the start, from the exact
+  // formula above (a start exactly on a plane gives S0 = 0); B = h |1/d|, the
+  // spacing of later crossings, which are S0 + m B after m steps on that axis
+  // (a sum of two positive terms: about 2^-46 relative, no cancellation);
+  // cnt = planes that axis crosses before the ray leaves the mesh.
+  df S[3], S0[3], B[3];
+  float m[3], cnt[3];
+  int cst[3];
   int cell = 0;
-  const int cstride[3] = {1, m.n[0], m.n[0] * m.n[1]};
+  const int cstride[3] = {1, M.n[0], M.n[0] * M.n[1]};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    df c = df_add_f(df_neg(m.org[k]), p[k]);  // p - org
+    df c = df_add_f(df_neg(M.org[k]), p[k]);  // p - org
     if (s_in.hi > 0.f && d[k] != 0.f) c = df_add(c, df_mul_f(s_in, d[k]));
-    i[k] = df_floor_clamp(df_mul(c, m.inv_h[k]), m.n[k]);
-    cell += i[k] * cstride[k];
-    stp[k] = d[k] > 0.f ? 1 : -1;
-    off[k] = d[k] > 0.f ? 1 : 0;
-    cst[k] = stp[k] * cstride[k];
-    S[k] = d[k] == 0.f ? inf : df_mul(df_add(D[k], df_mul_f(m.h[k], (float)(i[k] + off[k]))), R[k]);
+    const int ik = df_floor_clamp(df_mul(c, M.inv_h[k]), M.n[k]);
+    cell += ik * cstride[k];
+    m[k] = 0.f;
+    if (d[k] == 0.f) {
+      S[k] = inf; S0[k] = inf; B[k] = {0.f, 0.f}; cnt[k] = -1.f; cst[k] = 0;
+    } else {
+      const bool fwd = d[k] > 0.f;
+      S0[k] = df_mul(df_add(D[k], df_mul_f(M.h[k], (float)(ik + (fwd ? 1 : 0)))), R[k]);
+      B[k] = df_mul(M.h[k], fwd ? R[k] : df_neg(R[k]));
+      S[k] = S0[k];
+      cnt[k] = (float)(fwd ? M.n[k] - 1 - ik : ik);
+      cst[k] = fwd ? cstride[k] : -cstride[k];
+    }
   }
 
   Attenuation<FORM> att(wt);
   df s_cur = s_in;
-  unsigned mat = __ldg(m.mat + cell);
+  unsigned mat = __ldg(M.mat + cell);
   uint32_t nseg = 0;
-  const int max_steps = m.n[0] + m.n[1] + m.n[2] + 3;
+  const int max_steps = M.n[0] + M.n[1] + M.n[2] + 3;
   for (int step = 0;; ++step) {
     // axis of the nearest crossing (ties resolved x, then y, then z)
     const bool y_first = df_lt(S[1], S[0]);
@@ -310,10 +323,10 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float p
     const bool z_first = df_lt(S[2], Sk);
     if (z_first) Sk = S[2];
     const int k = z_first ? 2 : (y_first ? 1 : 0);
-    const int inew = (k == 0 ? i[0] : k == 1 ? i[1] : i[2]) + (k == 0 ? stp[0] : k == 1 ? stp[1] : stp[2]);
-    const bool leaving = (unsigned)inew >= (unsigned)(k == 0 ? m.n[0] : k == 1 ? m.n[1] : m.n[2]);
+    const float mk = k == 0 ? m[0] : k == 1 ? m[1] : m[2];
+    const bool leaving = mk == (k == 0 ? cnt[0] : k == 1 ? cnt[1] : cnt[2]);
     const int ncell = cell + (k == 0 ? cst[0] : k == 1 ? cst[1] : cst[2]);
-    const unsigned nmat = leaving ? 0u : __ldg(m.mat + ncell);  // prefetch the next cell
+    const unsigned nmat = leaving ? 0u : __ldg(M.mat + ncell);  // prefetch the next cell
 
     const float l = fmaxf(df_diff(Sk, s_cur), 0.f) * dn;
     typename Attenuation<FORM>::score_t sc;
@@ -331,15 +344,13 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &m, float px, float p
     s_cur = Sk;
     cell = ncell;
     mat = nmat;
-    // next crossing on the stepped axis, from its integer plane index
-    const df Dk = k == 0 ? D[0] : k == 1 ? D[1] : D[2];
-    const df hk = k == 0 ? m.h[0] : k == 1 ? m.h[1] : m.h[2];
-    const df Rk = k == 0 ? R[0] : k == 1 ? R[1] : R[2];
-    const int ok = k == 0 ? off[0] : k == 1 ? off[1] : off[2];
-    const df Sn = df_mul(df_add(Dk, df_mul_f(hk, (float)(inew + ok))), Rk);
+    // next crossing on the stepped axis
+    const float mn = mk + 1.f;
+    const df Sn = df_add(k == 0 ? S0[0] : k == 1 ? S0[1] : S0[2],
+                         df_mul_f(k == 0 ? B[0] : k == 1 ? B[1] : B[2], mn));
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      if (a == k) { i[a] = inew; S[a] = Sn; }
+      if (a == k) { m[a] = mn; S[a] = Sn; }
     }
   }
   return nseg;
