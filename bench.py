@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--sort", type=int, default=-1, help="ray sorting: -1 auto, 0 off, 1 on")
     ap.add_argument("--n-rays", type=int, default=1 << 24)
     ap.add_argument("--mesh", type=int, default=256)
-    ap.add_argument("--workload", choices=["slab256", "batched"], default="slab256")
+    ap.add_argument("--workload", choices=["slab256", "batched", "stream"], default="slab256")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity-sample", action="store_true")
@@ -306,6 +306,76 @@ def run_batched(args, rank, world, local):
     return 0
 
 
+# --------------------------------------------------------------------------- streaming
+
+def run_stream(args, rank, world, local):
+    """Producer overlap: CPU threads copy the slab256 rays into pinned
+    buffers of 2^20 records (the stand-in for a random walk filling its ray
+    buffer) while earlier buffers are uploaded and cast.  Reports the
+    producer alone, the GPU alone (buffers filled beforehand) and the two
+    overlapped, in rays/s and segments/s."""
+    import concurrent.futures as cf
+    import torch
+    from paper_1706_07476_gb300 import vrc
+    torch.cuda.set_device(local)
+    prob = workload(args)
+    records = np.ascontiguousarray(np.stack([prob.rays[k] for k in W.RAY_FIELDS], axis=1))
+    cap = 1 << 20
+    nbuf = (prob.n_rays + cap - 1) // cap
+    ctx = vrc.context_for(prob, vrc.vrc_default_options(form=vrc.VRC_FORM_FP32, device=local))
+    rs = vrc.RayStream(ctx, cap, 3)
+    pool = cf.ThreadPoolExecutor(max_workers=8)
+
+    def fill(buf, lo, n):
+        parts = [(i * n // 8, (i + 1) * n // 8) for i in range(8)]
+        list(pool.map(lambda ab: buf.__setitem__(slice(ab[0], ab[1]), records[lo + ab[0]:lo + ab[1]]), parts))
+
+    def run(produce: bool, cast: bool):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for b in range(nbuf):
+            lo = b * cap
+            n = min(cap, prob.n_rays - lo)
+            buf = rs.acquire()
+            if produce:
+                fill(buf, lo, n)
+            if cast:
+                rs.submit(n)
+            else:
+                rs.submit(0)
+        rs.finish()
+        return time.perf_counter() - t0
+
+    for _ in range(max(1, args.warmup)):
+        run(True, True)
+    t_cpu = min(run(True, False) for _ in range(2))
+    vrc.vrc_reset_tally(ctx)
+    t_gpu = min(run(False, True) for _ in range(2))
+    vrc.vrc_reset_tally(ctx)
+    vrc.vrc_sync(ctx)
+    t_both = [run(True, True) for _ in range(max(1, min(args.steps, 5)))]
+    rc, st = vrc.vrc_sync(ctx)
+    seg_per_pass = st["segments"] / len(t_both)
+    tb = min(t_both)
+    line = {
+        "metric": "streamed ray buffers: rays/s and segments/s with producer overlap",
+        "value": seg_per_pass / tb, "unit": UNIT, "n_gpus": world, "steps": len(t_both),
+        "warmup": args.warmup, "ms_per_step": 1e3 * tb, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "buffer_rays": cap, "buffers": 3, "producer_threads": 8},
+        "producer_only_rays_per_s": prob.n_rays / t_cpu,
+        "gpu_only_rays_per_s": prob.n_rays / t_gpu,
+        "overlapped_rays_per_s": prob.n_rays / tb,
+        "overlap_efficiency": max(t_cpu, t_gpu) / tb,
+        "gpu_time_over_cpu_time": t_gpu / t_cpu,
+    }
+    rs.close()
+    ctx.close()
+    pool.shutdown()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -315,6 +385,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batched":
         return run_batched(args, rank, world, local)
+    if args.workload == "stream":
+        return run_stream(args, rank, world, local)
 
     import torch
     import torch.distributed as dist

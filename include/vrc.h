@@ -207,6 +207,41 @@ void vrc_destroy(vrc_ctx *c);
 /* Thread-local description of the last error ("" if none). */
 const char *vrc_last_error(void);
 
+/* ---- streaming ray buffers ---------------------------------------------
+ * Sec. 3: the CPU random walk stores rays in a buffer; when it is full the
+ * buffer goes to the GPU and is cleared, and the CPU keeps simulating
+ * histories while the GPU casts it (Secs. 2-3: the casting cost hides behind
+ * the random walk).  A vrc_stream keeps n_buffers pinned host buffers of
+ * 32-byte ray records: the producer fills one while earlier ones are copied
+ * (on a copy stream) and cast (on the context's stream), the two ordered by
+ * events so that a buffer is reused only after its copy, and its device
+ * copy only after its cast, have finished. */
+typedef struct {
+  float x, y, z, u, v, w, E, wt;
+} vrc_ray_record;
+
+typedef struct vrc_stream vrc_stream;
+
+/* Allocates n_buffers (>= 2) pinned host buffers and device buffers of
+ * capacity rays each for context c.  Errors: VRC_ERR_ARG, VRC_ERR_OOM,
+ * VRC_ERR_CUDA. */
+int vrc_stream_create(vrc_ctx *c, int64_t capacity, int32_t n_buffers, vrc_stream **out);
+
+/* Hands out the next pinned host buffer to fill (capacity records); waits
+ * until that buffer's previous upload has finished.  Calling acquire twice
+ * without a submit returns the same buffer. */
+int vrc_stream_acquire(vrc_stream *s, vrc_ray_record **buffer, int64_t *capacity);
+
+/* Queues the first n records of the acquired buffer: asynchronous H2D copy,
+ * then the cast into the context's tally.  Returns at once. */
+int vrc_stream_submit(vrc_stream *s, int64_t n);
+
+/* Waits until every submitted buffer has been cast. */
+int vrc_stream_finish(vrc_stream *s);
+
+/* Waits for the stream's work and frees its buffers; NULL is a no-op. */
+void vrc_stream_destroy(vrc_stream *s);
+
 /* ---- learned cross-section surrogate ------------------------------------
  * Energy is constant along a ray (Eq. 4 has one E_j per ray), so Σt of every
  * material is needed once per ray.  The surrogate replaces the table lookup

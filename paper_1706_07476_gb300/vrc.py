@@ -84,6 +84,11 @@ def _load():
         "vrc_get_timing": ([P, P, P, P, P, I32], C.c_int),
         "vrc_launch_count": ([], C.c_int64),
         "vrc_sort_rays_static": ([P, P, P, P], C.c_int),
+        "vrc_stream_create": ([P, I64, I32, P], C.c_int),
+        "vrc_stream_acquire": ([P, P, P], C.c_int),
+        "vrc_stream_submit": ([P, I64], C.c_int),
+        "vrc_stream_finish": ([P], C.c_int),
+        "vrc_stream_destroy": ([P], None),
         "vrc_default_surrogate_options": ([P], None),
         "vrc_mlp_forward": ([P, P, I64, C.c_double, C.c_double, P, P], C.c_int),
         "vrc_mlp_loss_grad": ([P, P, P, P, I64, I64, C.c_double, C.c_double, P, P, P], C.c_int),
@@ -307,6 +312,42 @@ def vrc_get_surrogate_params(ctx: Context) -> np.ndarray:
     out = np.empty(VRC_MLP_PARAMS, np.float32)
     _check(_lib.vrc_get_surrogate_params(ctx.handle, out.ctypes.data))
     return out
+
+
+class RayStream:
+    """vrc_stream: pinned buffers of 32-byte ray records, filled by the caller
+    while earlier buffers are uploaded and cast (double buffering)."""
+
+    FIELDS = 8
+
+    def __init__(self, ctx: Context, capacity: int, n_buffers: int = 2):
+        h = C.c_void_p()
+        _check(_lib.vrc_stream_create(ctx.handle, int(capacity), int(n_buffers), C.byref(h)))
+        self.handle, self.ctx, self.capacity = h, ctx, int(capacity)
+
+    def acquire(self) -> np.ndarray:
+        """The next buffer as a (capacity, 8) float32 view: x y z u v w E wt."""
+        ptr, cap = C.c_void_p(), C.c_int64()
+        _check(_lib.vrc_stream_acquire(self.handle, C.byref(ptr), C.byref(cap)))
+        buf = (C.c_float * (cap.value * self.FIELDS)).from_address(ptr.value)
+        return np.ctypeslib.as_array(buf).reshape(cap.value, self.FIELDS)
+
+    def submit(self, n: int):
+        _check(_lib.vrc_stream_submit(self.handle, int(n)))
+
+    def finish(self):
+        _check(_lib.vrc_stream_finish(self.handle))
+
+    def close(self):
+        if self.handle:
+            _lib.vrc_stream_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class vrc_batch_options(C.Structure):
