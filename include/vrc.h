@@ -194,6 +194,14 @@ int vrc_read_tally(vrc_ctx *c, double *out_host, int64_t n, int32_t flags, void 
  * vrc_destroy.  NULL if c is NULL. */
 double *vrc_tally_device_ptr(vrc_ctx *c);
 
+/* The context's own stream (a cudaStream_t as void*): the stream that a NULL
+ * cuda_stream selects in every call on this context, and in vrc_batch_*
+ * calls on a batch whose first context this is.  A caller that produces
+ * device rays on another stream orders this one after it (an event and
+ * cudaStreamWaitEvent) before the call that reads them.  Owned by the
+ * context and valid until vrc_destroy; NULL if c is NULL. */
+void *vrc_context_stream(vrc_ctx *c);
+
 /* Zeroes the tally, the counters and the device status (stream-ordered on
  * cuda_stream). */
 int vrc_reset_tally(vrc_ctx *c, void *cuda_stream);
@@ -206,6 +214,43 @@ void vrc_destroy(vrc_ctx *c);
 
 /* Thread-local description of the last error ("" if none). */
 const char *vrc_last_error(void);
+
+/* ---- next-event (point-detector) estimator -----------------------------
+ * Sec. 6 names moving the next-event estimator to the GPU as future work.
+ * For every ray event (position, energy, weight; its direction is not used)
+ * and every detector point, adds wt * exp(-tau) / (4 pi R^2) to
+ * out[detector][group]: isotropic emission, R the distance from the event to
+ * the detector, tau the optical depth along that straight line through the
+ * mesh (vacuum outside).  An event exactly at a detector adds nothing.
+ * Rays: device or host arrays as in vrc_cast_rays.  det_xyz: HOST array of
+ * n_det (1..64) points (float64, rounded to float32 on the device).  out:
+ * HOST array of n_det * n_groups float64, overwritten.  Synchronous.  Does
+ * not touch the tally.  Errors: VRC_ERR_ARG, VRC_ERR_STATE, VRC_ERR_OOM,
+ * VRC_ERR_CUDA; VRC_ERR_TRAVERSAL if a walk hit the step bound. */
+int vrc_detector_flux(vrc_ctx *c, const vrc_rays *r, const double *det_xyz, int32_t n_det,
+                      double *out, void *cuda_stream);
+
+/* ---- tally statistics by batches ---------------------------------------
+ * The figure of merit (Eq. 5) and the fractional difference (Eq. 8) need the
+ * standard deviation of each cell's tally.  The batch method: the caller
+ * casts the rays of one batch of histories (for example one filled ray
+ * buffer), then folds the tally into running sums S1 = sum_b t_b and
+ * S2 = sum_b t_b^2 and clears it.  After B batches the tally total is S1 and
+ * its standard deviation sqrt(B/(B-1) (S2 - S1^2/B)). */
+
+/* Allocates (on != 0) or frees the two float64 moment arrays (tally size
+ * each) and zeroes the batch count. */
+int vrc_moments_enable(vrc_ctx *c, int32_t on);
+
+/* S1 += tally, S2 += tally^2, tally = 0, batch count + 1 (stream-ordered).
+ * VRC_ERR_STATE if moments are not enabled. */
+int vrc_moments_fold(vrc_ctx *c, void *cuda_stream);
+
+/* Synchronous: total = S1 and sigma = sqrt(B/(B-1) (S2 - S1^2/B)) per
+ * (group, cell) into HOST arrays of n = n_groups*nx*ny*nz float64 (sigma may
+ * be NULL; sigma is 0 with fewer than 2 batches); *batches receives B. */
+int vrc_moments_read(vrc_ctx *c, double *total, double *sigma, int64_t n, int64_t *batches,
+                     void *cuda_stream);
 
 /* ---- streaming ray buffers ---------------------------------------------
  * Sec. 3: the CPU random walk stores rays in a buffer; when it is full the

@@ -67,6 +67,8 @@ def _load():
             lib.orc_ray_segments.restype = I64
             lib.orc_cast.argtypes = [P, P, P, I32] + [P] * 8 + [I64, P, I32, P]
             lib.orc_cast.restype = I32
+            lib.orc_point_detector.argtypes = [P, P, P, I32] + [P] * 5 + [I64, P, I32, P]
+            lib.orc_point_detector.restype = I32
             lib.orc_hardware_threads.argtypes = []
             lib.orc_hardware_threads.restype = I32
             _lib = lib
@@ -204,3 +206,36 @@ def cast(problem, nthreads: int = 0, rays: dict | None = None, tally: np.ndarray
         raise MemoryError("oracle allocation failed")
     return tally, dict(segments=int(stats[0]), rejected=int(stats[1]),
                        overflow=int(stats[2]), threads=int(stats[3]))
+
+
+def batch_moments(batch_tallies):
+    """Tally total and its standard deviation by the batch method: with B
+    batch tallies t_b, total = sum_b t_b and sigma = sqrt(B/(B-1) *
+    (sum_b t_b^2 - total^2/B)) (sigma = 0 for B < 2), float64 per cell."""
+    T = np.asarray(batch_tallies, np.float64)
+    B = T.shape[0]
+    total = T.sum(axis=0)
+    if B < 2:
+        return total, np.zeros_like(total)
+    var = (np.sum(T * T, axis=0) - total * total / B) * (B / (B - 1.0))
+    return total, np.sqrt(np.maximum(var, 0.0))
+
+
+def point_detector(problem, detectors, rays: dict | None = None):
+    """Next-event flux at each detector point from every ray event:
+    sum over events of wt exp(-tau)/(4 pi R^2), float64 [n_det][n_groups]."""
+    ctx = _Ctx(problem.mesh, problem.tables)
+    r = problem.rays if rays is None else rays
+    arrs = [np.ascontiguousarray(r[k], np.float32) for k in ("x", "y", "z", "E", "wt")]
+    det = np.ascontiguousarray(detectors, np.float64).reshape(-1, 3)
+    out = np.zeros((det.shape[0], problem.n_groups), np.float64)
+    edges = problem.group_edges
+    keep = None if edges is None else np.ascontiguousarray(edges, np.float64)
+    ep = None if keep is None else _ptr(keep)
+    ng = 0 if keep is None else len(keep) - 1
+    rc = _load().orc_point_detector(C.byref(ctx.mesh), C.byref(ctx.xs), ep, ng,
+                                    *[_ptr(a) for a in arrs], int(arrs[0].shape[0]), _ptr(det),
+                                    det.shape[0], _ptr(out))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return out

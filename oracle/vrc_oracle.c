@@ -395,3 +395,54 @@ int32_t orc_cast(const orc_mesh *m, const orc_xs *xs, const double *edges, int32
   free(th);
   return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* next-event (point-detector) estimator                                */
+/* ------------------------------------------------------------------ */
+
+/* Flux at n_det detector points from every ray event, assuming isotropic
+ * emission: wt * exp(-tau) / (4 pi R^2), with R the distance from the event
+ * to the detector and tau the optical depth along that straight line
+ * (vacuum outside the mesh).  The event direction is not used.  An event
+ * exactly at a detector (R = 0) contributes nothing.  Adds to
+ * out[det][group] (n_det x n_groups, group layout as the tally). */
+int32_t orc_point_detector(const orc_mesh *m, const orc_xs *xs, const double *edges,
+                           int32_t n_groups, const float *x, const float *y, const float *z,
+                           const float *E, const float *wt, int64_t n, const double *det,
+                           int32_t n_det, double *out) {
+  const int64_t cap = (int64_t)m->nx + m->ny + m->nz + 3;
+  const int32_t G = (edges == NULL || n_groups <= 0) ? 1 : n_groups;
+  int64_t *cells = (int64_t *)malloc(sizeof(int64_t) * cap);
+  double *tin = (double *)malloc(sizeof(double) * cap);
+  double *lens = (double *)malloc(sizeof(double) * cap);
+  double *sig = (double *)malloc(sizeof(double) * (xs->n_materials + 1));
+  if (!cells || !tin || !lens || !sig) { free(cells); free(tin); free(lens); free(sig); return -1; }
+  for (int64_t r = 0; r < n; ++r) {
+    if (!isfinite(x[r]) || !isfinite(y[r]) || !isfinite(z[r]) || !isfinite(E[r]) ||
+        !isfinite(wt[r]) || !(E[r] > 0.0f))
+      continue;
+    const int32_t g = orc_group(edges, n_groups, (double)E[r]);
+    if (g < 0) continue;
+    for (int32_t k = 0; k < xs->n_materials; ++k) {
+      const int64_t a = xs->offs[k], b = xs->offs[k + 1];
+      sig[k] = orc_sigma_t(xs->E + a, xs->S + a, b - a, (double)E[r]);
+    }
+    const double p[3] = {x[r], y[r], z[r]};
+    for (int32_t k = 0; k < n_det; ++k) {
+      double d[3] = {det[3 * k] - p[0], det[3 * k + 1] - p[1], det[3 * k + 2] - p[2]};
+      const double R = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      if (!(R > 0.0)) continue;
+      d[0] /= R; d[1] /= R; d[2] /= R;
+      const int64_t ns = orc_trace_dda(m, p, d, cells, tin, lens, cap);
+      double tau = 0.0;
+      for (int64_t s = 0; s < ns; ++s) {
+        if (tin[s] >= R) break;
+        const double l = (tin[s] + lens[s] > R) ? R - tin[s] : lens[s];
+        tau += sig[m->material[cells[s]]] * l;
+      }
+      out[(int64_t)k * G + g] += (double)wt[r] * exp(-tau) / (4.0 * M_PI * R * R);
+    }
+  }
+  free(cells); free(tin); free(lens); free(sig);
+  return 0;
+}

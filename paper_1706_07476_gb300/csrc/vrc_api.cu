@@ -127,6 +127,10 @@ struct vrc_ctx {
   uint32_t mlp_mask = 0;          // outputs the surrogate models (non-void materials)
   double mlp_lo = 0, mlp_hi = 0;  // energy range of the tables
   DevBuf mlpParams, mlpFlags, sigBuf;
+  DevBuf momS1, momS2;  // batch moments of the tally
+  DevBuf detPos, detOut;  // next-event detectors and their flux
+  bool moments = false;
+  int64_t batches = 0;
 
   bool timing = false;
   std::vector<TimedSpan> pending;
@@ -171,6 +175,10 @@ struct vrc_ctx {
     mlpParams.release();
     mlpFlags.release();
     sigBuf.release();
+    momS1.release();
+    momS2.release();
+    detPos.release();
+    detOut.release();
     if (stream) cudaStreamDestroy(stream);
   }
 };
@@ -638,6 +646,8 @@ int vrc_read_tally(vrc_ctx *c, double *out_host, int64_t n, int32_t flags, void 
 }
 
 double *vrc_tally_device_ptr(vrc_ctx *c) { return c ? c->d_tally : nullptr; }
+
+void *vrc_context_stream(vrc_ctx *c) { return c ? static_cast<void *>(c->stream) : nullptr; }
 
 int vrc_reset_tally(vrc_ctx *c, void *cuda_stream) {
   if (!c) return fail(VRC_ERR_ARG, "context is NULL");
@@ -1446,5 +1456,139 @@ int vrc_stream_finish(vrc_stream *s) {
 }
 
 void vrc_stream_destroy(vrc_stream *s) { delete s; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batch moments of the tally.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int vrc_moments_enable(vrc_ctx *c, int32_t on) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  DeviceGuard g(c->device);
+  VRC_CUDA(cudaStreamSynchronize(c->stream), "synchronizing");
+  c->batches = 0;
+  if (!on) {
+    c->momS1.release();
+    c->momS2.release();
+    c->moments = false;
+    return VRC_OK;
+  }
+  const size_t bytes = sizeof(double) * (size_t)(c->ncells * c->n_groups);
+  VRC_CUDA(c->momS1.ensure(bytes), "allocating tally moments");
+  VRC_CUDA(c->momS2.ensure(bytes), "allocating tally moments");
+  VRC_CUDA(cudaMemsetAsync(c->momS1.p, 0, bytes, c->stream), "zeroing tally moments");
+  VRC_CUDA(cudaMemsetAsync(c->momS2.p, 0, bytes, c->stream), "zeroing tally moments");
+  c->moments = true;
+  return VRC_OK;
+}
+
+int vrc_moments_fold(vrc_ctx *c, void *cuda_stream) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  if (!c->moments) return fail(VRC_ERR_STATE, "moments are not enabled");
+  DeviceGuard g(c->device);
+  cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+  VRC_CUDA(launch_fold_moments(c->d_tally, static_cast<double *>(c->momS1.p),
+                               static_cast<double *>(c->momS2.p), c->ncells * c->n_groups, s),
+           "launching the moment fold");
+  c->batches += 1;
+  return VRC_OK;
+}
+
+int vrc_moments_read(vrc_ctx *c, double *total, double *sigma, int64_t n, int64_t *batches,
+                     void *cuda_stream) {
+  if (!c || !total) return fail(VRC_ERR_ARG, "bad arguments");
+  if (!c->moments) return fail(VRC_ERR_STATE, "moments are not enabled");
+  const int64_t N = c->ncells * c->n_groups;
+  if (n != N) return fail(VRC_ERR_ARG, "moment arrays have %lld entries, caller gave %lld", (long long)N, (long long)n);
+  DeviceGuard g(c->device);
+  int rc = sync_streams(c, cuda_stream);
+  if (rc) return rc;
+  VRC_CUDA(cudaMemcpy(total, c->momS1.p, sizeof(double) * N, cudaMemcpyDeviceToHost), "reading S1");
+  if (sigma) {
+    if (c->batches < 2) {
+      std::memset(sigma, 0, sizeof(double) * N);
+    } else {
+      const int64_t chunk = std::min<int64_t>(N, (int64_t)8 << 20);
+      VRC_CUDA(c->scratch.ensure(sizeof(double) * chunk), "allocating moment staging");
+      for (int64_t off = 0; off < N; off += chunk) {
+        const int64_t m = std::min(chunk, N - off);
+        VRC_CUDA(launch_moment_sigma(static_cast<double *>(c->momS1.p) + off,
+                                     static_cast<double *>(c->momS2.p) + off,
+                                     static_cast<double *>(c->scratch.p), m, (double)c->batches, c->stream),
+                 "launching the moment finalize");
+        VRC_CUDA(cudaMemcpyAsync(sigma + off, c->scratch.p, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream),
+                 "reading sigma");
+        VRC_CUDA(cudaStreamSynchronize(c->stream), "reading sigma");
+      }
+    }
+  }
+  if (batches) *batches = c->batches;
+  return VRC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Next-event (point-detector) estimator.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int vrc_detector_flux(vrc_ctx *c, const vrc_rays *r, const double *det_xyz, int32_t n_det,
+                      double *out, void *cuda_stream) {
+  if (!c || !r || !det_xyz || !out) return fail(VRC_ERR_ARG, "bad arguments");
+  if (n_det < 1 || n_det > 64) return fail(VRC_ERR_ARG, "n_det must be in 1..64");
+  if (r->n < 0) return fail(VRC_ERR_ARG, "ray count is negative");
+  const int64_t nout = (int64_t)n_det * c->n_groups;
+  if ((int64_t)n_det * c->n_groups * 8 > 64 * 1024) return fail(VRC_ERR_ARG, "n_det * n_groups too large");
+  for (int i = 0; i < 3 * n_det; ++i)
+    if (!std::isfinite(det_xyz[i])) return fail(VRC_ERR_ARG, "detector position is not finite");
+  if (r->n > 0 && (!r->x || !r->y || !r->z || !r->E || !r->wt)) return fail(VRC_ERR_ARG, "a ray array is NULL");
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(VRC_ERR_CUDA, "cannot select CUDA device %d", c->device);
+  if (c->xs_dirty) {
+    int rc = build_xs(c);
+    if (rc) { c->xs_dirty = true; return rc; }
+  }
+  cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+  std::vector<float> pos(3 * (size_t)n_det);
+  for (int i = 0; i < 3 * n_det; ++i) pos[i] = (float)det_xyz[i];
+  VRC_CUDA(c->detPos.ensure(sizeof(float) * pos.size()), "allocating detectors");
+  VRC_CUDA(c->detOut.ensure(sizeof(double) * nout), "allocating detector flux");
+  VRC_CUDA(cudaMemcpyAsync(c->detPos.p, pos.data(), sizeof(float) * pos.size(), cudaMemcpyHostToDevice, s),
+           "uploading detectors");
+  VRC_CUDA(cudaMemsetAsync(c->detOut.p, 0, sizeof(double) * nout, s), "zeroing detector flux");
+  RayPtrs rp;
+  std::memset(&rp, 0, sizeof rp);
+  rp.n = r->n;
+  if (r->n > 0) {
+    if (r->on_device) {
+      rp.x = r->x; rp.y = r->y; rp.z = r->z; rp.u = r->u; rp.v = r->v; rp.w = r->w; rp.E = r->E; rp.wt = r->wt;
+    } else {
+      const size_t bytes = sizeof(float) * (size_t)r->n;
+      VRC_CUDA(c->stage.ensure(8 * bytes), "allocating ray staging");
+      float *base = static_cast<float *>(c->stage.p);
+      const float *src[5] = {r->x, r->y, r->z, r->E, r->wt};
+      const float **dst[5] = {&rp.x, &rp.y, &rp.z, &rp.E, &rp.wt};
+      for (int k = 0; k < 5; ++k) {
+        float *dk = base + (size_t)k * r->n;
+        VRC_CUDA(cudaMemcpyAsync(dk, src[k], bytes, cudaMemcpyHostToDevice, s), "copying rays");
+        *dst[k] = dk;
+      }
+      rp.u = rp.v = rp.w = rp.x;  // directions are not used
+    }
+    CastArgs a = make_args(c, rp);
+    VRC_CUDA(launch_detectors(c->opt.form, a, static_cast<const float *>(c->detPos.p), n_det,
+                              static_cast<double *>(c->detOut.p), c->num_sms, s),
+             "launching the detector kernel");
+  }
+  VRC_CUDA(cudaMemcpyAsync(out, c->detOut.p, sizeof(double) * nout, cudaMemcpyDeviceToHost, s), "reading detector flux");
+  VRC_CUDA(cudaStreamSynchronize(s), "waiting for the detector kernel");
+  unsigned st = 0;
+  VRC_CUDA(cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost), "reading status");
+  if (st & kStatusTraversal) return status_code(st);
+  return VRC_OK;
+}
 
 }  // extern "C"

@@ -443,4 +443,85 @@ __device__ __forceinline__ void flush_counts(RayCounts c, unsigned long long *co
   }
 }
 
+// Optical depth along the segment p -> q (vacuum outside the mesh) for the
+// next-event estimator: the same double-float grid walk as cast_ray, with the
+// segment parametrised as p + s (q - p), s in [0, 1], and the last cell cut at
+// s = 1.  sg[mat * stride] holds sigma of each material for the ray's energy.
+// Returns tau as a compensated float32 pair.
+__device__ __forceinline__ df optical_depth(const MeshDev &M, const float p[3], const float q[3],
+                                            const float *sg, int stride, bool *overflow) {
+  const float d[3] = {q[0] - p[0], q[1] - p[1], q[2] - p[2]};
+  const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  const df inf = {INFINITY, 0.f};
+  df tau = {0.f, 0.f};
+  df D[3], R[3];
+  df s_in = {0.f, 0.f}, s_out = {1.f, 0.f};
+  bool miss = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    D[k] = df_add_f(M.org[k], -p[k]);
+    const df Dn = df_add(D[k], df_mul_f(M.h[k], (float)M.n[k]));
+    if (d[k] == 0.f) {
+      R[k] = {0.f, 0.f};
+      if (df_pos(D[k]) || !df_pos(Dn)) miss = true;
+    } else {
+      R[k] = df_rcp(d[k]);
+      df a = df_mul(D[k], R[k]);
+      df b = df_mul(Dn, R[k]);
+      if (d[k] < 0.f) { df t = a; a = b; b = t; }
+      if (df_lt(s_in, a)) s_in = a;
+      if (df_lt(b, s_out)) s_out = b;
+    }
+  }
+  if (miss || !df_lt(s_in, s_out)) return tau;
+  df S[3], S0[3], B[3];
+  float m[3];
+  int cst[3];
+  int cell = 0;
+  const int cstride[3] = {1, M.n[0], M.n[0] * M.n[1]};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    df c = df_add_f(df_neg(M.org[k]), p[k]);
+    if (s_in.hi > 0.f && d[k] != 0.f) c = df_add(c, df_mul_f(s_in, d[k]));
+    const int ik = df_floor_clamp(df_mul(c, M.inv_h[k]), M.n[k]);
+    cell += ik * cstride[k];
+    m[k] = 0.f;
+    if (d[k] == 0.f) {
+      S[k] = inf; S0[k] = inf; B[k] = {0.f, 0.f}; cst[k] = 0;
+    } else {
+      const bool fwd = d[k] > 0.f;
+      S0[k] = df_mul(df_add(D[k], df_mul_f(M.h[k], (float)(ik + (fwd ? 1 : 0)))), R[k]);
+      B[k] = df_mul(M.h[k], fwd ? R[k] : df_neg(R[k]));
+      S[k] = S0[k];
+      cst[k] = fwd ? cstride[k] : -cstride[k];
+    }
+  }
+  df s_cur = s_in;
+  const int max_steps = M.n[0] + M.n[1] + M.n[2] + 3;
+  for (int step = 0;; ++step) {
+    const bool y_first = df_lt(S[1], S[0]);
+    df Sk = y_first ? S[1] : S[0];
+    const bool z_first = df_lt(S[2], Sk);
+    if (z_first) Sk = S[2];
+    const int k = z_first ? 2 : (y_first ? 1 : 0);
+    const bool last = !df_lt(Sk, s_out);  // the segment ends (detector or mesh exit) in this cell
+    const df s_end = last ? s_out : Sk;
+    const float l = fmaxf(df_diff(s_end, s_cur), 0.f) * dn;
+    const float sig = sg[__ldg(M.mat + cell) * stride];
+    tau = df_add_f(tau, sig * l);
+    if (last) break;
+    if (step >= max_steps) { *overflow = true; break; }
+    s_cur = Sk;
+    cell += k == 0 ? cst[0] : k == 1 ? cst[1] : cst[2];
+    const float mn = (k == 0 ? m[0] : k == 1 ? m[1] : m[2]) + 1.f;
+    const df Sn = df_add(k == 0 ? S0[0] : k == 1 ? S0[1] : S0[2],
+                         df_mul_f(k == 0 ? B[0] : k == 1 ? B[1] : B[2], mn));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a == k) { m[a] = mn; S[a] = Sn; }
+    }
+  }
+  return tau;
+}
+
 }  // namespace vrc

@@ -85,6 +85,11 @@ cudaError_t launch_batched_cast(int form, const CastArgs *probs, const BatchItem
                                 unsigned int *queue, const BatchShape &sh, int grid, int block,
                                 cudaStream_t s);
 
+// Next-event estimator (vrc_detect.cu): adds every ray's flux at n_det
+// detector points (float [n_det][3]) to out [n_det][n_groups] (device).
+cudaError_t launch_detectors(int form, const CastArgs &a, const float *det, int n_det, double *out,
+                             int num_sms, cudaStream_t s);
+
 // Process-wide count of kernels launched by libvrc (vrc_launch_count).
 void note_launches(int n);
 
@@ -95,5 +100,8 @@ cudaError_t launch_cast(int form, const CastArgs &a, int grid, int block, cudaSt
 cudaError_t cast_occupancy(int form, const CastArgs &a, int block, int *blocks_per_sm);
 cudaError_t launch_scale_copy(const double *src, double *dst, int64_t n, double scale,
                               cudaStream_t s);
+cudaError_t launch_fold_moments(double *tally, double *s1, double *s2, int64_t n, cudaStream_t s);
+cudaError_t launch_moment_sigma(const double *s1, const double *s2, double *sigma, int64_t n, double B,
+                                cudaStream_t s);
 
 }  // namespace vrc

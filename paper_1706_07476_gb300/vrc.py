@@ -75,6 +75,7 @@ def _load():
         "vrc_sync": ([P, P, P], C.c_int),
         "vrc_read_tally": ([P, P, I64, I32, P], C.c_int),
         "vrc_tally_device_ptr": ([P], C.c_void_p),
+        "vrc_context_stream": ([P], C.c_void_p),
         "vrc_reset_tally": ([P, P], C.c_int),
         "vrc_set_options": ([P, P], C.c_int),
         "vrc_destroy": ([P], None),
@@ -84,6 +85,10 @@ def _load():
         "vrc_get_timing": ([P, P, P, P, P, I32], C.c_int),
         "vrc_launch_count": ([], C.c_int64),
         "vrc_sort_rays_static": ([P, P, P, P], C.c_int),
+        "vrc_detector_flux": ([P, P, P, I32, P, P], C.c_int),
+        "vrc_moments_enable": ([P, I32], C.c_int),
+        "vrc_moments_fold": ([P, P], C.c_int),
+        "vrc_moments_read": ([P, P, P, I64, P, P], C.c_int),
         "vrc_stream_create": ([P, I64, I32, P], C.c_int),
         "vrc_stream_acquire": ([P, P, P], C.c_int),
         "vrc_stream_submit": ([P, I64], C.c_int),
@@ -166,7 +171,7 @@ class Context:
         self.ncells = ncells
         self.n_groups = n_groups
         self.spacing = spacing
-        self._keep = []
+        self._inflight = []
 
     @property
     def tally_size(self):
@@ -176,6 +181,7 @@ class Context:
         if self.handle:
             _lib.vrc_destroy(self.handle)
             self.handle = None
+        self._inflight = []
 
     def __del__(self):
         try:
@@ -215,6 +221,38 @@ def vrc_load_xs(ctx: Context, material: int, E, sigma):
     _check(_lib.vrc_load_xs(ctx.handle, int(material), E.ctypes.data, S.ctypes.data, len(E)))
 
 
+def vrc_context_stream(ctx: Context) -> int:
+    return int(_lib.vrc_context_stream(ctx.handle) or 0)
+
+
+def _order_device_inputs(ctx: Context, stream, tensors):
+    """Makes the stream a library call runs on wait for torch's current stream
+    (which produced the device tensors).  Returns the device tensors."""
+    dev = [t for t in tensors if not isinstance(t, np.ndarray) and t.is_cuda]
+    if dev:
+        import torch
+        handle = _stream_handle(stream) or vrc_context_stream(ctx)
+        cur = torch.cuda.current_stream(dev[0].device)
+        if handle != cur.cuda_stream:
+            torch.cuda.ExternalStream(handle, device=dev[0].device).wait_stream(cur)
+    return dev
+
+
+def _hold_until_done(ctx: Context, stream, dev):
+    """Keeps device inputs referenced until the stream has passed the call just
+    enqueued, so the caching allocator cannot hand their memory to a later
+    producer while the library still reads it.  Entries are dropped once their
+    event completes, and all of them when the context is closed (vrc_destroy
+    waits for the context's stream)."""
+    ctx._inflight = [(e, t) for e, t in ctx._inflight if not e.query()]
+    if dev:
+        import torch
+        handle = _stream_handle(stream) or vrc_context_stream(ctx)
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.ExternalStream(handle, device=dev[0].device))
+        ctx._inflight.append((ev, dev))
+
+
 def _ray_struct(rays: dict):
     arrs = [rays[k] for k in RAY_FIELDS]
     keep = []
@@ -243,16 +281,19 @@ def _ray_struct(rays: dict):
 
 def vrc_cast_rays(ctx: Context, rays: dict, stream=None):
     r, keep = _ray_struct(rays)
+    dev = _order_device_inputs(ctx, stream, keep)
     _check(_lib.vrc_cast_rays(ctx.handle, C.byref(r), _stream_handle(stream)))
-    ctx._keep = keep  # device arrays stay referenced until the next cast
+    _hold_until_done(ctx, stream, dev)
 
 
 def vrc_sort_rays_static(ctx: Context, rays: dict, out, stream=None):
     """No-allocation ray sort: device rays in; `out` is a caller-owned device
     float32 tensor of 8*n elements receiving x, y, z, u, v, w, E, wt blocks."""
     r, keep = _ray_struct(rays)
+    dev = _order_device_inputs(ctx, stream, keep + ([] if out is None else [out]))
     ptr = None if out is None else out.data_ptr()
     _check(_lib.vrc_sort_rays_static(ctx.handle, C.byref(r), ptr, _stream_handle(stream)))
+    _hold_until_done(ctx, stream, dev)
 
 
 VRC_MLP_PARAMS = 26896
@@ -312,6 +353,35 @@ def vrc_get_surrogate_params(ctx: Context) -> np.ndarray:
     out = np.empty(VRC_MLP_PARAMS, np.float32)
     _check(_lib.vrc_get_surrogate_params(ctx.handle, out.ctypes.data))
     return out
+
+
+def vrc_detector_flux(ctx: Context, rays: dict, detectors, stream=None) -> np.ndarray:
+    """Next-event flux at each detector, float64 [n_det][n_groups]."""
+    r, keep = _ray_struct(rays)
+    det = np.ascontiguousarray(detectors, np.float64).reshape(-1, 3)
+    out = np.empty((det.shape[0], ctx.n_groups), np.float64)
+    _order_device_inputs(ctx, stream, keep)
+    _check(_lib.vrc_detector_flux(ctx.handle, C.byref(r), det.ctypes.data, det.shape[0],
+                                  out.ctypes.data, _stream_handle(stream)))
+    return out
+
+
+def vrc_moments_enable(ctx: Context, on: bool = True):
+    _check(_lib.vrc_moments_enable(ctx.handle, int(bool(on))))
+
+
+def vrc_moments_fold(ctx: Context, stream=None):
+    _check(_lib.vrc_moments_fold(ctx.handle, _stream_handle(stream)))
+
+
+def vrc_moments_read(ctx: Context, stream=None):
+    """Returns (total, sigma, batches) as host float64 arrays."""
+    total = np.empty(ctx.tally_size, np.float64)
+    sigma = np.empty(ctx.tally_size, np.float64)
+    b = C.c_int64()
+    _check(_lib.vrc_moments_read(ctx.handle, total.ctypes.data, sigma.ctypes.data, total.size,
+                                 C.byref(b), _stream_handle(stream)))
+    return total, sigma, b.value
 
 
 class RayStream:
@@ -412,6 +482,8 @@ def vrc_batch_create(ctxs, rays_list, options: vrc_batch_options | None = None) 
 
 
 def vrc_batch_launch(batch: Batch, stream=None):
+    # the Batch holds its rays and vrc_batch_destroy waits for its stream
+    _order_device_inputs(batch.ctxs[0], stream, batch._keep[2][0] if batch._keep[2] else [])
     _check(_lib.vrc_batch_launch(batch.handle, _stream_handle(stream)))
 
 
@@ -422,6 +494,7 @@ def vrc_batch_destroy(batch: Batch):
 def vrc_cast_batched(ctxs, rays_list, stream=None):
     carr = _ctx_array(ctxs)
     rarr, keep = _rays_array(rays_list)
+    _order_device_inputs(ctxs[0], stream, [t for k in keep for t in k])
     _check(_lib.vrc_cast_batched(carr, rarr, len(ctxs), _stream_handle(stream)))
 
 

@@ -371,3 +371,52 @@ def test_uniform_workload_segment_count_and_scale():
     assert st["rejected"] == 0 and st["overflow"] == 0
     assert 2.7e6 < st["segments"] < 3.1e6
     assert np.all(tal > 0)
+
+
+def test_batch_moments_closed_forms():
+    """Two batches: sigma = |t1 - t2| (B/(B-1) (t1^2 + t2^2 - (t1+t2)^2/2) =
+    (t1 - t2)^2); equal batches: sigma = 0; one batch: sigma = 0."""
+    t1 = np.array([1.0, 3.0, 0.0, 2.5])
+    t2 = np.array([2.0, 3.0, 5.0, 0.5])
+    total, sig = oracle.batch_moments([t1, t2])
+    np.testing.assert_allclose(total, t1 + t2)
+    np.testing.assert_allclose(sig, np.abs(t1 - t2), rtol=1e-14, atol=1e-14)
+    total, sig = oracle.batch_moments([t1, t1, t1])
+    np.testing.assert_allclose(sig, 0.0, atol=1e-14)
+    _, sig = oracle.batch_moments([t1])
+    assert not sig.any()
+    # sigma scales with sqrt(B) for B copies of the same two-valued spread
+    a, b = np.array([1.0]), np.array([3.0])
+    _, s4 = oracle.batch_moments([a, b, a, b])
+    assert s4[0] == pytest.approx(np.sqrt(4 / 3 * (20 - 64 / 4)), rel=1e-14)
+
+
+def test_point_detector_closed_forms():
+    """Homogeneous medium: exp(-Sigma R)/(4 pi R^2) per unit weight; void: the
+    bare 1/(4 pi R^2); a detector outside the mesh sees only the chord inside
+    (vacuum outside); groups route by energy."""
+    mesh = _mesh((4, 4, 4))
+    sig = 0.7
+    ev = _rays([[1.25, 2.0, 2.5], [3.5, 0.5, 0.5]], [[1, 0, 0], [0, 1, 0]], [1.0, 1e6], [2.0, 0.5])
+    det = np.array([[3.0, 2.0, 2.5], [1.0, 3.0, 3.0]])
+    prob = W.Problem("pd", mesh, [_const_table(sig)], np.array([1e-5, 10.0, 2e7]), ev)
+    got = oracle.point_detector(prob, det)
+    p = np.stack([ev["x"], ev["y"], ev["z"]], 1).astype(np.float64)
+    want = np.zeros((2, 2))
+    for i, g in enumerate([0, 1]):
+        for k in range(2):
+            R = np.linalg.norm(det[k] - p[i])
+            want[k, g] += float(ev["wt"][i]) * np.exp(-sig * R) / (4 * np.pi * R * R)
+    np.testing.assert_allclose(got, want, rtol=1e-13)
+    # void: no attenuation
+    vprob = W.Problem("pdv", mesh, [None], None, ev)
+    got = oracle.point_detector(vprob, det)
+    R = np.linalg.norm(det[None, :, :] - p[:, None, :], axis=2)
+    np.testing.assert_allclose(got[:, 0], (ev["wt"].astype(np.float64)[:, None] / (4 * np.pi * R ** 2)).sum(0),
+                               rtol=1e-13)
+    # detector 2 cm beyond the +x face: attenuation only over the 4 - 1.25 cm inside
+    far = np.array([[6.0, 2.0, 2.5]])
+    one = W.Problem("pdf", mesh, [_const_table(sig)], None, W.take_rays(prob, [0]).rays)
+    got = oracle.point_detector(one, far)
+    R = 6.0 - 1.25
+    assert got[0, 0] == pytest.approx(2.0 * np.exp(-sig * (4.0 - 1.25)) / (4 * np.pi * R * R), rel=1e-13)
