@@ -221,6 +221,31 @@ def batch_moments(batch_tallies):
     return total, np.sqrt(np.maximum(var, 0.0))
 
 
+def history_moments(problem, history, n_histories: int, rays: dict | None = None):
+    """Per-history moments behind the sigma of Eqs. 5 and 8: x_h = the tally of
+    the rays of history h (every ray with that id), total = sum_h x_h and
+    sigma = sqrt(N/(N-1) (sum_h x_h^2 - total^2/N)) with N = n_histories;
+    histories without rays count as zero scores.  Returns (total, sigma, S2),
+    float64 per cell, S2 = sum_h x_h^2."""
+    r = problem.rays if rays is None else rays
+    hist = np.asarray(history).reshape(-1)
+    ids = np.unique(hist)
+    N = int(n_histories)
+    if len(ids) > N:
+        raise ValueError("more distinct history ids than n_histories")
+    s1 = np.zeros(problem.tally_size, np.float64)
+    s2 = np.zeros(problem.tally_size, np.float64)
+    for h in ids:
+        sel = np.flatnonzero(hist == h)
+        x, _ = cast(problem, nthreads=1, rays={k: np.asarray(v)[sel] for k, v in r.items()})
+        s1 += x
+        s2 += x * x
+    if N < 2:
+        return s1, np.zeros_like(s1), s2
+    var = (s2 - s1 * s1 / N) * (N / (N - 1.0))
+    return s1, np.sqrt(np.maximum(var, 0.0)), s2
+
+
 def point_detector(problem, detectors, rays: dict | None = None):
     """Next-event flux at each detector point from every ray event:
     sum over events of wt exp(-tau)/(4 pi R^2), float64 [n_det][n_groups]."""

@@ -420,3 +420,30 @@ def test_point_detector_closed_forms():
     got = oracle.point_detector(one, far)
     R = 6.0 - 1.25
     assert got[0, 0] == pytest.approx(2.0 * np.exp(-sig * (4.0 - 1.25)) / (4 * np.pi * R * R), rel=1e-13)
+
+
+def test_history_moments_closed_form():
+    """Void 4x1x1 mesh, rays along +x from x = 0.5: chord 0.5 in cell 0 and 1
+    in cells 1..3, times wt.  History 7 has two rays (wt 1 and 2), history 3
+    one ray (wt 1), and one more history has no ray (N = 3).  Then
+    x_7 = 3 l, x_3 = l per cell, S1 = 4 l, S2 = 10 l^2 and
+    sigma^2 = 3/2 (10 - 16/3) l^2 = 7 l^2.  Squaring ray by ray instead of
+    history by history would give S2 = 6 l^2 and sigma = l."""
+    mesh = _mesh((4, 1, 1))
+    ev = _rays([[0.5, 0.5, 0.5]] * 3, [[1, 0, 0]] * 3, 1.0, [1.0, 2.0, 1.0])
+    prob = W.Problem("hist", mesh, [None], None, ev)
+    l = np.array([0.5, 1.0, 1.0, 1.0])
+    total, sig, s2 = oracle.history_moments(prob, np.array([7, 7, 3], np.uint32), 3)
+    np.testing.assert_allclose(total, 4 * l, rtol=1e-15)
+    np.testing.assert_allclose(s2, 10 * l * l, rtol=1e-15)
+    np.testing.assert_allclose(sig, np.sqrt(7.0) * l, rtol=1e-14)
+    # the same rays with N = 2 (no empty history): sigma^2 = 2 (10 - 8) l^2
+    _, sig2, _ = oracle.history_moments(prob, np.array([7, 7, 3], np.uint32), 2)
+    np.testing.assert_allclose(sig2, 2.0 * l, rtol=1e-14)
+    # ray order and id values do not matter, only which rays share an id
+    perm = [2, 0, 1]
+    rays = {k: v[perm] for k, v in ev.items()}
+    _, sig3, _ = oracle.history_moments(prob, np.array([1, 9, 9], np.uint32), 3, rays=rays)
+    np.testing.assert_allclose(sig3, sig, rtol=1e-15)
+    with pytest.raises(ValueError):
+        oracle.history_moments(prob, np.array([1, 2, 3], np.uint32), 2)
