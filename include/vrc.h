@@ -230,26 +230,57 @@ const char *vrc_last_error(void);
 int vrc_detector_flux(vrc_ctx *c, const vrc_rays *r, const double *det_xyz, int32_t n_det,
                       double *out, void *cuda_stream);
 
-/* ---- tally statistics by batches ---------------------------------------
+/* ---- tally statistics: batches or histories ----------------------------
  * The figure of merit (Eq. 5) and the fractional difference (Eq. 8) need the
- * standard deviation of each cell's tally.  The batch method: the caller
- * casts the rays of one batch of histories (for example one filled ray
- * buffer), then folds the tally into running sums S1 = sum_b t_b and
- * S2 = sum_b t_b^2 and clears it.  After B batches the tally total is S1 and
- * its standard deviation sqrt(B/(B-1) (S2 - S1^2/B)). */
+ * standard deviation of each cell's tally.  Two ways to get it, both ending
+ * in running sums S1 = sum_b x_b and S2 = sum_b x_b^2 over B samples, after
+ * which the tally total is S1 and its standard deviation
+ * sqrt(B/(B-1) (S2 - S1^2/B)):
+ *  - VRC_MOMENTS_BATCH: a sample is the tally of one batch of histories.  The
+ *    caller casts one batch (for example one filled ray buffer) with
+ *    vrc_cast_rays, then vrc_moments_fold moves the tally into S1/S2.
+ *  - VRC_MOMENTS_HISTORY: a sample is one history's score x_h.  Each ray
+ *    carries the id of its history; vrc_cast_histories sums the scores of a
+ *    history's rays per cell and adds x_h to S1 and x_h^2 to S2.  With the
+ *    1/N of Eq. 4 folded into wt, this sigma is the usual Monte Carlo
+ *    standard deviation of the tally mean over N histories. */
+#define VRC_MOMENTS_OFF 0
+#define VRC_MOMENTS_BATCH 1
+#define VRC_MOMENTS_HISTORY 2
 
-/* Allocates (on != 0) or frees the two float64 moment arrays (tally size
- * each) and zeroes the batch count. */
-int vrc_moments_enable(vrc_ctx *c, int32_t on);
+/* Allocates (mode BATCH or HISTORY) or frees (OFF) the two float64 moment
+ * arrays (tally size each) and zeroes them and the sample count.  Waits for
+ * the context's stream.  VRC_ERR_ARG for another mode. */
+int vrc_moments_enable(vrc_ctx *c, int32_t mode);
 
-/* S1 += tally, S2 += tally^2, tally = 0, batch count + 1 (stream-ordered).
- * VRC_ERR_STATE if moments are not enabled. */
+/* S1 += tally, S2 += tally^2, tally = 0, sample count + 1 (stream-ordered).
+ * VRC_ERR_STATE unless the mode is VRC_MOMENTS_BATCH. */
 int vrc_moments_fold(vrc_ctx *c, void *cuda_stream);
+
+/* Per-history cast (mode VRC_MOMENTS_HISTORY, else VRC_ERR_STATE).
+ * history[i] (uint32) is the history of ray i, on the same side as the rays
+ * (device if r->on_device, else host); the rays of one history may sit
+ * anywhere in the call, but a history must not continue in a later call.
+ * n_histories is the number of histories the call completes, counting those
+ * without rays (their score is zero); it is added to the sample count.
+ * Scores go to S1/S2 only: the tally is untouched.  The tabulated cross
+ * sections are used (not the surrogate) and the rays are not sorted.
+ * Needs (group count x cells) < 2^32 - 1.  Device scratch: a table of
+ * 16-byte slots sized to twice an upper bound of the call's segments, kept
+ * for later calls; VRC_ERR_OOM when it does not fit (split the call).  The
+ * call waits for that bound (one small device-to-host read); the cast and
+ * the fold into S1/S2 are then queued on cuda_stream (NULL = the context's
+ * stream).  Host arrays may be reused on return; device arrays must stay
+ * valid until the stream passes the call. */
+int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, int64_t n_histories,
+                       void *cuda_stream);
 
 /* Synchronous: total = S1 and sigma = sqrt(B/(B-1) (S2 - S1^2/B)) per
  * (group, cell) into HOST arrays of n = n_groups*nx*ny*nz float64 (sigma may
- * be NULL; sigma is 0 with fewer than 2 batches); *batches receives B. */
-int vrc_moments_read(vrc_ctx *c, double *total, double *sigma, int64_t n, int64_t *batches,
+ * be NULL; sigma is 0 with fewer than 2 samples); *samples receives B (the
+ * batch or history count).  Reports a per-history table overflow as
+ * VRC_ERR_OOM. */
+int vrc_moments_read(vrc_ctx *c, double *total, double *sigma, int64_t n, int64_t *samples,
                      void *cuda_stream);
 
 /* ---- streaming ray buffers ---------------------------------------------

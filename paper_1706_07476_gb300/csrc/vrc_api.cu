@@ -127,10 +127,15 @@ struct vrc_ctx {
   uint32_t mlp_mask = 0;          // outputs the surrogate models (non-void materials)
   double mlp_lo = 0, mlp_hi = 0;  // energy range of the tables
   DevBuf mlpParams, mlpFlags, sigBuf;
-  DevBuf momS1, momS2;  // batch moments of the tally
+  DevBuf momS1, momS2;  // moments of the tally: sums of samples and of their squares
   DevBuf detPos, detOut;  // next-event detectors and their flux
   bool moments = false;
-  int64_t batches = 0;
+  int moment_mode = VRC_MOMENTS_OFF;
+  int64_t batches = 0;    // samples folded into the moments (batches or histories)
+  DevBuf histTab;         // per-history table, histCap slots of 16 bytes, all zero between calls
+  unsigned long long histCap = 0;
+  DevBuf histIds;         // device copy of host history ids
+  DevBuf histBound;       // segment bound of the current call
 
   bool timing = false;
   std::vector<TimedSpan> pending;
@@ -177,6 +182,9 @@ struct vrc_ctx {
     sigBuf.release();
     momS1.release();
     momS2.release();
+    histTab.release();
+    histIds.release();
+    histBound.release();
     detPos.release();
     detOut.release();
     if (stream) cudaStreamDestroy(stream);
@@ -297,6 +305,8 @@ CastArgs make_args(const vrc_ctx *c, const RayPtrs &rays) {
 }
 
 int status_code(unsigned st) {
+  if (st & kStatusTableFull)
+    return fail(VRC_ERR_OOM, "the per-history table overflowed; its scores are incomplete");
   if (st & kStatusTraversal)
     return fail(VRC_ERR_TRAVERSAL, "a ray needed more grid steps than the mesh allows");
   if (st & kStatusNonfinite)
@@ -412,6 +422,31 @@ int cast_device(vrc_ctx *c, RayPtrs rp, cudaStream_t s) {
     c->pending.push_back(span);
     c->cast_launches += 1;
   }
+  return VRC_OK;
+}
+
+// Device view of a ray batch: device arrays as given, host arrays copied
+// into the context's staging buffer on stream s.
+int ray_ptrs(vrc_ctx *c, const vrc_rays *r, cudaStream_t s, RayPtrs *out) {
+  RayPtrs rp;
+  rp.aos = nullptr;
+  rp.n = r->n;
+  if (r->on_device) {
+    rp.x = r->x; rp.y = r->y; rp.z = r->z; rp.u = r->u;
+    rp.v = r->v; rp.w = r->w; rp.E = r->E; rp.wt = r->wt;
+  } else {
+    const size_t bytes = sizeof(float) * (size_t)r->n;
+    VRC_CUDA(c->stage.ensure(8 * bytes), "allocating ray staging");
+    float *base = static_cast<float *>(c->stage.p);
+    const float *src[8] = {r->x, r->y, r->z, r->u, r->v, r->w, r->E, r->wt};
+    const float **dst[8] = {&rp.x, &rp.y, &rp.z, &rp.u, &rp.v, &rp.w, &rp.E, &rp.wt};
+    for (int k = 0; k < 8; ++k) {
+      float *dk = base + (size_t)k * r->n;
+      VRC_CUDA(cudaMemcpyAsync(dk, src[k], bytes, cudaMemcpyHostToDevice, s), "copying rays to the device");
+      *dst[k] = dk;
+    }
+  }
+  *out = rp;
   return VRC_OK;
 }
 
@@ -562,22 +597,9 @@ int vrc_cast_rays(vrc_ctx *c, const vrc_rays *r, void *cuda_stream) {
   }
   cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
   RayPtrs rp;
-  rp.aos = nullptr;
-  rp.n = r->n;
-  if (r->on_device) {
-    rp.x = r->x; rp.y = r->y; rp.z = r->z; rp.u = r->u;
-    rp.v = r->v; rp.w = r->w; rp.E = r->E; rp.wt = r->wt;
-  } else {
-    const size_t bytes = sizeof(float) * (size_t)r->n;
-    VRC_CUDA(c->stage.ensure(8 * bytes), "allocating ray staging");
-    float *base = static_cast<float *>(c->stage.p);
-    const float *src[8] = {r->x, r->y, r->z, r->u, r->v, r->w, r->E, r->wt};
-    const float **dst[8] = {&rp.x, &rp.y, &rp.z, &rp.u, &rp.v, &rp.w, &rp.E, &rp.wt};
-    for (int k = 0; k < 8; ++k) {
-      float *dk = base + (size_t)k * r->n;
-      VRC_CUDA(cudaMemcpyAsync(dk, src[k], bytes, cudaMemcpyHostToDevice, s), "copying rays to the device");
-      *dst[k] = dk;
-    }
+  {
+    int rc = ray_ptrs(c, r, s, &rp);
+    if (rc) return rc;
   }
   cudaEvent_t uploaded = nullptr;
   if (!r->on_device) {
@@ -1464,14 +1486,19 @@ void vrc_stream_destroy(vrc_stream *s) { delete s; }
 // ---------------------------------------------------------------------------
 extern "C" {
 
-int vrc_moments_enable(vrc_ctx *c, int32_t on) {
+int vrc_moments_enable(vrc_ctx *c, int32_t mode) {
   if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  if (mode != VRC_MOMENTS_OFF && mode != VRC_MOMENTS_BATCH && mode != VRC_MOMENTS_HISTORY)
+    return fail(VRC_ERR_ARG, "unknown moments mode %d", mode);
   DeviceGuard g(c->device);
   VRC_CUDA(cudaStreamSynchronize(c->stream), "synchronizing");
   c->batches = 0;
-  if (!on) {
+  c->moment_mode = mode;
+  if (mode == VRC_MOMENTS_OFF) {
     c->momS1.release();
     c->momS2.release();
+    c->histTab.release();
+    c->histCap = 0;
     c->moments = false;
     return VRC_OK;
   }
@@ -1487,12 +1514,99 @@ int vrc_moments_enable(vrc_ctx *c, int32_t on) {
 int vrc_moments_fold(vrc_ctx *c, void *cuda_stream) {
   if (!c) return fail(VRC_ERR_ARG, "context is NULL");
   if (!c->moments) return fail(VRC_ERR_STATE, "moments are not enabled");
+  if (c->moment_mode != VRC_MOMENTS_BATCH) return fail(VRC_ERR_STATE, "moments are per history, not per batch");
   DeviceGuard g(c->device);
   cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
   VRC_CUDA(launch_fold_moments(c->d_tally, static_cast<double *>(c->momS1.p),
                                static_cast<double *>(c->momS2.p), c->ncells * c->n_groups, s),
            "launching the moment fold");
   c->batches += 1;
+  return VRC_OK;
+}
+
+int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, int64_t n_histories,
+                       void *cuda_stream) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  if (!r) return fail(VRC_ERR_ARG, "rays is NULL");
+  if (r->n < 0 || n_histories < 0) return fail(VRC_ERR_ARG, "negative ray or history count");
+  if (!c->moments || c->moment_mode != VRC_MOMENTS_HISTORY)
+    return fail(VRC_ERR_STATE, "per-history moments are not enabled");
+  if (c->ncells * c->n_groups >= (int64_t)0xffffffff)
+    return fail(VRC_ERR_ARG, "per-history moments need fewer than 2^32 - 1 (group, cell) bins");
+  if (r->n > 0 && (!history || !r->x || !r->y || !r->z || !r->u || !r->v || !r->w || !r->E || !r->wt))
+    return fail(VRC_ERR_ARG, "a ray or history array is NULL");
+  if (r->n == 0) {
+    c->batches += n_histories;
+    return VRC_OK;
+  }
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(VRC_ERR_CUDA, "cannot select CUDA device %d", c->device);
+  if (c->xs_dirty) {
+    int rc = build_xs(c);
+    if (rc) {
+      c->xs_dirty = true;
+      return rc;
+    }
+  }
+  cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+  RayPtrs rp;
+  {
+    int rc = ray_ptrs(c, r, s, &rp);
+    if (rc) return rc;
+  }
+  const uint32_t *hist = history;
+  if (!r->on_device) {
+    VRC_CUDA(c->histIds.ensure(sizeof(uint32_t) * (size_t)r->n), "allocating history staging");
+    VRC_CUDA(cudaMemcpyAsync(c->histIds.p, history, sizeof(uint32_t) * (size_t)r->n, cudaMemcpyHostToDevice, s),
+             "copying history ids to the device");
+    hist = static_cast<const uint32_t *>(c->histIds.p);
+  }
+  // table size: twice an upper bound of the call's segments, a power of two
+  BoundGeom G;
+  for (int k = 0; k < 3; ++k) {
+    G.lo[k] = c->org[k];
+    G.h[k] = c->h[k];
+    G.n[k] = c->n[k];
+  }
+  VRC_CUDA(c->histBound.ensure(sizeof(unsigned long long)), "allocating the segment bound");
+  unsigned long long *d_bound = static_cast<unsigned long long *>(c->histBound.p);
+  VRC_CUDA(cudaMemsetAsync(d_bound, 0, sizeof(unsigned long long), s), "zeroing the segment bound");
+  VRC_CUDA(launch_segment_bound(G, rp, d_bound, c->num_sms, s), "launching the segment bound");
+  unsigned long long bound = 0;
+  VRC_CUDA(cudaMemcpyAsync(&bound, d_bound, sizeof bound, cudaMemcpyDeviceToHost, s), "reading the segment bound");
+  VRC_CUDA(cudaStreamSynchronize(s), "waiting for the segment bound");  // host arrays are free from here
+  unsigned long long cap = 1024;
+  while (cap < 2 * bound) cap <<= 1;
+  if (cap > c->histCap) {
+    c->histTab.release();
+    c->histCap = 0;
+    size_t free_b = 0, total_b = 0;
+    VRC_CUDA(cudaMemGetInfo(&free_b, &total_b), "querying device memory");
+    const unsigned long long bytes = 16ull * cap;
+    if (bytes > free_b / 10 * 9)
+      return fail(VRC_ERR_OOM, "this call's histories need a %.1f GB table (%.1f GB free); split the call",
+                  bytes / 1e9, free_b / 1e9);
+    VRC_CUDA(c->histTab.ensure(bytes), "allocating the per-history table");
+    VRC_CUDA(cudaMemsetAsync(c->histTab.p, 0, bytes, s), "clearing the per-history table");
+    c->histCap = cap;
+  }
+  CastArgs a = make_args(c, rp);
+  a.hist = hist;
+  a.htab.e = static_cast<unsigned long long *>(c->histTab.p);
+  a.htab.mask = cap - 1;
+  const int form = c->opt.form;
+  const int block = c->opt.block > 0 ? c->opt.block : 256;
+  int bps = c->opt.blocks_per_sm;
+  if (bps <= 0) {
+    VRC_CUDA(cast_hist_occupancy(form, a, block, &bps), "querying occupancy");
+    if (bps <= 0) return fail(VRC_ERR_ARG, "cast kernel does not fit on an SM with %d materials", c->n_materials);
+  }
+  const int grid = (int)std::min<int64_t>((rp.n + block - 1) / block, (int64_t)c->num_sms * bps);
+  VRC_CUDA(launch_cast_hist(form, a, grid, block, s), "launching the per-history cast");
+  VRC_CUDA(launch_hist_drain(a.htab, static_cast<double *>(c->momS1.p), static_cast<double *>(c->momS2.p),
+                             c->num_sms, s),
+           "launching the per-history fold");
+  c->batches += n_histories;
   return VRC_OK;
 }
 
@@ -1525,7 +1639,9 @@ int vrc_moments_read(vrc_ctx *c, double *total, double *sigma, int64_t n, int64_
     }
   }
   if (batches) *batches = c->batches;
-  return VRC_OK;
+  unsigned st = 0;
+  VRC_CUDA(cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost), "reading status");
+  return (st & kStatusTableFull) ? status_code(kStatusTableFull) : VRC_OK;
 }
 
 }  // extern "C"

@@ -38,7 +38,7 @@ SmemLayout smem_layout(int form, const CastArgs &a, int block) {
   return L;
 }
 
-template <int FORM, bool SURR>
+template <int FORM, bool SURR, typename Maker = TallyMaker>
 __global__ void __launch_bounds__(256, 4) k_cast(CastArgs a, SmemLayout L) {
   typedef typename Attenuation<FORM>::inv_t inv_t;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256, 4) k_cast(CastArgs a, SmemLayout L) {
   RayCounts cnt;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.rays.n;
        r += (int64_t)gridDim.x * blockDim.x)
-    cast_one<FORM, SURR>(a, r, hash_s, edges, sig_s, inv_s, stride, cnt);
+    cast_one<FORM, SURR, Maker>(a, r, hash_s, edges, sig_s, inv_s, stride, cnt);
   flush_counts(cnt, a.counters, a.status);
 }
 
@@ -116,20 +116,20 @@ size_t cast_smem_bytes(int form, const CastArgs &a, int block) {
   return smem_layout(form, a, block).total;
 }
 
-template <int FORM, bool SURR>
+template <int FORM, bool SURR, typename Maker = TallyMaker>
 cudaError_t occupancy_t(const CastArgs &a, int block, int *bps) {
   const size_t smem = cast_smem_bytes(FORM, a, block);
-  cudaError_t e = cudaFuncSetAttribute(k_cast<FORM, SURR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_cast<FORM, SURR, Maker>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_cast<FORM, SURR>, block, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_cast<FORM, SURR, Maker>, block, smem);
 }
 
-template <int FORM, bool SURR>
+template <int FORM, bool SURR, typename Maker = TallyMaker>
 cudaError_t launch_t(const CastArgs &a, int grid, int block, cudaStream_t s) {
   const SmemLayout L = smem_layout(FORM, a, block);
-  cudaError_t e = cudaFuncSetAttribute(k_cast<FORM, SURR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  cudaError_t e = cudaFuncSetAttribute(k_cast<FORM, SURR, Maker>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
   if (e != cudaSuccess) return e;
-  k_cast<FORM, SURR><<<grid, block, L.total, s>>>(a, L);
+  k_cast<FORM, SURR, Maker><<<grid, block, L.total, s>>>(a, L);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -146,6 +146,18 @@ cudaError_t launch_cast(int form, const CastArgs &a, int grid, int block, cudaSt
   if (form == kFormPlain)
     return surr ? launch_t<kFormPlain, true>(a, grid, block, s) : launch_t<kFormPlain, false>(a, grid, block, s);
   return surr ? launch_t<kFormFp32, true>(a, grid, block, s) : launch_t<kFormFp32, false>(a, grid, block, s);
+}
+
+// Per-history cast: the same kernel with the history table as the sink
+// (tabulated cross sections; the ray order is the caller's).
+cudaError_t cast_hist_occupancy(int form, const CastArgs &a, int block, int *blocks_per_sm) {
+  if (form == kFormPlain) return occupancy_t<kFormPlain, false, HistMaker>(a, block, blocks_per_sm);
+  return occupancy_t<kFormFp32, false, HistMaker>(a, block, blocks_per_sm);
+}
+
+cudaError_t launch_cast_hist(int form, const CastArgs &a, int grid, int block, cudaStream_t s) {
+  if (form == kFormPlain) return launch_t<kFormPlain, false, HistMaker>(a, grid, block, s);
+  return launch_t<kFormFp32, false, HistMaker>(a, grid, block, s);
 }
 
 cudaError_t launch_scale_copy(const double *src, double *dst, int64_t n, double scale,

@@ -240,8 +240,69 @@ struct Attenuation<kFormFp32> {
   __device__ __forceinline__ static double to_double(float s) { return f2d_bits(s); }
 };
 
+// ---------------------------------------------------------------------------
+// Score sinks: where the walk puts each segment's score.
+// ---------------------------------------------------------------------------
+// The tally: one float64 atomic add into the ray's group slice.
+struct TallySink {
+  double *tal;
+  __device__ __forceinline__ void add(int cell, double v) const { atomicAdd(tal + cell, v); }
+};
+
+// Finalizer of SplitMix64 (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014): a bijective 64-bit mix.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// The per-history table: the score of (history, bin) is summed in one slot,
+// found by linear probing from mix64(key); the first writer claims an empty
+// slot with a compare-and-swap.  At most cap probes; a full table sets
+// kStatusTableFull and drops the score (the host sizes the table at twice an
+// upper bound of the segments, so this does not happen in practice).
+struct HistSink {
+  HistTable t;
+  unsigned long long base;  // (history << 32) + group * ncells + 1
+  unsigned int *status;
+  __device__ __forceinline__ void add(int cell, double v) const {
+    const unsigned long long key = base + (unsigned)cell;
+    unsigned long long i = mix64(key) & t.mask;
+    for (unsigned long long probe = 0; probe <= t.mask; ++probe) {
+      unsigned long long *slot = t.e + 2 * i;
+      unsigned long long k = *reinterpret_cast<volatile unsigned long long *>(slot);
+      if (k == 0ull) {
+        k = atomicCAS(slot, 0ull, key);
+        if (k == 0ull) k = key;
+      }
+      if (k == key) {
+        atomicAdd(reinterpret_cast<double *>(slot + 1), v);
+        return;
+      }
+      i = (i + 1) & t.mask;
+    }
+    atomicOr(status, kStatusTableFull);
+  }
+};
+
+// Sink of ray r in group g for a plain cast and for a per-history cast.
+struct TallyMaker {
+  __device__ __forceinline__ static TallySink make(const CastArgs &a, int64_t, int g) {
+    return {a.tally + (int64_t)g * a.mesh.ncells};
+  }
+};
+struct HistMaker {
+  __device__ __forceinline__ static HistSink make(const CastArgs &a, int64_t r, int g) {
+    return {a.htab,
+            ((unsigned long long)__ldg(a.hist + r) << 32) + (unsigned long long)g * a.mesh.ncells + 1ull,
+            a.status};
+  }
+};
+
 // Walks one ray through the mesh and adds its Eq. 4 score to every crossed
-// cell of `tal` (the ray's group slice).  The ray is the half-line p + s d,
+// cell through `sink` (the ray's group slice of the tally, or its history's
+// slots).  The ray is the half-line p + s d,
 // s >= 0, with d not necessarily unit: crossing parameters are in units of
 // |d| and lengths are scaled by |d| at the end.  The crossing parameter of
 // plane j on axis k, ((org_k - p_k) + j h_k) * (1/d_k), is re-evaluated in
@@ -252,10 +313,10 @@ struct Attenuation<kFormFp32> {
 // outside the box is clipped to it (vacuum outside); the walk ends when the
 // ray leaves the mesh or after max_steps steps (then *overflow is set).
 // Returns the number of positive-length segments scored.
-template <int FORM>
+template <int FORM, typename Sink>
 __device__ __forceinline__ uint32_t cast_ray(const MeshDev &M, float px, float py, float pz,
                                              float u, float v, float w, float wt, float dn,
-                                             double *__restrict__ tal, const float *sg,
+                                             const Sink &sink, const float *sg,
                                              const typename Attenuation<FORM>::inv_t *inv,
                                              int stride, bool *overflow) {
   const float p[3] = {px, py, pz};
@@ -336,7 +397,7 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &M, float px, float p
     } else {
       sc = att.score(sg[mat * stride], inv[mat * stride], l);
     }
-    if (sc != 0) atomicAdd(tal + cell, Attenuation<FORM>::to_double(sc));
+    if (sc != 0) sink.add(cell, Attenuation<FORM>::to_double(sc));
     nseg += l > 0.f;
 
     if (leaving) break;
@@ -374,7 +435,7 @@ struct RayCounts {
 };
 
 // One ray of a cast: validation, group, cross sections, walk and score.
-template <int FORM, bool SURR = false>
+template <int FORM, bool SURR = false, typename Maker = TallyMaker>
 __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int32_t *hash_s,
                                          const double *edges, float *sig_s,
                                          typename Attenuation<FORM>::inv_t *inv_s, int stride,
@@ -415,8 +476,8 @@ __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int
   }
   if (from_table) xs_lookup(a.xs, hash_s, E, sig_s, inv_s, stride);
   bool ovf = false;
-  c.seg += cast_ray<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, a.tally + (int64_t)g * a.mesh.ncells,
-                          sig_s, inv_s, stride, &ovf);
+  c.seg += cast_ray<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, Maker::make(a, r, g), sig_s, inv_s,
+                          stride, &ovf);
   c.ovf += ovf;
 }
 

@@ -1,0 +1,100 @@
+// Per-history tally moments: the segment bound that sizes the history table
+// and the drain that turns the table's per-(history, cell) sums x into
+// S1 += x and S2 += x^2 (the sums behind the tally's standard deviation in
+// Eqs. 5 and 8).
+#include <algorithm>
+#include <math.h>
+
+#include "vrc_internal.h"
+
+namespace vrc {
+
+namespace {
+
+// Upper bound of the cells one ray crosses: the ray p + s d is clipped to
+// the box in float64, and the cell indices at its entry and exit differ by
+// the planes it crosses on each axis; one cell more, plus one per axis for
+// rounding differences from the walk.  Rays that miss the box, or that the
+// cast rejects (non-finite, zero direction), count 0.
+__device__ __forceinline__ unsigned long long ray_bound(const BoundGeom &G, const float f[6]) {
+  const double p[3] = {f[0], f[1], f[2]};
+  const double d[3] = {f[3], f[4], f[5]};
+  if (!(d[0] != 0.0 || d[1] != 0.0 || d[2] != 0.0)) return 0;
+  double s_in = 0.0, s_out = INFINITY;
+  for (int k = 0; k < 3; ++k) {
+    const double lo = G.lo[k], hi = G.lo[k] + G.h[k] * G.n[k];
+    if (d[k] == 0.0) {
+      if (!(p[k] >= lo && p[k] < hi)) return 0;
+    } else {
+      double a = (lo - p[k]) / d[k], b = (hi - p[k]) / d[k];
+      if (d[k] < 0.0) { const double t = a; a = b; b = t; }
+      s_in = fmax(s_in, a);
+      s_out = fmin(s_out, b);
+    }
+  }
+  if (!(s_in < s_out)) return 0;  // also false for NaN
+  unsigned long long cells = 1 + 3;
+  for (int k = 0; k < 3; ++k) {
+    if (d[k] == 0.0) continue;
+    const double n = G.n[k];
+    const double a = fmin(fmax(floor((p[k] + s_in * d[k] - G.lo[k]) / G.h[k]), 0.0), n - 1.0);
+    const double b = fmin(fmax(floor((p[k] + s_out * d[k] - G.lo[k]) / G.h[k]), 0.0), n - 1.0);
+    cells += (unsigned long long)fabs(b - a);
+  }
+  return cells;
+}
+
+__global__ void k_segment_bound(BoundGeom G, RayPtrs R, unsigned long long *bound) {
+  unsigned long long acc = 0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R.n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    float f[6];
+    if (R.aos) {
+      const float4 a = R.aos[2 * r], b = R.aos[2 * r + 1];
+      f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y;
+    } else {
+      f[0] = R.x[r]; f[1] = R.y[r]; f[2] = R.z[r]; f[3] = R.u[r]; f[4] = R.v[r]; f[5] = R.w[r];
+    }
+    acc += ray_bound(G, f);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(bound, acc);
+}
+
+// Every occupied slot (key + 1, x): S1[bin] += x, S2[bin] += x^2, slot = 0.
+__global__ void k_hist_drain(ulonglong2 *e, unsigned long long cap, double *__restrict__ s1,
+                             double *__restrict__ s2) {
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const ulonglong2 v = e[i];
+    if (v.x == 0ull) continue;
+    const unsigned bin = (unsigned)((v.x - 1ull) & 0xffffffffull);
+    const double x = __longlong_as_double((long long)v.y);
+    atomicAdd(s1 + bin, x);
+    atomicAdd(s2 + bin, x * x);
+    e[i] = make_ulonglong2(0ull, 0ull);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_segment_bound(const BoundGeom &g, const RayPtrs &rays, unsigned long long *bound,
+                                 int num_sms, cudaStream_t s) {
+  if (rays.n <= 0) return cudaSuccess;
+  const int block = 256;
+  const int grid = (int)std::min<int64_t>((rays.n + block - 1) / block, (int64_t)num_sms * 8);
+  k_segment_bound<<<grid, block, 0, s>>>(g, rays, bound);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist_drain(const HistTable &t, double *s1, double *s2, int num_sms, cudaStream_t s) {
+  const unsigned long long cap = t.mask + 1ull;
+  const int block = 256;
+  const int grid = (int)std::min<unsigned long long>((cap + block - 1) / block, (unsigned long long)num_sms * 8);
+  k_hist_drain<<<grid, block, 0, s>>>(reinterpret_cast<ulonglong2 *>(t.e), cap, s1, s2);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace vrc

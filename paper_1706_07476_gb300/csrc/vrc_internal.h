@@ -13,6 +13,7 @@ constexpr int kMaxGroups = 1024;
 // Status bits written by kernels (read by vrc_sync / vrc_read_tally).
 constexpr unsigned kStatusNonfinite = 1u;
 constexpr unsigned kStatusTraversal = 2u;
+constexpr unsigned kStatusTableFull = 4u;  // a per-history table insert found no free slot
 
 // Device counters (unsigned long long each).
 enum Counter { kCntSegments = 0, kCntRays = 1, kCntRejected = 2, kCntOverflow = 3, kNumCounters = 4 };
@@ -55,6 +56,14 @@ struct RayPtrs {
   int64_t n;
 };
 
+// Per-history scratch table: 2^k entries of two 64-bit words, (key + 1,
+// float64 value bits), 0 marking an empty slot; key = history << 32 | bin,
+// bin = group * ncells + cell.
+struct HistTable {
+  unsigned long long *e;       // [cap][2]
+  unsigned long long mask;     // cap - 1
+};
+
 struct CastArgs {
   MeshDev mesh;
   XsDev xs;
@@ -63,6 +72,8 @@ struct CastArgs {
   RayPtrs rays;
   const float *sig_ray; // [n][16] per-ray sigma from the surrogate (NaN in [0] = use the table), or nullptr
   double *tally;        // [n_groups][ncells]
+  const uint32_t *hist; // [n] history id of each ray (per-history cast only)
+  HistTable htab;       // per-history cast only
   unsigned long long *counters;
   unsigned int *status;
 };
@@ -101,6 +112,19 @@ cudaError_t cast_occupancy(int form, const CastArgs &a, int block, int *blocks_p
 cudaError_t launch_scale_copy(const double *src, double *dst, int64_t n, double scale,
                               cudaStream_t s);
 cudaError_t launch_fold_moments(double *tally, double *s1, double *s2, int64_t n, cudaStream_t s);
+// Per-history moments (vrc_history.cu and vrc_cast.cu): an upper bound of
+// the segments of a ray batch (added to *bound), the cast that scores into
+// the history table, and the drain S1 += x, S2 += x^2 that also empties it.
+struct BoundGeom {
+  double lo[3], h[3];
+  int32_t n[3];
+};
+cudaError_t launch_segment_bound(const BoundGeom &g, const RayPtrs &rays, unsigned long long *bound,
+                                 int num_sms, cudaStream_t s);
+cudaError_t launch_cast_hist(int form, const CastArgs &a, int grid, int block, cudaStream_t s);
+cudaError_t cast_hist_occupancy(int form, const CastArgs &a, int block, int *blocks_per_sm);
+cudaError_t launch_hist_drain(const HistTable &t, double *s1, double *s2, int num_sms, cudaStream_t s);
+
 cudaError_t launch_moment_sigma(const double *s1, const double *s2, double *sigma, int64_t n, double B,
                                 cudaStream_t s);
 

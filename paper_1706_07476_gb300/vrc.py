@@ -89,6 +89,7 @@ def _load():
         "vrc_moments_enable": ([P, I32], C.c_int),
         "vrc_moments_fold": ([P, P], C.c_int),
         "vrc_moments_read": ([P, P, P, I64, P, P], C.c_int),
+        "vrc_cast_histories": ([P, P, P, I64, P], C.c_int),
         "vrc_stream_create": ([P, I64, I32, P], C.c_int),
         "vrc_stream_acquire": ([P, P, P], C.c_int),
         "vrc_stream_submit": ([P, I64], C.c_int),
@@ -366,8 +367,36 @@ def vrc_detector_flux(ctx: Context, rays: dict, detectors, stream=None) -> np.nd
     return out
 
 
-def vrc_moments_enable(ctx: Context, on: bool = True):
-    _check(_lib.vrc_moments_enable(ctx.handle, int(bool(on))))
+VRC_MOMENTS_OFF = 0
+VRC_MOMENTS_BATCH = 1
+VRC_MOMENTS_HISTORY = 2
+
+
+def vrc_moments_enable(ctx: Context, mode: int = VRC_MOMENTS_BATCH):
+    _check(_lib.vrc_moments_enable(ctx.handle, int(mode)))
+
+
+def vrc_cast_histories(ctx: Context, rays: dict, history, n_histories: int, stream=None):
+    """Per-history cast: history is a uint32 array (numpy for host rays, a
+    torch int32/uint32 tensor for device rays) with the history id of each ray."""
+    r, keep = _ray_struct(rays)
+    if isinstance(history, np.ndarray):
+        if r.on_device:
+            raise ValueError("history ids must be on the same side as the rays")
+        h = np.ascontiguousarray(history, np.uint32)
+        if h.shape[0] != r.n:
+            raise ValueError("one history id per ray")
+        hp = h.ctypes.data
+        dev = []
+    else:
+        if not r.on_device or not history.is_cuda or history.element_size() != 4 or not history.is_contiguous():
+            raise ValueError("device history ids: a contiguous 4-byte tensor beside device rays")
+        if history.shape[0] != r.n:
+            raise ValueError("one history id per ray")
+        hp = history.data_ptr()
+        dev = _order_device_inputs(ctx, stream, keep + [history])
+    _check(_lib.vrc_cast_histories(ctx.handle, C.byref(r), hp, int(n_histories), _stream_handle(stream)))
+    _hold_until_done(ctx, stream, dev)
 
 
 def vrc_moments_fold(ctx: Context, stream=None):
@@ -375,7 +404,8 @@ def vrc_moments_fold(ctx: Context, stream=None):
 
 
 def vrc_moments_read(ctx: Context, stream=None):
-    """Returns (total, sigma, batches) as host float64 arrays."""
+    """Returns (total, sigma, samples): host float64 arrays and the batch or
+    history count."""
     total = np.empty(ctx.tally_size, np.float64)
     sigma = np.empty(ctx.tally_size, np.float64)
     b = C.c_int64()
