@@ -41,7 +41,8 @@ class _Mesh(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
-                ("material", C.c_void_p)]
+                ("material", C.c_void_p), ("xe", C.c_void_p), ("ye", C.c_void_p),
+                ("ze", C.c_void_p)]
 
 
 class _XS(C.Structure):
@@ -85,8 +86,15 @@ class _Ctx:
     def __init__(self, mesh, tables=None):
         self.mat = np.ascontiguousarray(mesh.material, dtype=np.uint8).reshape(-1)
         assert self.mat.size == mesh.nx * mesh.ny * mesh.nz
+        # a rectilinear mesh carries its plane positions per axis
+        self.edges = [None if getattr(mesh, a, None) is None
+                      else np.ascontiguousarray(getattr(mesh, a), np.float64)
+                      for a in ("xe", "ye", "ze")]
+        for e, n in zip(self.edges, (mesh.nx, mesh.ny, mesh.nz)):
+            assert e is None or (e.shape == (n + 1,) and np.all(np.diff(e) > 0))
+        ep = [None if e is None else e.ctypes.data for e in self.edges]
         self.mesh = _Mesh(mesh.nx, mesh.ny, mesh.nz, mesh.x0, mesh.y0, mesh.z0,
-                          mesh.dx, mesh.dy, mesh.dz, self.mat.ctypes.data)
+                          mesh.dx, mesh.dy, mesh.dz, self.mat.ctypes.data, *ep)
         if tables is not None:
             Es, Ss, offs = [], [], [0]
             for t in tables:

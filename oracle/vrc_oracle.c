@@ -17,7 +17,9 @@
  *  - the energy group of a ray: half-open [e_g, e_g+1), last group closed;
  *    rays outside every group score nothing.
  *  - the cells a ray crosses and its length in each, by a 3-D Amanatides-Woo
- *    grid walk.  The next crossing on every axis is recomputed from the
+ *    grid walk on a uniform mesh (planes at x0 + j dx) or a rectilinear one
+ *    (planes at given per-axis edges: the non-uniform Cartesian meshes of
+ *    the paper's outlook, Sec. 6).  The next crossing on every axis is recomputed from the
  *    integer cell index each step (never accumulated).  The ray is a
  *    half-line from its start point; a start outside the mesh is clipped to
  *    the mesh box (vacuum outside, Sec. 5.1: vacuum boundary only), and the
@@ -47,6 +49,10 @@ typedef struct {
   int32_t nx, ny, nz;
   double x0, y0, z0, dx, dy, dz;
   const uint8_t *material; /* [nz][ny][nx] */
+  /* Optional plane positions per axis (n+1 strictly ascending values each);
+   * NULL on every axis = the uniform mesh x0 + j dx.  When set, x0..dz are
+   * ignored. */
+  const double *xe, *ye, *ze;
 } orc_mesh;
 
 /* Concatenated per-material tables: material m owns entries offs[m] ..
@@ -94,22 +100,63 @@ int32_t orc_group(const double *edges, int32_t n_groups, double e) {
 /* traversal                                                            */
 /* ------------------------------------------------------------------ */
 
+static const double *axis_edges(const orc_mesh *m, int k) {
+  return k == 0 ? m->xe : (k == 1 ? m->ye : m->ze);
+}
+
+static int32_t axis_cells(const orc_mesh *m, int k) {
+  return k == 0 ? m->nx : (k == 1 ? m->ny : m->nz);
+}
+
+/* Position of plane j (0..n) on axis k. */
+static double plane(const orc_mesh *m, int k, int64_t j) {
+  const double *e = axis_edges(m, k);
+  if (e) return e[j];
+  const double lo[3] = {m->x0, m->y0, m->z0};
+  const double h[3] = {m->dx, m->dy, m->dz};
+  return lo[k] + (double)j * h[k];
+}
+
+static int32_t clampi(int64_t i, int32_t n) {
+  if (i < 0) return 0;
+  if (i >= n) return n - 1;
+  return (int32_t)i;
+}
+
+/* Cell index on axis k of coordinate q: plane(j) <= q < plane(j+1), clamped
+ * to 0..n-1. */
+static int32_t locate(const orc_mesh *m, int k, double q) {
+  const int32_t n = axis_cells(m, k);
+  const double *e = axis_edges(m, k);
+  if (!e) {
+    const double lo[3] = {m->x0, m->y0, m->z0};
+    const double h[3] = {m->dx, m->dy, m->dz};
+    return clampi((int64_t)floor((q - lo[k]) / h[k]), n);
+  }
+  if (!(q >= e[0])) return 0;
+  if (q >= e[n]) return n - 1;
+  int32_t lo = 0, hi = n; /* invariant: e[lo] <= q < e[hi] */
+  while (hi - lo > 1) {
+    int32_t mid = lo + (hi - lo) / 2;
+    if (e[mid] <= q) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 /* Clip the half-line p + t d (t >= 0) to the mesh box.  Returns 0 when the
  * ray misses, else 1 with [*t0, *t1] the part inside the box.  On an axis
  * with d == 0 the ray must satisfy lo <= p < hi. */
 static int clip_box(const orc_mesh *m, const double p[3], const double d[3], double *t0,
                     double *t1) {
-  const double lo[3] = {m->x0, m->y0, m->z0};
-  const double h[3] = {m->dx, m->dy, m->dz};
-  const int32_t n[3] = {m->nx, m->ny, m->nz};
   double a = 0.0, b = INFINITY;
   for (int k = 0; k < 3; ++k) {
-    double hi = lo[k] + n[k] * h[k];
+    const double lo = plane(m, k, 0);
+    const double hi = plane(m, k, axis_cells(m, k));
     if (d[k] == 0.0) {
-      if (p[k] < lo[k] || p[k] >= hi) return 0;
+      if (p[k] < lo || p[k] >= hi) return 0;
       continue;
     }
-    double ta = (lo[k] - p[k]) / d[k];
+    double ta = (lo - p[k]) / d[k];
     double tb = (hi - p[k]) / d[k];
     if (ta > tb) { double s = ta; ta = tb; tb = s; }
     if (ta > a) a = ta;
@@ -121,12 +168,6 @@ static int clip_box(const orc_mesh *m, const double p[3], const double d[3], dou
   return 1;
 }
 
-static int32_t clampi(int64_t i, int32_t n) {
-  if (i < 0) return 0;
-  if (i >= n) return n - 1;
-  return (int32_t)i;
-}
-
 /* Grid walk.  d must be a unit vector.  Writes, per step, the linear cell
  * index, the entry distance and the length (zero-length steps at exact
  * edge/corner crossings included).  Returns the number of steps, or -1 if
@@ -135,23 +176,18 @@ int64_t orc_trace_dda(const orc_mesh *m, const double p[3], const double d[3], i
                       double *t_in, double *lens, int64_t cap) {
   double t0, t1;
   if (!clip_box(m, p, d, &t0, &t1)) return 0;
-  const double lo[3] = {m->x0, m->y0, m->z0};
-  const double h[3] = {m->dx, m->dy, m->dz};
   const int32_t n[3] = {m->nx, m->ny, m->nz};
   int32_t idx[3];
-  for (int k = 0; k < 3; ++k) {
-    double q = p[k] + t0 * d[k];
-    idx[k] = clampi((int64_t)floor((q - lo[k]) / h[k]), n[k]);
-  }
+  for (int k = 0; k < 3; ++k) idx[k] = locate(m, k, p[k] + t0 * d[k]);
   double t = t0;
   int64_t count = 0;
   for (;;) {
     double tn[3];
     for (int k = 0; k < 3; ++k) {
       if (d[k] > 0.0)
-        tn[k] = (lo[k] + (double)(idx[k] + 1) * h[k] - p[k]) / d[k];
+        tn[k] = (plane(m, k, idx[k] + 1) - p[k]) / d[k];
       else if (d[k] < 0.0)
-        tn[k] = (lo[k] + (double)idx[k] * h[k] - p[k]) / d[k];
+        tn[k] = (plane(m, k, idx[k]) - p[k]) / d[k];
       else
         tn[k] = INFINITY;
     }
@@ -177,17 +213,15 @@ static int cmp_double(const void *a, const void *b) {
   return (x > y) - (x < y);
 }
 
-/* Brute-force traversal: every plane crossing x = x0 + j dx (and y, z)
+/* Brute-force traversal: every plane crossing x = plane(j) (and y, z)
  * strictly inside the clipped interval is collected and sorted; each
- * positive-length interval's midpoint is classified by floor().  tbuf needs
+ * positive-length interval's midpoint is classified by locate().  tbuf needs
  * room for nx+ny+nz+5 values.  Returns the number of positive-length
  * segments, or -1 if cap is too small. */
 int64_t orc_trace_brute(const orc_mesh *m, const double p[3], const double d[3], int64_t *cells,
                         double *t_in, double *lens, int64_t cap, double *tbuf) {
   double t0, t1;
   if (!clip_box(m, p, d, &t0, &t1)) return 0;
-  const double lo[3] = {m->x0, m->y0, m->z0};
-  const double h[3] = {m->dx, m->dy, m->dz};
   const int32_t n[3] = {m->nx, m->ny, m->nz};
   int64_t nt = 0;
   tbuf[nt++] = t0;
@@ -195,7 +229,7 @@ int64_t orc_trace_brute(const orc_mesh *m, const double p[3], const double d[3],
   for (int k = 0; k < 3; ++k) {
     if (d[k] == 0.0) continue;
     for (int32_t j = 0; j <= n[k]; ++j) {
-      double t = (lo[k] + (double)j * h[k] - p[k]) / d[k];
+      double t = (plane(m, k, j) - p[k]) / d[k];
       if (t > t0 && t < t1) tbuf[nt++] = t;
     }
   }
@@ -206,8 +240,7 @@ int64_t orc_trace_brute(const orc_mesh *m, const double p[3], const double d[3],
     if (!(b > a)) continue;
     double mid = 0.5 * (a + b);
     int32_t idx[3];
-    for (int k = 0; k < 3; ++k)
-      idx[k] = clampi((int64_t)floor((p[k] + mid * d[k] - lo[k]) / h[k]), n[k]);
+    for (int k = 0; k < 3; ++k) idx[k] = locate(m, k, p[k] + mid * d[k]);
     if (count >= cap) return -1;
     cells[count] = ((int64_t)idx[2] * m->ny + idx[1]) * m->nx + idx[0];
     t_in[count] = a;

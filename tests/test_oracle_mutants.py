@@ -21,15 +21,17 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "vrc_oracle.c")
 MUTANTS = {
     "drop_attenuation": ("return wt * exp(-tau) * path;", "return wt * path;"),
     "expm1_sign": ("-expm1(-sig * l) / sig", "expm1(sig * l) / sig"),
-    "transposed_spacing": ("tn[k] = (lo[k] + (double)idx[k] * h[k] - p[k]) / d[k];",
-                           "tn[k] = (lo[k] + (double)idx[k] * h[(k + 1) % 3] - p[k]) / d[k];"),
-    "boundary_off_by_one": ("(lo[k] + (double)(idx[k] + 1) * h[k] - p[k]) / d[k]",
-                            "(lo[k] + (double)(idx[k] + 2) * h[k] - p[k]) / d[k]"),
+    "transposed_spacing": ("return lo[k] + (double)j * h[k];",
+                           "return lo[k] + (double)j * h[(k + 1) % 3];"),
+    "boundary_off_by_one": ("tn[k] = (plane(m, k, idx[k] + 1) - p[k]) / d[k];",
+                            "tn[k] = (plane(m, k, idx[k] + 2) - p[k]) / d[k];"),
     "interp_wrong_end": ("S[lo] + (e - E[lo]) * (S[hi] - S[lo])", "S[lo] + (E[hi] - e) * (S[hi] - S[lo])"),
     "tau_not_accumulated": ("tau += sg * lens[s];", ""),
     "no_vacuum_clip": ("if (ta > a) a = ta;", ""),
     "wrong_group_bin": ("if (edges[mid] <= e) lo = mid; else hi = mid;",
                         "if (edges[mid] < e) lo = mid; else hi = mid;"),
+    "rect_edge_index_shift": ("if (e) return e[j];", "if (e) return e[j > 0 ? j - 1 : 0];"),
+    "rect_locate_as_uniform": ("  if (!e) {\n    const double lo[3]", "  if (1) {\n    const double lo[3]"),
 }
 
 
@@ -39,7 +41,9 @@ def _pins():
     checks += [P.test_sigma_linlin_matches_numpy_interp, P.test_homogeneous_total_is_eq1_closed_form,
                P.test_void_scores_geometric_chord, P.test_telescoping_invariant,
                P.test_start_outside_equals_start_at_entry, P.test_group_edges,
-               P.test_brute_force_quadrature_tiny_meshes]
+               P.test_brute_force_quadrature_tiny_meshes, P.test_rect_void_chords_are_cell_widths,
+               P.test_rect_axis_aligned_per_cell_scores, P.test_rect_inserted_plane_additivity,
+               P.test_rect_dda_matches_brute_force_traversal]
     return checks
 
 

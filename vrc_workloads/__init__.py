@@ -62,6 +62,51 @@ class Mesh:
 
 
 @dataclasses.dataclass
+class RectMesh:
+    """A rectilinear (non-uniform Cartesian) mesh: cell (ix, iy, iz) spans
+    [xe[ix], xe[ix+1]) x [ye[iy], ye[iy+1]) x [ze[iz], ze[iz+1]); each edge
+    array is strictly ascending float64 of n+1 values; ``material`` is uint8
+    [nz][ny][nx]."""
+
+    xe: np.ndarray
+    ye: np.ndarray
+    ze: np.ndarray
+    material: np.ndarray
+
+    @property
+    def nx(self) -> int:
+        return len(self.xe) - 1
+
+    @property
+    def ny(self) -> int:
+        return len(self.ye) - 1
+
+    @property
+    def nz(self) -> int:
+        return len(self.ze) - 1
+
+    @property
+    def ncells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    # first plane and mean spacing per axis (the box; not cell sizes)
+    x0 = property(lambda self: float(self.xe[0]))
+    y0 = property(lambda self: float(self.ye[0]))
+    z0 = property(lambda self: float(self.ze[0]))
+    dx = property(lambda self: float(self.xe[-1] - self.xe[0]) / self.nx)
+    dy = property(lambda self: float(self.ye[-1] - self.ye[0]) / self.ny)
+    dz = property(lambda self: float(self.ze[-1] - self.ze[0]) / self.nz)
+
+    @property
+    def lo(self):
+        return (self.x0, self.y0, self.z0)
+
+    @property
+    def hi(self):
+        return (float(self.xe[-1]), float(self.ye[-1]), float(self.ze[-1]))
+
+
+@dataclasses.dataclass
 class Problem:
     """One tally problem: mesh, per-material tables, group edges, rays."""
 
@@ -255,6 +300,84 @@ def pin_lattice(seed: int = 2, pins: int = 17, cells_per_pin: int = 32, nz: int 
     E = log_uniform(rng, n_rays)
     wt = np.ones(n_rays, np.float32)
     return Problem("pinlattice", mesh, tables, None, make_rays(x, y, z, u, v, w, E, wt))
+
+
+def graded_edges(fine_cells: int, fine_width: float, grow: float, coarse_width: float,
+                 half_width: float) -> np.ndarray:
+    """Symmetric graded edges: fine_cells cells of fine_width centred on 0,
+    then cells growing by the factor grow up to coarse_width on each side
+    until |x| reaches half_width (the last cell is cut at half_width)."""
+    core = fine_cells * fine_width / 2.0
+    right = list(np.linspace(0.0, core, fine_cells // 2 + 1)) if fine_cells % 2 == 0 else None
+    if right is None:
+        raise ValueError("fine_cells must be even")
+    w = fine_width
+    x = core
+    while x < half_width - 1e-12:
+        w = min(w * grow, coarse_width)
+        x = min(x + w, half_width)
+        right.append(x)
+    right = np.asarray(right)
+    return np.concatenate([-right[:0:-1], right])
+
+
+def graded_assembly(seed: int = 5, pins: int = 16, cells_per_pin: int = 21, reflector: float = 30.0,
+                    nz: int = 5, height: float = 100.0, n_rays: int = 1 << 24,
+                    n_points: int = 20000, n_resonances: int = 200,
+                    inside_frac: float = 0.7) -> Problem:
+    """A 16x16 pin assembly on a graded (rectilinear) mesh.
+
+    The PWR test put a 0.6 mm mesh over the whole 340 x 340 x 5 problem,
+    reflector included; a non-uniform Cartesian mesh (Sec. 6 outlook) keeps
+    0.6 mm cells (1.26 cm pitch / 21) over the assembly and grows them by
+    1.1x per cell up to 2 cm through a 30 cm solution-and-graphite
+    reflector.  Materials: 0 moderator, 1 fuel (r < 0.36), 2 void gap
+    (0.36 <= r < 0.40), 3 cladding (0.40 <= r < 0.45), 4 uranyl-nitrate-like
+    solution (first 10 cm outside the assembly), 5 graphite beyond; nz
+    uniform layers over the height.  70% of starts uniform in the fuel
+    discs, the rest uniform over the box; energies 1/E; seed 5.
+    """
+    rng = np.random.default_rng(seed)
+    pitch = 1.26
+    half_core = pins * pitch / 2.0
+    xe = graded_edges(pins * cells_per_pin, pitch / cells_per_pin, 1.1, 2.0, half_core + reflector)
+    ze = np.linspace(0.0, height, nz + 1)
+    c = 0.5 * (xe[:-1] + xe[1:])
+    inside = np.abs(c) < half_core
+    local = np.mod(c + half_core, pitch) - 0.5 * pitch
+    r = np.sqrt(local[None, :] ** 2 + local[:, None] ** 2)  # [iy][ix]
+    core = inside[None, :] & inside[:, None]
+    layer = np.zeros(r.shape, np.uint8)
+    layer[core & (r < 0.45)] = 3
+    layer[core & (r < 0.40)] = 2
+    layer[core & (r < 0.36)] = 1
+    dist = np.maximum(np.abs(c)[None, :], np.abs(c)[:, None]) - half_core
+    layer[(~core) & (dist < 10.0)] = 4
+    layer[(~core) & (dist >= 10.0)] = 5
+    mat = np.ascontiguousarray(np.broadcast_to(layer, (nz, len(c), len(c))))
+    mesh = RectMesh(xe, xe.copy(), ze, mat)
+    tables = [xs_table(rng, n_points, n_resonances), xs_table(rng, n_points, n_resonances), None,
+              xs_table(rng, n_points, n_resonances), xs_table(rng, n_points, n_resonances),
+              xs_table(rng, n_points, n_resonances)]
+    n_in = int(round(inside_frac * n_rays))
+    n_out = n_rays - n_in
+    pin = rng.integers(0, pins * pins, n_in)
+    rr = 0.36 * np.sqrt(rng.random(n_in))
+    th = 2.0 * math.pi * rng.random(n_in)
+    xi = -half_core + ((pin % pins) + 0.5) * pitch + rr * np.cos(th)
+    yi = -half_core + ((pin // pins) + 0.5) * pitch + rr * np.sin(th)
+    zi = height * rng.random(n_in)
+    xo, yo, zo = uniform_positions(rng, mesh, n_out)
+    hi = mesh.hi
+    x = np.concatenate([xi.astype(np.float32), xo])
+    y = np.concatenate([yi.astype(np.float32), yo])
+    z = np.concatenate([zi.astype(np.float32), zo])
+    for arr, h in ((x, hi[0]), (y, hi[1]), (z, hi[2])):
+        np.minimum(arr, np.nextafter(np.float32(h), np.float32(-np.inf)), out=arr)
+    u, v, w = isotropic_dirs(rng, n_rays)
+    E = log_uniform(rng, n_rays)
+    wt = np.ones(n_rays, np.float32)
+    return Problem("graded", mesh, tables, None, make_rays(x, y, z, u, v, w, E, wt))
 
 
 def batched_problems(seed: int = 3, n_problems: int = 1024, side_lo: int = 16,
