@@ -126,6 +126,29 @@ void vrc_default_options(vrc_options *opt);
  * edges), VRC_ERR_OOM, VRC_ERR_CUDA. */
 int vrc_create_mesh(const vrc_mesh_desc *d, const vrc_options *opt, vrc_ctx **out);
 
+/* A rectilinear (non-uniform Cartesian) mesh, the structured meshes of the
+ * Sec. 6 outlook: cell (ix, iy, iz) spans [x_edges[ix], x_edges[ix+1]) x
+ * [y_edges[iy], y_edges[iy+1]) x [z_edges[iz], z_edges[iz+1]).  Each edge
+ * array is a HOST array of n+1 finite, strictly ascending float64 plane
+ * positions (cm), copied; every other field means what it does in
+ * vrc_mesh_desc.  The walk takes each crossing from the plane positions
+ * (kept on the device as double-float pairs, about 48 bits). */
+typedef struct {
+  int32_t nx, ny, nz;
+  const double *x_edges, *y_edges, *z_edges;
+  const uint8_t *material;
+  int32_t n_materials;
+  int32_t n_groups;
+  const double *group_edges;
+} vrc_rect_mesh_desc;
+
+/* vrc_create_mesh for a rectilinear mesh.  Every call on the context works
+ * as on a uniform mesh (VRC_PER_VOLUME divides by each cell's own volume),
+ * except vrc_detector_flux and the batched form, which return VRC_ERR_ARG.
+ * Errors: as vrc_create_mesh, and VRC_ERR_ARG for NULL, non-finite or
+ * non-ascending edges. */
+int vrc_create_rect_mesh(const vrc_rect_mesh_desc *d, const vrc_options *opt, vrc_ctx **out);
+
 /* Loads the total macroscopic cross-section table of one material (Sec. 3:
  * continuous-energy total cross sections, linearly interpolated between
  * table points; clamped to the end values outside the table).  E_eV and

@@ -101,7 +101,12 @@ struct vrc_ctx {
   cudaStream_t stream = nullptr;
   vrc_options opt;
   int32_t n[3] = {0, 0, 0};
-  double org[3] = {0, 0, 0}, h[3] = {0, 0, 0};
+  double org[3] = {0, 0, 0}, h[3] = {0, 0, 0};  // rectilinear: first plane, mean spacing
+  bool rect = false;
+  DevBuf rectDf;     // plane positions as (hi, lo) float pairs, x then y then z
+  DevBuf rectD;      // plane positions, float64, same order
+  DevBuf rectWidth;  // cell widths, float64, x then y then z
+  int64_t rect_off[3] = {0, 0, 0};  // first plane of each axis in rectDf / rectD
   int64_t ncells = 0;
   int32_t n_materials = 0, n_groups = 1;
   std::vector<double> edges;
@@ -185,6 +190,9 @@ struct vrc_ctx {
     histTab.release();
     histIds.release();
     histBound.release();
+    rectDf.release();
+    rectD.release();
+    rectWidth.release();
     detPos.release();
     detOut.release();
     if (stream) cudaStreamDestroy(stream);
@@ -285,6 +293,10 @@ CastArgs make_args(const vrc_ctx *c, const RayPtrs &rays) {
   a.mesh.stride[2] = (int64_t)c->n[0] * c->n[1];
   a.mesh.ncells = c->ncells;
   a.mesh.mat = c->d_mat;
+  if (c->rect) {
+    a.mesh.rect = 1;
+    for (int k = 0; k < 3; ++k) a.mesh.edge[k] = static_cast<const float2 *>(c->rectDf.p) + c->rect_off[k];
+  }
   a.xs.n_union = c->n_union;
   a.xs.m_pad = c->m_pad;
   a.xs.n_mat = c->n_materials;
@@ -558,6 +570,62 @@ int vrc_create_mesh(const vrc_mesh_desc *d, const vrc_options *opt, vrc_ctx **ou
   return VRC_OK;
 }
 
+int vrc_create_rect_mesh(const vrc_rect_mesh_desc *d, const vrc_options *opt, vrc_ctx **out) {
+  if (!out) return fail(VRC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(VRC_ERR_ARG, "mesh descriptor is NULL");
+  const int32_t n[3] = {d->nx, d->ny, d->nz};
+  const double *e[3] = {d->x_edges, d->y_edges, d->z_edges};
+  for (int k = 0; k < 3; ++k) {
+    if (n[k] <= 0) return fail(VRC_ERR_ARG, "mesh dimensions must be positive (got %d x %d x %d)", d->nx, d->ny, d->nz);
+    if (!e[k]) return fail(VRC_ERR_ARG, "edge array %d is NULL", k);
+    for (int32_t j = 0; j <= n[k]; ++j) {
+      if (!std::isfinite(e[k][j])) return fail(VRC_ERR_ARG, "edge %d of axis %d is not finite", j, k);
+      if (j > 0 && !(e[k][j] > e[k][j - 1])) return fail(VRC_ERR_ARG, "edges of axis %d must be strictly ascending", k);
+    }
+  }
+  vrc_mesh_desc u;
+  u.nx = d->nx; u.ny = d->ny; u.nz = d->nz;
+  u.x0 = e[0][0]; u.y0 = e[1][0]; u.z0 = e[2][0];
+  u.dx = (e[0][n[0]] - e[0][0]) / n[0];
+  u.dy = (e[1][n[1]] - e[1][0]) / n[1];
+  u.dz = (e[2][n[2]] - e[2][0]) / n[2];
+  u.material = d->material;
+  u.n_materials = d->n_materials;
+  u.n_groups = d->n_groups;
+  u.group_edges = d->group_edges;
+  vrc_ctx *c = nullptr;
+  int rc = vrc_create_mesh(&u, opt, &c);
+  if (rc) return rc;
+  DeviceGuard g(c->device);
+  const int64_t planes = (int64_t)n[0] + n[1] + n[2] + 3;
+  std::vector<float2> df2(planes);
+  std::vector<double> dd(planes), width(planes - 3);
+  int64_t o = 0, ow = 0;
+  for (int k = 0; k < 3; ++k) {
+    c->rect_off[k] = o;
+    for (int32_t j = 0; j <= n[k]; ++j, ++o) {
+      const df sp = split(e[k][j]);
+      df2[o] = make_float2(sp.hi, sp.lo);
+      dd[o] = e[k][j];
+      if (j < n[k]) width[ow++] = e[k][j + 1] - e[k][j];
+    }
+  }
+  cudaError_t err;
+  if ((err = c->rectDf.ensure(sizeof(float2) * planes)) != cudaSuccess ||
+      (err = c->rectD.ensure(sizeof(double) * planes)) != cudaSuccess ||
+      (err = c->rectWidth.ensure(sizeof(double) * width.size())) != cudaSuccess ||
+      (err = cudaMemcpy(c->rectDf.p, df2.data(), sizeof(float2) * planes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMemcpy(c->rectD.p, dd.data(), sizeof(double) * planes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMemcpy(c->rectWidth.p, width.data(), sizeof(double) * width.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    delete c;
+    return cuda_fail(err, "uploading the mesh planes");
+  }
+  c->rect = true;
+  *out = c;
+  return VRC_OK;
+}
+
 int vrc_load_xs(vrc_ctx *c, int32_t material, const double *E_eV, const double *sigma_t, int64_t n) {
   if (!c) return fail(VRC_ERR_ARG, "context is NULL");
   if (material < 0 || material >= c->n_materials)
@@ -651,8 +719,15 @@ int vrc_read_tally(vrc_ctx *c, double *out_host, int64_t n, int32_t flags, void 
     VRC_CUDA(c->scratch.ensure(sizeof(double) * chunk), "allocating tally staging");
     for (int64_t off = 0; off < total; off += chunk) {
       const int64_t m = std::min(chunk, total - off);
-      VRC_CUDA(launch_scale_copy(c->d_tally + off, static_cast<double *>(c->scratch.p), m, scale, c->stream),
-               "launching the tally finalize kernel");
+      if (c->rect) {
+        const double *w = static_cast<const double *>(c->rectWidth.p);
+        VRC_CUDA(launch_per_volume_rect(c->d_tally + off, static_cast<double *>(c->scratch.p), m, off, c->n[0],
+                                        c->n[1], c->ncells, w, w + c->n[0], w + c->n[0] + c->n[1], c->stream),
+                 "launching the tally finalize kernel");
+      } else {
+        VRC_CUDA(launch_scale_copy(c->d_tally + off, static_cast<double *>(c->scratch.p), m, scale, c->stream),
+                 "launching the tally finalize kernel");
+      }
       VRC_CUDA(cudaMemcpyAsync(out_host + off, c->scratch.p, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream),
                "copying the tally");
       VRC_CUDA(cudaStreamSynchronize(c->stream), "copying the tally");
@@ -883,6 +958,7 @@ int vrc_batch_create(vrc_ctx *const *ctxs, const vrc_rays *rays, int32_t n_probl
     if (ctxs[p]->opt.form != form) return fail(VRC_ERR_ARG, "all contexts must use one precision form");
     const vrc_rays &r = rays[p];
     if (!r.on_device) return fail(VRC_ERR_ARG, "problem %d: the batched form takes device rays", p);
+    if (ctxs[p]->rect) return fail(VRC_ERR_ARG, "problem %d: the batched form takes uniform meshes", p);
     if (r.n < 0) return fail(VRC_ERR_ARG, "problem %d: negative ray count", p);
     if (r.n > 0 && (!r.x || !r.y || !r.z || !r.u || !r.v || !r.w || !r.E || !r.wt))
       return fail(VRC_ERR_ARG, "problem %d: a ray array is NULL", p);
@@ -1567,6 +1643,7 @@ int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, i
     G.lo[k] = c->org[k];
     G.h[k] = c->h[k];
     G.n[k] = c->n[k];
+    G.e[k] = c->rect ? static_cast<const double *>(c->rectD.p) + c->rect_off[k] : nullptr;
   }
   VRC_CUDA(c->histBound.ensure(sizeof(unsigned long long)), "allocating the segment bound");
   unsigned long long *d_bound = static_cast<unsigned long long *>(c->histBound.p);
@@ -1655,6 +1732,7 @@ int vrc_detector_flux(vrc_ctx *c, const vrc_rays *r, const double *det_xyz, int3
                       double *out, void *cuda_stream) {
   if (!c || !r || !det_xyz || !out) return fail(VRC_ERR_ARG, "bad arguments");
   if (n_det < 1 || n_det > 64) return fail(VRC_ERR_ARG, "n_det must be in 1..64");
+  if (c->rect) return fail(VRC_ERR_ARG, "the next-event estimator takes a uniform mesh");
   if (r->n < 0) return fail(VRC_ERR_ARG, "ray count is negative");
   const int64_t nout = (int64_t)n_det * c->n_groups;
   if ((int64_t)n_det * c->n_groups * 8 > 64 * 1024) return fail(VRC_ERR_ARG, "n_det * n_groups too large");

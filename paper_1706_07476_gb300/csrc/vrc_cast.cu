@@ -38,7 +38,7 @@ SmemLayout smem_layout(int form, const CastArgs &a, int block) {
   return L;
 }
 
-template <int FORM, bool SURR, typename Maker = TallyMaker>
+template <int FORM, bool SURR, typename Maker = TallyMaker, bool RECT = false>
 __global__ void __launch_bounds__(256, 4) k_cast(CastArgs a, SmemLayout L) {
   typedef typename Attenuation<FORM>::inv_t inv_t;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256, 4) k_cast(CastArgs a, SmemLayout L) {
   RayCounts cnt;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.rays.n;
        r += (int64_t)gridDim.x * blockDim.x)
-    cast_one<FORM, SURR, Maker>(a, r, hash_s, edges, sig_s, inv_s, stride, cnt);
+    cast_one<FORM, SURR, Maker, RECT>(a, r, hash_s, edges, sig_s, inv_s, stride, cnt);
   flush_counts(cnt, a.counters, a.status);
 }
 
@@ -116,22 +116,35 @@ size_t cast_smem_bytes(int form, const CastArgs &a, int block) {
   return smem_layout(form, a, block).total;
 }
 
+template <int FORM, bool SURR, typename Maker, bool RECT>
+cudaError_t occupancy_r(const CastArgs &a, int block, int *bps) {
+  const size_t smem = cast_smem_bytes(FORM, a, block);
+  cudaError_t e = cudaFuncSetAttribute(k_cast<FORM, SURR, Maker, RECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_cast<FORM, SURR, Maker, RECT>, block, smem);
+}
+
+template <int FORM, bool SURR, typename Maker, bool RECT>
+cudaError_t launch_r(const CastArgs &a, int grid, int block, cudaStream_t s) {
+  const SmemLayout L = smem_layout(FORM, a, block);
+  cudaError_t e = cudaFuncSetAttribute(k_cast<FORM, SURR, Maker, RECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  if (e != cudaSuccess) return e;
+  k_cast<FORM, SURR, Maker, RECT><<<grid, block, L.total, s>>>(a, L);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// uniform or rectilinear mesh, chosen by the mesh descriptor
 template <int FORM, bool SURR, typename Maker = TallyMaker>
 cudaError_t occupancy_t(const CastArgs &a, int block, int *bps) {
-  const size_t smem = cast_smem_bytes(FORM, a, block);
-  cudaError_t e = cudaFuncSetAttribute(k_cast<FORM, SURR, Maker>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_cast<FORM, SURR, Maker>, block, smem);
+  return a.mesh.rect ? occupancy_r<FORM, SURR, Maker, true>(a, block, bps)
+                     : occupancy_r<FORM, SURR, Maker, false>(a, block, bps);
 }
 
 template <int FORM, bool SURR, typename Maker = TallyMaker>
 cudaError_t launch_t(const CastArgs &a, int grid, int block, cudaStream_t s) {
-  const SmemLayout L = smem_layout(FORM, a, block);
-  cudaError_t e = cudaFuncSetAttribute(k_cast<FORM, SURR, Maker>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-  if (e != cudaSuccess) return e;
-  k_cast<FORM, SURR, Maker><<<grid, block, L.total, s>>>(a, L);
-  note_launches(1);
-  return cudaGetLastError();
+  return a.mesh.rect ? launch_r<FORM, SURR, Maker, true>(a, grid, block, s)
+                     : launch_r<FORM, SURR, Maker, false>(a, grid, block, s);
 }
 
 cudaError_t cast_occupancy(int form, const CastArgs &a, int block, int *blocks_per_sm) {
@@ -158,6 +171,30 @@ cudaError_t cast_hist_occupancy(int form, const CastArgs &a, int block, int *blo
 cudaError_t launch_cast_hist(int form, const CastArgs &a, int grid, int block, cudaStream_t s) {
   if (form == kFormPlain) return launch_t<kFormPlain, false, HistMaker>(a, grid, block, s);
   return launch_t<kFormFp32, false, HistMaker>(a, grid, block, s);
+}
+
+namespace {
+__global__ void k_per_volume_rect(const double *__restrict__ src, double *__restrict__ dst, int64_t n,
+                                  int64_t first, int32_t nx, int32_t ny, int64_t ncells,
+                                  const double *__restrict__ wx, const double *__restrict__ wy,
+                                  const double *__restrict__ wz) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = (first + i) % ncells;
+    const int64_t ix = cell % nx, iy = (cell / nx) % ny, iz = cell / ((int64_t)nx * ny);
+    dst[i] = src[i] / (wx[ix] * wy[iy] * wz[iz]);
+  }
+}
+}  // namespace
+
+cudaError_t launch_per_volume_rect(const double *src, double *dst, int64_t n, int64_t first, int32_t nx,
+                                   int32_t ny, int64_t ncells, const double *wx, const double *wy,
+                                   const double *wz, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  k_per_volume_rect<<<grid, 256, 0, s>>>(src, dst, n, first, nx, ny, ncells, wx, wy, wz);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_scale_copy(const double *src, double *dst, int64_t n, double scale,

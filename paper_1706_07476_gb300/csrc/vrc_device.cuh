@@ -417,6 +417,126 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &M, float px, float p
   return nseg;
 }
 
+// Plane j on axis k of a rectilinear mesh.
+__device__ __forceinline__ df mesh_plane(const MeshDev &M, int k, int j) {
+  const float2 e = __ldg(M.edge[k] + j);
+  return {e.x, e.y};
+}
+
+// Cell index on axis k of a rectilinear mesh holding coordinate c:
+// edge[j] <= c < edge[j+1] by binary search, clamped to 0..n-1.
+__device__ __forceinline__ int locate_rect(const MeshDev &M, int k, df c) {
+  const int n = M.n[k];
+  if (!df_lt(c, mesh_plane(M, k, n))) return n - 1;
+  if (df_lt(c, mesh_plane(M, k, 0))) return 0;
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (df_lt(c, mesh_plane(M, k, mid))) hi = mid; else lo = mid;
+  }
+  return lo;
+}
+
+// cast_ray on a rectilinear mesh (planes at given positions per axis).  The
+// crossing of plane j on axis k, (edge_k[j] - p_k) * (1/d_k), is evaluated
+// in double-float from the plane index at every step (never accumulated);
+// the walk leaves the mesh when the stepped axis crosses its last plane.
+template <int FORM, typename Sink>
+__device__ __forceinline__ uint32_t cast_ray_rect(const MeshDev &M, float px, float py, float pz,
+                                                  float u, float v, float w, float wt, float dn,
+                                                  const Sink &sink, const float *sg,
+                                                  const typename Attenuation<FORM>::inv_t *inv,
+                                                  int stride, bool *overflow) {
+  const float p[3] = {px, py, pz};
+  const float d[3] = {u, v, w};
+  const df inf = {INFINITY, 0.f};
+  df R[3];
+  df s_in = {0.f, 0.f}, s_out = inf;
+  bool miss = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const df D0 = df_add_f(mesh_plane(M, k, 0), -p[k]);
+    const df Dn = df_add_f(mesh_plane(M, k, M.n[k]), -p[k]);
+    if (d[k] == 0.f) {
+      R[k] = {0.f, 0.f};
+      if (df_pos(D0) || !df_pos(Dn)) miss = true;  // p < lo or p >= hi
+    } else {
+      R[k] = df_rcp(d[k]);
+      df a = df_mul(D0, R[k]);
+      df b = df_mul(Dn, R[k]);
+      if (d[k] < 0.f) { df t = a; a = b; b = t; }
+      if (df_lt(s_in, a)) s_in = a;
+      if (df_lt(b, s_out)) s_out = b;
+    }
+  }
+  if (miss || !df_lt(s_in, s_out)) return 0;
+
+  // per axis: J = index of the next plane ahead, last = the plane that
+  // leaves the mesh, js = +-1 plane step
+  df S[3];
+  int J[3], last[3], js[3], cst[3];
+  int cell = 0;
+  const int cstride[3] = {1, M.n[0], M.n[0] * M.n[1]};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    df c = {p[k], 0.f};
+    if (s_in.hi > 0.f && d[k] != 0.f) c = df_add(c, df_mul_f(s_in, d[k]));
+    const int ik = locate_rect(M, k, c);
+    cell += ik * cstride[k];
+    if (d[k] == 0.f) {
+      S[k] = inf; J[k] = 0; last[k] = -1; js[k] = 0; cst[k] = 0;
+    } else {
+      const bool fwd = d[k] > 0.f;
+      J[k] = fwd ? ik + 1 : ik;
+      last[k] = fwd ? M.n[k] : 0;
+      js[k] = fwd ? 1 : -1;
+      cst[k] = fwd ? cstride[k] : -cstride[k];
+      S[k] = df_mul(df_add_f(mesh_plane(M, k, J[k]), -p[k]), R[k]);
+    }
+  }
+
+  Attenuation<FORM> att(wt);
+  df s_cur = s_in;
+  unsigned mat = __ldg(M.mat + cell);
+  uint32_t nseg = 0;
+  const int max_steps = M.n[0] + M.n[1] + M.n[2] + 3;
+  for (int step = 0;; ++step) {
+    const bool y_first = df_lt(S[1], S[0]);
+    df Sk = y_first ? S[1] : S[0];
+    const bool z_first = df_lt(S[2], Sk);
+    if (z_first) Sk = S[2];
+    const int k = z_first ? 2 : (y_first ? 1 : 0);
+    const int Jk = k == 0 ? J[0] : k == 1 ? J[1] : J[2];
+    const bool leaving = Jk == (k == 0 ? last[0] : k == 1 ? last[1] : last[2]);
+    const int ncell = cell + (k == 0 ? cst[0] : k == 1 ? cst[1] : cst[2]);
+    const unsigned nmat = leaving ? 0u : __ldg(M.mat + ncell);
+
+    const float l = fmaxf(df_diff(Sk, s_cur), 0.f) * dn;
+    typename Attenuation<FORM>::score_t sc;
+    if constexpr (FORM == kFormFp32) {
+      const float2 si = *reinterpret_cast<const float2 *>(sg + mat * stride);
+      sc = att.score(si.x, si.y, l);
+    } else {
+      sc = att.score(sg[mat * stride], inv[mat * stride], l);
+    }
+    if (sc != 0) sink.add(cell, Attenuation<FORM>::to_double(sc));
+    nseg += l > 0.f;
+
+    if (leaving) break;
+    if (step >= max_steps) { *overflow = true; break; }
+    s_cur = Sk;
+    cell = ncell;
+    mat = nmat;
+    const int Jn = Jk + (k == 0 ? js[0] : k == 1 ? js[1] : js[2]);
+    const df Sn = df_mul(df_add_f(mesh_plane(M, k, Jn), -p[k]), k == 0 ? R[0] : k == 1 ? R[1] : R[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a == k) { J[a] = Jn; S[a] = Sn; }
+    }
+  }
+  return nseg;
+}
+
 // The eight fields of ray r (SoA or 32-byte records).
 __device__ __forceinline__ void load_ray(const RayPtrs &R, int64_t r, float (&f)[8]) {
   if (R.aos) {
@@ -435,7 +555,7 @@ struct RayCounts {
 };
 
 // One ray of a cast: validation, group, cross sections, walk and score.
-template <int FORM, bool SURR = false, typename Maker = TallyMaker>
+template <int FORM, bool SURR = false, typename Maker = TallyMaker, bool RECT = false>
 __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int32_t *hash_s,
                                          const double *edges, float *sig_s,
                                          typename Attenuation<FORM>::inv_t *inv_s, int stride,
@@ -476,8 +596,12 @@ __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int
   }
   if (from_table) xs_lookup(a.xs, hash_s, E, sig_s, inv_s, stride);
   bool ovf = false;
-  c.seg += cast_ray<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, Maker::make(a, r, g), sig_s, inv_s,
-                          stride, &ovf);
+  if constexpr (RECT)
+    c.seg += cast_ray_rect<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, Maker::make(a, r, g), sig_s, inv_s,
+                                 stride, &ovf);
+  else
+    c.seg += cast_ray<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, Maker::make(a, r, g), sig_s, inv_s,
+                            stride, &ovf);
   c.ovf += ovf;
 }
 

@@ -11,6 +11,29 @@ namespace vrc {
 
 namespace {
 
+__device__ __forceinline__ double plane_lo(const BoundGeom &G, int k) {
+  return G.e[k] ? G.e[k][0] : G.lo[k];
+}
+__device__ __forceinline__ double plane_hi(const BoundGeom &G, int k) {
+  return G.e[k] ? G.e[k][G.n[k]] : G.lo[k] + G.h[k] * G.n[k];
+}
+
+// Cell index on axis k of coordinate q, clamped (uniform: floor; rectilinear:
+// binary search on the plane positions).
+__device__ __forceinline__ double cell_of(const BoundGeom &G, int k, double q) {
+  const int n = G.n[k];
+  if (!G.e[k]) return fmin(fmax(floor((q - G.lo[k]) / G.h[k]), 0.0), n - 1.0);
+  const double *e = G.e[k];
+  if (!(q >= e[0])) return 0.0;
+  if (q >= e[n]) return n - 1.0;
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (e[mid] <= q) lo = mid; else hi = mid;
+  }
+  return (double)lo;
+}
+
 // Upper bound of the cells one ray crosses: the ray p + s d is clipped to
 // the box in float64, and the cell indices at its entry and exit differ by
 // the planes it crosses on each axis; one cell more, plus one per axis for
@@ -22,7 +45,7 @@ __device__ __forceinline__ unsigned long long ray_bound(const BoundGeom &G, cons
   if (!(d[0] != 0.0 || d[1] != 0.0 || d[2] != 0.0)) return 0;
   double s_in = 0.0, s_out = INFINITY;
   for (int k = 0; k < 3; ++k) {
-    const double lo = G.lo[k], hi = G.lo[k] + G.h[k] * G.n[k];
+    const double lo = plane_lo(G, k), hi = plane_hi(G, k);
     if (d[k] == 0.0) {
       if (!(p[k] >= lo && p[k] < hi)) return 0;
     } else {
@@ -36,9 +59,8 @@ __device__ __forceinline__ unsigned long long ray_bound(const BoundGeom &G, cons
   unsigned long long cells = 1 + 3;
   for (int k = 0; k < 3; ++k) {
     if (d[k] == 0.0) continue;
-    const double n = G.n[k];
-    const double a = fmin(fmax(floor((p[k] + s_in * d[k] - G.lo[k]) / G.h[k]), 0.0), n - 1.0);
-    const double b = fmin(fmax(floor((p[k] + s_out * d[k] - G.lo[k]) / G.h[k]), 0.0), n - 1.0);
+    const double a = cell_of(G, k, p[k] + s_in * d[k]);
+    const double b = cell_of(G, k, p[k] + s_out * d[k]);
     cells += (unsigned long long)fabs(b - a);
   }
   return cells;

@@ -23,7 +23,9 @@ struct df {
   float hi, lo;
 };
 
-// Uniform Cartesian mesh, geometry split into double-float pairs on the host.
+// Cartesian mesh, geometry split into double-float pairs on the host.  A
+// uniform mesh has planes at org + j h; a rectilinear one (rect != 0) at
+// edge[k][j], j = 0..n[k], each plane position as a (hi, lo) float pair.
 struct MeshDev {
   int32_t n[3];
   int64_t ncells;
@@ -32,6 +34,8 @@ struct MeshDev {
   df h[3];            // dx, dy, dz
   df inv_h[3];        // 1/dx, 1/dy, 1/dz
   const uint8_t *mat; // [nz][ny][nx]
+  const float2 *edge[3];
+  int32_t rect;
 };
 
 // Cross sections on the union energy grid of all materials.
@@ -111,6 +115,11 @@ cudaError_t launch_cast(int form, const CastArgs &a, int grid, int block, cudaSt
 cudaError_t cast_occupancy(int form, const CastArgs &a, int block, int *blocks_per_sm);
 cudaError_t launch_scale_copy(const double *src, double *dst, int64_t n, double scale,
                               cudaStream_t s);
+// Per-volume copy of a rectilinear tally slice: dst[i] = src[i] / volume of
+// cell (first + i) mod ncells, volumes from per-axis widths w[k] (device).
+cudaError_t launch_per_volume_rect(const double *src, double *dst, int64_t n, int64_t first, int32_t nx,
+                                   int32_t ny, int64_t ncells, const double *wx, const double *wy,
+                                   const double *wz, cudaStream_t s);
 cudaError_t launch_fold_moments(double *tally, double *s1, double *s2, int64_t n, cudaStream_t s);
 // Per-history moments (vrc_history.cu and vrc_cast.cu): an upper bound of
 // the segments of a ray batch (added to *bound), the cast that scores into
@@ -118,6 +127,7 @@ cudaError_t launch_fold_moments(double *tally, double *s1, double *s2, int64_t n
 struct BoundGeom {
   double lo[3], h[3];
   int32_t n[3];
+  const double *e[3];  // rectilinear plane positions (device), or nullptr
 };
 cudaError_t launch_segment_bound(const BoundGeom &g, const RayPtrs &rays, unsigned long long *bound,
                                  int num_sms, cudaStream_t s);

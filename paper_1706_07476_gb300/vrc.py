@@ -52,6 +52,13 @@ class vrc_mesh_desc(C.Structure):
                 ("group_edges", C.c_void_p)]
 
 
+class vrc_rect_mesh_desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("x_edges", C.c_void_p), ("y_edges", C.c_void_p), ("z_edges", C.c_void_p),
+                ("material", C.c_void_p), ("n_materials", C.c_int32), ("n_groups", C.c_int32),
+                ("group_edges", C.c_void_p)]
+
+
 class vrc_rays(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in RAY_FIELDS] + [("n", C.c_int64), ("on_device", C.c_int32)]
 
@@ -76,6 +83,7 @@ def _load():
         "vrc_read_tally": ([P, P, I64, I32, P], C.c_int),
         "vrc_tally_device_ptr": ([P], C.c_void_p),
         "vrc_context_stream": ([P], C.c_void_p),
+        "vrc_create_rect_mesh": ([P, P, P], C.c_int),
         "vrc_reset_tally": ([P, P], C.c_int),
         "vrc_set_options": ([P, P], C.c_int),
         "vrc_destroy": ([P], None),
@@ -209,6 +217,22 @@ def vrc_create_mesh(mesh, n_materials: int, group_edges=None, options: vrc_optio
     _check(_lib.vrc_create_mesh(C.byref(d), None if options is None else C.byref(options),
                                 C.byref(h)))
     return Context(h, mesh.nx * mesh.ny * mesh.nz, d.n_groups, (mesh.dx, mesh.dy, mesh.dz))
+
+
+def vrc_create_rect_mesh(mesh, n_materials: int, group_edges=None,
+                         options: vrc_options | None = None) -> Context:
+    """mesh: object with float64 plane arrays xe, ye, ze and uint8 material [nz][ny][nx]."""
+    mat = np.ascontiguousarray(mesh.material, dtype=np.uint8).reshape(-1)
+    xe, ye, ze = (np.ascontiguousarray(e, np.float64) for e in (mesh.xe, mesh.ye, mesh.ze))
+    edges = None if group_edges is None else np.ascontiguousarray(group_edges, np.float64)
+    d = vrc_rect_mesh_desc(len(xe) - 1, len(ye) - 1, len(ze) - 1, xe.ctypes.data, ye.ctypes.data,
+                           ze.ctypes.data, mat.ctypes.data, int(n_materials),
+                           1 if edges is None else len(edges) - 1,
+                           None if edges is None else edges.ctypes.data)
+    h = C.c_void_p()
+    _check(_lib.vrc_create_rect_mesh(C.byref(d), None if options is None else C.byref(options),
+                                     C.byref(h)))
+    return Context(h, (len(xe) - 1) * (len(ye) - 1) * (len(ze) - 1), d.n_groups, None)
 
 
 def vrc_load_xs(ctx: Context, material: int, E, sigma):
@@ -580,8 +604,12 @@ def vrc_destroy(ctx: Context):
 
 
 def context_for(problem, options: vrc_options | None = None) -> Context:
-    """vrc_create_mesh + vrc_load_xs for a vrc_workloads.Problem."""
-    ctx = vrc_create_mesh(problem.mesh, problem.n_materials, problem.group_edges, options)
+    """vrc_create_mesh (or vrc_create_rect_mesh for a mesh with plane arrays)
+    + vrc_load_xs for a vrc_workloads.Problem."""
+    if getattr(problem.mesh, "xe", None) is not None:
+        ctx = vrc_create_rect_mesh(problem.mesh, problem.n_materials, problem.group_edges, options)
+    else:
+        ctx = vrc_create_mesh(problem.mesh, problem.n_materials, problem.group_edges, options)
     for m, t in enumerate(problem.tables):
         if t is None:
             vrc_load_xs(ctx, m, None, None)

@@ -93,6 +93,29 @@ int main(void) {
   vrc_batch_destroy(NULL);
   EXPECT(vrc_cast_batched(NULL, &r, 1, NULL) == VRC_ERR_ARG);
   EXPECT(vrc_sort_rays_static(NULL, &r, NULL, NULL) == VRC_ERR_ARG);
+
+  /* rectilinear meshes: edge checks come before any device work */
+  double xe[3] = {0.0, 0.5, 2.0}, ye[3] = {-1.0, 0.0, 1.0}, ze[3] = {0.0, 3.0, 4.0};
+  vrc_rect_mesh_desc rd = {2, 2, 2, xe, ye, ze, mat, 2, 1, NULL};
+  EXPECT(vrc_create_rect_mesh(NULL, NULL, &c) == VRC_ERR_ARG && c == NULL);
+  EXPECT(vrc_create_rect_mesh(&rd, NULL, NULL) == VRC_ERR_ARG);
+  vrc_rect_mesh_desc rb = rd; rb.y_edges = NULL;
+  EXPECT(vrc_create_rect_mesh(&rb, NULL, &c) == VRC_ERR_ARG);
+  xe[1] = 0.0; /* not strictly ascending */
+  EXPECT(vrc_create_rect_mesh(&rd, NULL, &c) == VRC_ERR_ARG);
+  EXPECT(strstr(vrc_last_error(), "ascending") != NULL);
+  xe[1] = NAN;
+  EXPECT(vrc_create_rect_mesh(&rd, NULL, &c) == VRC_ERR_ARG);
+  xe[1] = 0.5;
+  rb = rd; rb.nz = 0;
+  EXPECT(vrc_create_rect_mesh(&rb, NULL, &c) == VRC_ERR_ARG);
+
+  /* moments and per-history casts on a NULL context */
+  uint32_t hist[1] = {0};
+  EXPECT(vrc_moments_enable(NULL, VRC_MOMENTS_HISTORY) == VRC_ERR_ARG);
+  EXPECT(vrc_moments_fold(NULL, NULL) == VRC_ERR_ARG);
+  EXPECT(vrc_cast_histories(NULL, &r, hist, 1, NULL) == VRC_ERR_ARG);
+  EXPECT(vrc_context_stream(NULL) == NULL);
   EXPECT(vrc_version() >= 100);
   EXPECT(vrc_device_count() >= 0);
 
