@@ -35,6 +35,13 @@ WORKLOAD = ("slab256: 256^3 mesh of 1 cm cells, 8 materials with 20,000-point ta
             "(200 Lorentzian resonances each), 16 random axis-aligned slabs, 2^24 rays "
             "(uniform positions, isotropic directions, log-uniform energies, lognormal(0,0.5) "
             "weights), 16 log-uniform energy groups, seed 1")
+GRADED = ("graded: 16x16-pin assembly (pitch 1.26 cm; fuel, void gap, cladding, moderator) on a "
+          "rectilinear 420x420x5 mesh, 0.6 mm cells over the assembly growing 1.1x per cell to 2 cm "
+          "through a 30 cm solution + graphite reflector, 6 materials (5 with 20,000-point tables), "
+          "2^24 rays (70% in fuel discs), 1/E energies, one group, seed 5")
+HISTORY = ("history: the slab256 rays grouped into histories of 1..15 consecutive rays "
+           "(uniform, mean 8), cast per history in 16 calls of 2^20 rays each; per-history "
+           "moments S1 += x_h, S2 += x_h^2 per (group, cell)")
 METRIC = "ray-cell segments/s at <=1e-4 tally rel. err vs FP64 oracle; % HBM roofline"
 UNIT = "segments/s"
 # Algorithmic bytes: per segment 8 B tally read + 8 B tally write + 1 B material
@@ -53,7 +60,8 @@ def parse():
     ap.add_argument("--sort", type=int, default=-1, help="ray sorting: -1 auto, 0 off, 1 on")
     ap.add_argument("--n-rays", type=int, default=1 << 24)
     ap.add_argument("--mesh", type=int, default=256)
-    ap.add_argument("--workload", choices=["slab256", "batched", "stream"], default="slab256")
+    ap.add_argument("--workload", choices=["slab256", "batched", "stream", "graded", "history"],
+                    default="slab256")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity-sample", action="store_true")
@@ -71,7 +79,15 @@ def dist_env():
 
 
 def workload(args):
+    if args.workload == "graded":
+        return W.graded_assembly(seed=5, n_rays=args.n_rays)
     return W.slab_room(seed=1, n=args.mesh, n_rays=args.n_rays)
+
+
+def workload_text(args, prob):
+    if args.workload == "graded":
+        return GRADED, f"float64 [{prob.n_groups}][{prob.mesh.nz}][{prob.mesh.ny}][{prob.mesh.nx}]"
+    return WORKLOAD, "float64 [16][256^3] (2 GiB)"
 
 
 # --------------------------------------------------------------------------- clocks
@@ -146,11 +162,12 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def profiled_traffic(kernel_tag: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current cast kernel source (matched by the recorded source hash)."""
+def profiled_traffic(kernel_tag: str, workload_tag: str):
+    """DRAM bytes per launch from a committed ncu summary of this kernel on
+    this workload, if it was taken on the current cast kernel source (matched
+    by the recorded source hash)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", f"{kernel_tag}_slab256.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}_{workload_tag}.md")
     try:
         text = open(path).read()
     except OSError:
@@ -183,7 +200,7 @@ def cpu_baseline(prob, target_s: float, oracle):
             break
         n = int(min(prob.n_rays, n * min(64.0, 0.9 * target_s / max(dt, 1e-3))))
     return dict(value=st["segments"] / dt, unit=UNIT, cores=st["threads"], kind="oracle",
-                sample=f"first {n} of the {prob.n_rays} rays of the slab256 workload "
+                sample=f"first {n} of the {prob.n_rays} rays of the {prob.name} workload "
                        f"({st['segments']} segments, {dt:.1f} s)"), tally, n
 
 
@@ -376,6 +393,88 @@ def run_stream(args, rank, world, local):
     return 0
 
 
+# --------------------------------------------------------------------------- per-history moments
+
+def run_history(args, rank, world, local):
+    """Per-history moments: every step casts the slab256 rays in 16 calls of
+    2^20 rays through vrc_cast_histories (segment bound, cast into the
+    history table, fold into S1/S2), FP32 form, timed with CUDA events on the
+    calling stream; the plain tally cast of the same rays is timed beside it."""
+    import torch
+    from paper_1706_07476_gb300 import vrc
+    torch.cuda.set_device(local)
+    prob = workload(args)
+    rng = np.random.default_rng(6)
+    lengths = rng.integers(1, 16, size=prob.n_rays // 4)
+    hist = np.repeat(np.arange(lengths.size, dtype=np.uint32), lengths)[:prob.n_rays]
+    chunk = 1 << 20
+    starts = list(range(0, prob.n_rays, chunk))
+    # calls end on a history boundary: move each cut back to its history's first ray
+    cuts = [0]
+    for s0 in starts[1:]:
+        c = s0
+        while c > cuts[-1] and hist[c] == hist[c - 1]:
+            c -= 1
+        cuts.append(c)
+    cuts.append(prob.n_rays)
+    dev = {k: torch.from_numpy(v).cuda() for k, v in prob.rays.items()}
+    hdev = torch.from_numpy(hist.view(np.int32)).cuda()
+    parts = [({k: v[a:b] for k, v in dev.items()}, hdev[a:b], int(hist[b - 1]) - int(hist[a]) + 1)
+             for a, b in zip(cuts[:-1], cuts[1:])]
+    ctx = vrc.context_for(prob, vrc.vrc_default_options(form=vrc.VRC_FORM_FP32, sort=0, device=local))
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    def step_hist():
+        for r, h, nh in parts:
+            vrc.vrc_cast_histories(ctx, r, h, nh, stream=stream)
+
+    def step_tally():
+        for r, _, _ in parts:
+            vrc.vrc_cast_rays(ctx, r, stream=stream)
+
+    out = {}
+    for name, fn, mode in (("tally", step_tally, vrc.VRC_MOMENTS_OFF), ("history", step_hist, vrc.VRC_MOMENTS_HISTORY)):
+        vrc.vrc_moments_enable(ctx, mode)
+        for _ in range(args.warmup):
+            fn()
+        stream.synchronize()
+        vrc.vrc_reset_tally(ctx, stream)
+        vrc.vrc_moments_enable(ctx, mode)
+        torch.cuda.synchronize()
+        steps = max(1, min(args.steps, 10))
+        l0 = vrc.vrc_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        wall = time.perf_counter() - t0
+        rc, st = vrc.vrc_sync(ctx, stream)
+        assert rc == vrc.VRC_OK and st["overflow"] == 0, (rc, st)
+        dt = e0.elapsed_time(e1) / 1e3
+        out[name] = {"segments_per_s": st["segments"] / dt, "ms_per_step": 1e3 * dt / steps,
+                     "wall_ms_per_step": 1e3 * wall / steps, "segments_per_step": st["segments"] / steps,
+                     "steps": steps, "launches": vrc.vrc_launch_count() - l0}
+    _, _, samples = vrc.vrc_moments_read(ctx)
+    H = out["history"]
+    line = {
+        "metric": "per-history moments: ray-cell segments/s", "value": H["segments_per_s"],
+        "unit": UNIT, "n_gpus": world, "steps": H["steps"], "warmup": args.warmup,
+        "ms_per_step": H["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": HISTORY, "rays_per_step": prob.n_rays, "calls_per_step": len(parts),
+                   "histories_per_step": int(hist[-1]) + 1, "form": "fp32", "sort": 0},
+        "history_over_tally_time": H["ms_per_step"] / out["tally"]["ms_per_step"],
+        "modes": out, "histories_folded": samples, "gpu_launches": H["launches"],
+    }
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -387,6 +486,8 @@ def main():
         return run_batched(args, rank, world, local)
     if args.workload == "stream":
         return run_stream(args, rank, world, local)
+    if args.workload == "history":
+        return run_history(args, rank, world, local)
 
     import torch
     import torch.distributed as dist
@@ -504,7 +605,7 @@ def main():
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     roof = {"bound": "hbm", "achieved": R["alg_gbs"], "peak": hbm, "unit": "GB/s",
-            "frac": R["alg_gbs"] / hbm, "traffic": profiled_traffic(f"k_cast_{head}"),
+            "frac": R["alg_gbs"] / hbm, "traffic": profiled_traffic(f"k_cast_{head}", args.workload),
             "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)",
             "algorithmic_bytes": f"{BYTES_PER_SEGMENT} B/segment + {BYTES_PER_RAY} B/ray",
             "kernel": f"k_cast<{head}>", "kernel_ms": R["kernel_ms"]}
@@ -531,10 +632,12 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": R["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if head == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "rays_per_step": prob.n_rays,
+        "config": {"workload": workload_text(args, prob)[0], "rays_per_step": prob.n_rays,
                    "segments_per_step": R["segments_per_step"], "form": head,
-                   "sort": args.sort, "tally": "float64 [16][256^3] (2 GiB)",
-                   "l2": "inputs larger than L2 (512 MiB rays, 2 GiB tally, 16 MiB mesh); no flush",
+                   "sort": args.sort, "tally": workload_text(args, prob)[1],
+                   "l2": ("inputs larger than L2 (512 MiB rays, 2 GiB tally, 16 MiB mesh); no flush"
+                          if args.workload == "slab256" else
+                          "inputs larger than L2 (512 MiB rays); tally 7 MB; no flush"),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "forms": results,
         "roofline": roof,
