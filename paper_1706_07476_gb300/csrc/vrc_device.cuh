@@ -257,28 +257,58 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
-// The per-history table: the score of (history, bin) is summed in one slot,
-// found by linear probing from mix64(key); the first writer claims an empty
-// slot with a compare-and-swap.  At most cap probes; a full table sets
-// kStatusTableFull and drops the score (the host sizes the table at twice an
-// upper bound of the segments, so this does not happen in practice).
+// One 128-bit compare-and-swap on a 16-byte slot (lo = first 8 bytes):
+// returns the slot's previous contents in (old_lo, old_hi).
+__device__ __forceinline__ void cas128(unsigned long long *slot, unsigned long long cmp_lo,
+                                       unsigned long long cmp_hi, unsigned long long new_lo,
+                                       unsigned long long new_hi, unsigned long long &old_lo,
+                                       unsigned long long &old_hi) {
+  asm volatile(
+      "{\n\t.reg .b128 d, b, c;\n\t"
+      "mov.b128 b, {%2, %3};\n\t"
+      "mov.b128 c, {%4, %5};\n\t"
+      "atom.global.cas.b128 d, [%6], b, c;\n\t"
+      "mov.b128 {%0, %1}, d;\n\t}"
+      : "=l"(old_lo), "=l"(old_hi)
+      : "l"(cmp_lo), "l"(cmp_hi), "l"(new_lo), "l"(new_hi), "l"(slot)
+      : "memory");
+}
+
+// The per-history table: the score of (history, bin) is summed in one
+// 16-byte slot (key + 1, value bits), found by linear probing from
+// mix64(key).  Every access is a 128-bit compare-and-swap on the whole slot:
+// the first, expecting an empty slot, claims it with the score in one step;
+// a slot that already holds the key is updated by compare-and-swap from the
+// contents that the failed claim returned.  Each failed update means another
+// thread's update went in; after kMaxCasRetries of them, or after probing the
+// whole table, kStatusTableFull is set and the score dropped (the host sizes
+// the table at twice an upper bound of the segments, so a full table does not
+// happen in practice).
+constexpr int kMaxCasRetries = 1 << 16;
+
 struct HistSink {
   HistTable t;
   unsigned long long base;  // (history << 32) + group * ncells + 1
   unsigned int *status;
   __device__ __forceinline__ void add(int cell, double v) const {
     const unsigned long long key = base + (unsigned)cell;
+    const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
     unsigned long long i = mix64(key) & t.mask;
     for (unsigned long long probe = 0; probe <= t.mask; ++probe) {
       unsigned long long *slot = t.e + 2 * i;
-      unsigned long long k = *reinterpret_cast<volatile unsigned long long *>(slot);
-      if (k == 0ull) {
-        k = atomicCAS(slot, 0ull, key);
-        if (k == 0ull) k = key;
-      }
-      if (k == key) {
-        atomicAdd(reinterpret_cast<double *>(slot + 1), v);
-        return;
+      unsigned long long ok, ov;
+      cas128(slot, 0ull, 0ull, key, vb, ok, ov);
+      if (ok == 0ull && ov == 0ull) return;  // claimed with the score
+      if (ok == key) {
+        for (int it = 0; it < kMaxCasRetries; ++it) {
+          const unsigned long long nv =
+              (unsigned long long)__double_as_longlong(__longlong_as_double((long long)ov) + v);
+          unsigned long long k2, v2;
+          cas128(slot, key, ov, key, nv, k2, v2);
+          if (v2 == ov) return;
+          ov = v2;  // another update of this slot went in first
+        }
+        break;
       }
       i = (i + 1) & t.mask;
     }
