@@ -42,6 +42,9 @@ GRADED = ("graded: 16x16-pin assembly (pitch 1.26 cm; fuel, void gap, cladding, 
 HISTORY = ("history: the slab256 rays grouped into histories of 1..15 consecutive rays "
            "(uniform, mean 8), cast per history in 16 calls of 2^20 rays each; per-history "
            "moments S1 += x_h, S2 += x_h^2 per (group, cell)")
+DETECTORS = ("detectors: the slab256 rays as collision events, each scored at 8 detector "
+             "points (a 2x2x2 lattice at 1/4 and 3/4 of the box) by the next-event estimator "
+             "wt exp(-tau)/(4 pi R^2), tau by the grid walk from the event to the detector")
 METRIC = "ray-cell segments/s at <=1e-4 tally rel. err vs FP64 oracle; % HBM roofline"
 UNIT = "segments/s"
 # Algorithmic bytes: per segment 8 B tally read + 8 B tally write + 1 B material
@@ -60,7 +63,8 @@ def parse():
     ap.add_argument("--sort", type=int, default=-1, help="ray sorting: -1 auto, 0 off, 1 on")
     ap.add_argument("--n-rays", type=int, default=1 << 24)
     ap.add_argument("--mesh", type=int, default=256)
-    ap.add_argument("--workload", choices=["slab256", "batched", "stream", "graded", "history"],
+    ap.add_argument("--workload", choices=["slab256", "batched", "stream", "graded", "history",
+                                           "detectors"],
                     default="slab256")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -475,6 +479,56 @@ def run_history(args, rank, world, local):
     return 0
 
 
+# --------------------------------------------------------------------------- next-event detectors
+
+def run_detectors(args, rank, world, local):
+    """Next-event estimator: every step scores all slab256 rays at 8 detector
+    points through vrc_detector_flux (device rays, both forms), timed with
+    CUDA events on the calling stream; the unit is (ray, detector) pairs."""
+    import torch
+    from paper_1706_07476_gb300 import vrc
+    torch.cuda.set_device(local)
+    prob = workload(args)
+    hi = np.array(prob.mesh.hi)
+    det = np.array([[fx, fy, fz] for fz in (0.25, 0.75) for fy in (0.25, 0.75) for fx in (0.25, 0.75)]) * hi
+    dev = {k: torch.from_numpy(v).cuda() for k, v in prob.rays.items()}
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {}
+    launches = 0
+    for form in [f.strip() for f in args.forms.split(",") if f.strip()]:
+        fid = vrc.VRC_FORM_FP32 if form == "fp32" else vrc.VRC_FORM_PLAIN
+        ctx = vrc.context_for(prob, vrc.vrc_default_options(form=fid, device=local))
+        for _ in range(args.warmup):
+            vrc.vrc_detector_flux(ctx, dev, det, stream=stream)
+        steps = max(1, min(args.steps, 5))
+        l0 = vrc.vrc_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            flux = vrc.vrc_detector_flux(ctx, dev, det, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        launches = vrc.vrc_launch_count() - l0
+        dt = e0.elapsed_time(e1) / 1e3 / steps
+        rc, _ = vrc.vrc_sync(ctx)
+        assert rc == vrc.VRC_OK, rc
+        out[form] = {"pairs_per_s": prob.n_rays * len(det) / dt, "ms_per_step": 1e3 * dt,
+                     "flux_total": float(flux.sum())}
+        ctx.close()
+    head = out[list(out)[-1]]
+    line = {
+        "metric": "next-event detector estimates: (ray, detector) pairs/s", "value": head["pairs_per_s"],
+        "unit": "pairs/s", "n_gpus": world, "steps": max(1, min(args.steps, 5)), "warmup": args.warmup,
+        "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if list(out)[-1] == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": DETECTORS, "rays_per_step": prob.n_rays, "detectors": len(det)},
+        "forms": out, "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -488,6 +542,8 @@ def main():
         return run_stream(args, rank, world, local)
     if args.workload == "history":
         return run_history(args, rank, world, local)
+    if args.workload == "detectors":
+        return run_detectors(args, rank, world, local)
 
     import torch
     import torch.distributed as dist
