@@ -166,6 +166,9 @@ __device__ __forceinline__ double f2d_bits(float f) {
 // Eq. 4 along one ray, in the two precision forms.  score() returns the
 // segment's contribution as a double; an exact +0 (the transmitted fraction
 // has underflowed) needs no tally update, since adding +0 changes no bit.
+// Once the transmitted fraction T is exactly 0 it stays 0 (the optical depth
+// only grows), so every later score of the ray is exactly +0: score() then
+// returns at once and the walk goes on only to cross (and count) the cells.
 // ---------------------------------------------------------------------------
 template <int FORM>
 struct Attenuation;
@@ -182,6 +185,7 @@ struct Attenuation<kFormPlain> {
   double wt;
   __device__ __forceinline__ explicit Attenuation(float w) : wt((double)w) {}
   __device__ __forceinline__ double score(float sig, double inv, float l) {
+    if (T == 0.0) return 0.0;
     double path, factor;
     if (sig > 0.f) {
       double x = (double)sig * (double)l;  // exact: a float product fits a double
@@ -196,6 +200,7 @@ struct Attenuation<kFormPlain> {
     T *= factor;
     return s;
   }
+  __device__ __forceinline__ bool dead() const { return T == 0.0; }
   __device__ __forceinline__ static double to_double(double s) { return s; }
 };
 
@@ -203,9 +208,11 @@ struct Attenuation<kFormPlain> {
 // float32; only the tally accumulation stays float64.  One exponential per
 // segment: T = exp(-tau) at the cell exit is recomputed from the compensated
 // optical depth and carried as the next cell's entry value.  The path term
-// (1 - e^-x)/Sigma, x = Sigma l, is (T_in - T_out)/Sigma for x >= 1/2 (no
-// cancellation: T_out <= 0.61 T_in) and l (1 - e^-x)/x from the Taylor series
-// sum_k (-x)^k/(k+1)! to k = 8 below (truncation < 6e-10 at x = 1/2).
+// (1 - e^-x)/Sigma, x = Sigma l, is (T_in - T_out)/Sigma for x >= 1/8 (the
+// difference of two transmitted fractions within a few ulp loses at most a
+// factor 1/x = 8 of relative accuracy) and l (1 - e^-x)/x from the Taylor
+// series sum_k (-x)^k/(k+1)! to k = 6 below (truncation < 6e-11 at x = 1/8).
+// Both are formed and one is selected, so lanes do not diverge on x.
 template <>
 struct Attenuation<kFormFp32> {
   typedef float inv_t;
@@ -215,28 +222,23 @@ struct Attenuation<kFormFp32> {
   float wt;
   __device__ __forceinline__ explicit Attenuation(float w) : wt(w) {}
   __device__ __forceinline__ float score(float sig, float inv, float l) {
+    if (T == 0.f) return 0.f;
     if (!(sig > 0.f)) return wt * T * l;  // void: T unchanged
     const float x = sig * l;
     tau = df_add_f(tau, x);
     const float T_out = expf(-tau.hi) * (1.0f - tau.lo);
-    float s;
-    if (x < 0.5f) {
-      float q = 1.f / 362880.f;
-      q = fmaf(q, x, -1.f / 40320.f);
-      q = fmaf(q, x, 1.f / 5040.f);
-      q = fmaf(q, x, -1.f / 720.f);
-      q = fmaf(q, x, 1.f / 120.f);
-      q = fmaf(q, x, -1.f / 24.f);
-      q = fmaf(q, x, 1.f / 6.f);
-      q = fmaf(q, x, -0.5f);
-      q = fmaf(q, x, 1.f);
-      s = wt * T * (l * q);
-    } else {
-      s = wt * (T - T_out) * inv;
-    }
+    float q = -1.f / 5040.f;
+    q = fmaf(q, x, 1.f / 720.f);
+    q = fmaf(q, x, -1.f / 120.f);
+    q = fmaf(q, x, 1.f / 24.f);
+    q = fmaf(q, x, -1.f / 6.f);
+    q = fmaf(q, x, 0.5f);
+    q = fmaf(q, -x, 1.f);
+    const float a = x < 0.125f ? T * (l * q) : (T - T_out) * inv;
     T = T_out;
-    return s;
+    return wt * a;
   }
+  __device__ __forceinline__ bool dead() const { return T == 0.f; }
   __device__ __forceinline__ static double to_double(float s) { return f2d_bits(s); }
 };
 
@@ -417,17 +419,22 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &M, float px, float p
     const float mk = k == 0 ? m[0] : k == 1 ? m[1] : m[2];
     const bool leaving = mk == (k == 0 ? cnt[0] : k == 1 ? cnt[1] : cnt[2]);
     const int ncell = cell + (k == 0 ? cst[0] : k == 1 ? cst[1] : cst[2]);
-    const unsigned nmat = leaving ? 0u : __ldg(M.mat + ncell);  // prefetch the next cell
+    // FP32 form: once every score is +0 the walk skips the loads of the next
+    // cell's material and of sigma (the plain form measured faster keeping them)
+    const bool live = FORM == kFormFp32 ? !att.dead() : true;
+    const unsigned nmat = (leaving || !live) ? 0u : __ldg(M.mat + ncell);  // prefetch the next cell
 
     const float l = fmaxf(df_diff(Sk, s_cur), 0.f) * dn;
-    typename Attenuation<FORM>::score_t sc;
-    if constexpr (FORM == kFormFp32) {  // sigma and 1/sigma interleaved: one 8-byte load
-      const float2 si = *reinterpret_cast<const float2 *>(sg + mat * stride);
-      sc = att.score(si.x, si.y, l);
-    } else {
-      sc = att.score(sg[mat * stride], inv[mat * stride], l);
+    if (live) {
+      typename Attenuation<FORM>::score_t sc;
+      if constexpr (FORM == kFormFp32) {  // sigma and 1/sigma interleaved: one 8-byte load
+        const float2 si = *reinterpret_cast<const float2 *>(sg + mat * stride);
+        sc = att.score(si.x, si.y, l);
+      } else {
+        sc = att.score(sg[mat * stride], inv[mat * stride], l);
+      }
+      if (sc != 0) sink.add(cell, Attenuation<FORM>::to_double(sc));
     }
-    if (sc != 0) sink.add(cell, Attenuation<FORM>::to_double(sc));
     nseg += l > 0.f;
 
     if (leaving) break;
@@ -539,17 +546,20 @@ __device__ __forceinline__ uint32_t cast_ray_rect(const MeshDev &M, float px, fl
     const int Jk = k == 0 ? J[0] : k == 1 ? J[1] : J[2];
     const bool leaving = Jk == (k == 0 ? last[0] : k == 1 ? last[1] : last[2]);
     const int ncell = cell + (k == 0 ? cst[0] : k == 1 ? cst[1] : cst[2]);
-    const unsigned nmat = leaving ? 0u : __ldg(M.mat + ncell);
+    const bool live = FORM == kFormFp32 ? !att.dead() : true;
+    const unsigned nmat = (leaving || !live) ? 0u : __ldg(M.mat + ncell);
 
     const float l = fmaxf(df_diff(Sk, s_cur), 0.f) * dn;
-    typename Attenuation<FORM>::score_t sc;
-    if constexpr (FORM == kFormFp32) {
-      const float2 si = *reinterpret_cast<const float2 *>(sg + mat * stride);
-      sc = att.score(si.x, si.y, l);
-    } else {
-      sc = att.score(sg[mat * stride], inv[mat * stride], l);
+    if (live) {
+      typename Attenuation<FORM>::score_t sc;
+      if constexpr (FORM == kFormFp32) {
+        const float2 si = *reinterpret_cast<const float2 *>(sg + mat * stride);
+        sc = att.score(si.x, si.y, l);
+      } else {
+        sc = att.score(sg[mat * stride], inv[mat * stride], l);
+      }
+      if (sc != 0) sink.add(cell, Attenuation<FORM>::to_double(sc));
     }
-    if (sc != 0) sink.add(cell, Attenuation<FORM>::to_double(sc));
     nseg += l > 0.f;
 
     if (leaving) break;
