@@ -10,6 +10,11 @@ namespace vrc {
 namespace {
 
 constexpr float kInv4Pi = 0.0795774715459476678f;  // 1 / (4 pi)
+// Optical depths past which exp(-tau) is exactly 0: e^-750 is below half the
+// smallest float64 subnormal (e^-744.4) and e^-110 below half the smallest
+// float32 subnormal (e^-103.3); the walk to a detector stops there.
+constexpr float kTauZeroF64 = 750.f;
+constexpr float kTauZeroF32 = 110.f;
 
 template <int FORM>
 __global__ void __launch_bounds__(256) k_detectors(CastArgs a, const float *__restrict__ det, int n_det,
@@ -42,7 +47,8 @@ __global__ void __launch_bounds__(256) k_detectors(CastArgs a, const float *__re
       const float q[3] = {det[3 * k], det[3 * k + 1], det[3 * k + 2]};
       const float R2 = (q[0] - p[0]) * (q[0] - p[0]) + (q[1] - p[1]) * (q[1] - p[1]) + (q[2] - p[2]) * (q[2] - p[2]);
       if (!(R2 > 0.f)) continue;
-      const df tau = optical_depth(a.mesh, p, q, sig_s, stride, &ovf);
+      const df tau = optical_depth(a.mesh, p, q, sig_s, stride,
+                                   FORM == kFormPlain ? kTauZeroF64 : kTauZeroF32, &ovf);
       double v;
       if (FORM == kFormPlain)
         v = (double)f[7] * exp(-((double)tau.hi + (double)tau.lo)) * (double)kInv4Pi / (double)R2;

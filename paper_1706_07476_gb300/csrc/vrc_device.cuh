@@ -672,9 +672,12 @@ __device__ __forceinline__ void flush_counts(RayCounts c, unsigned long long *co
 // next-event estimator: the same double-float grid walk as cast_ray, with the
 // segment parametrised as p + s (q - p), s in [0, 1], and the last cell cut at
 // s = 1.  sg[mat * stride] holds sigma of each material for the ray's energy.
+// The walk stops early once tau.hi exceeds tau_zero, a depth at which the
+// caller's exp(-tau) is exactly 0 (tau only grows, so the result is the same).
 // Returns tau as a compensated float32 pair.
 __device__ __forceinline__ df optical_depth(const MeshDev &M, const float p[3], const float q[3],
-                                            const float *sg, int stride, bool *overflow) {
+                                            const float *sg, int stride, float tau_zero,
+                                            bool *overflow) {
   const float d[3] = {q[0] - p[0], q[1] - p[1], q[2] - p[2]};
   const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
   const df inf = {INFINITY, 0.f};
@@ -734,7 +737,7 @@ __device__ __forceinline__ df optical_depth(const MeshDev &M, const float p[3], 
     const float l = fmaxf(df_diff(s_end, s_cur), 0.f) * dn;
     const float sig = sg[__ldg(M.mat + cell) * stride];
     tau = df_add_f(tau, sig * l);
-    if (last) break;
+    if (last || tau.hi > tau_zero) break;
     if (step >= max_steps) { *overflow = true; break; }
     s_cur = Sk;
     cell += k == 0 ? cst[0] : k == 1 ? cst[1] : cst[2];
