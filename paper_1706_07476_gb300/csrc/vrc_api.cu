@@ -125,6 +125,12 @@ struct vrc_ctx {
   float l2min = 0.f, inv_bw = 0.f;
   DevBuf xsE, xsInvdE, xsS, xsHash;
   DevBuf stage;    // device copy of host rays
+  // pipelined upload of large host batches: a copy stream, two staging slots
+  // of one chunk each, and per slot an event after its upload and one after
+  // the cast that reads it
+  cudaStream_t up_stream = nullptr;
+  DevBuf up_slot[2];
+  cudaEvent_t up_copied[2] = {nullptr, nullptr}, up_freed[2] = {nullptr, nullptr};
   DevBuf scratch;  // finalize staging
   DevBuf sortKeys, sortTable, sortOffsets, sortTiles, sortRays;  // ray-sort scratch
   int xs_mode = VRC_XS_TABLE;
@@ -160,6 +166,13 @@ struct vrc_ctx {
   ~vrc_ctx() {
     DeviceGuard g(device);
     if (stream) cudaStreamSynchronize(stream);
+    if (up_stream) cudaStreamSynchronize(up_stream);
+    for (int i = 0; i < 2; ++i) {
+      if (up_copied[i]) cudaEventDestroy(up_copied[i]);
+      if (up_freed[i]) cudaEventDestroy(up_freed[i]);
+      up_slot[i].release();
+    }
+    if (up_stream) cudaStreamDestroy(up_stream);
     for (auto &t : pending) {
       cudaEventSynchronize(t.stop);
       cudaEventDestroy(t.start);
@@ -464,6 +477,54 @@ int ray_ptrs(vrc_ctx *c, const vrc_rays *r, cudaStream_t s, RayPtrs *out) {
 
 }  // namespace
 
+// Host batches above this many rays are uploaded and cast chunk by chunk.
+constexpr int64_t kUploadChunk = (int64_t)1 << 22;
+
+// Cast of a large host batch with the upload overlapped: chunk i+1 is copied
+// on the context's copy stream while chunk i is sorted and cast on stream s.
+// Each chunk's cast waits for its upload (event), and an upload into a slot
+// waits for the cast that last read that slot (event; this also orders a
+// call after the previous call's casts).  Returns once every upload has
+// completed, so the caller may reuse its host arrays.
+int cast_host_pipelined(vrc_ctx *c, const vrc_rays *r, cudaStream_t s) {
+  if (!c->up_stream) {
+    VRC_CUDA(cudaStreamCreateWithFlags(&c->up_stream, cudaStreamNonBlocking), "creating the upload stream");
+    for (int i = 0; i < 2; ++i) {
+      VRC_CUDA(cudaEventCreateWithFlags(&c->up_copied[i], cudaEventDisableTiming), "creating an upload event");
+      VRC_CUDA(cudaEventCreateWithFlags(&c->up_freed[i], cudaEventDisableTiming), "creating an upload event");
+    }
+  }
+  const size_t slot_bytes = 8 * sizeof(float) * (size_t)kUploadChunk;
+  for (int i = 0; i < 2; ++i) VRC_CUDA(c->up_slot[i].ensure(slot_bytes), "allocating upload slots");
+  const float *src[8] = {r->x, r->y, r->z, r->u, r->v, r->w, r->E, r->wt};
+  int last = 0;
+  for (int64_t off = 0, i = 0; off < r->n; off += kUploadChunk, ++i) {
+    const int slot = (int)(i & 1);
+    const int64_t m = std::min(kUploadChunk, r->n - off);
+    float *base = static_cast<float *>(c->up_slot[slot].p);
+    VRC_CUDA(cudaStreamWaitEvent(c->up_stream, c->up_freed[slot], 0), "ordering an upload");
+    RayPtrs rp;
+    rp.aos = nullptr;
+    rp.n = m;
+    const float **dst[8] = {&rp.x, &rp.y, &rp.z, &rp.u, &rp.v, &rp.w, &rp.E, &rp.wt};
+    for (int k = 0; k < 8; ++k) {
+      float *dk = base + (size_t)k * m;
+      VRC_CUDA(cudaMemcpyAsync(dk, src[k] + off, sizeof(float) * (size_t)m, cudaMemcpyHostToDevice, c->up_stream),
+               "copying rays to the device");
+      *dst[k] = dk;
+    }
+    VRC_CUDA(cudaEventRecord(c->up_copied[slot], c->up_stream), "recording an upload");
+    VRC_CUDA(cudaStreamWaitEvent(s, c->up_copied[slot], 0), "ordering a cast after its upload");
+    int rc = cast_device(c, rp, s);
+    if (rc) return rc;
+    VRC_CUDA(cudaEventRecord(c->up_freed[slot], s), "recording a cast");
+    last = slot;
+  }
+  // uploads run in order on one stream: the last one done means all are
+  VRC_CUDA(cudaEventSynchronize(c->up_copied[last]), "waiting for the ray upload");
+  return VRC_OK;
+}
+
 extern "C" {
 
 void vrc_default_options(vrc_options *opt) {
@@ -664,6 +725,7 @@ int vrc_cast_rays(vrc_ctx *c, const vrc_rays *r, void *cuda_stream) {
     }
   }
   cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+  if (!r->on_device && r->n > kUploadChunk) return cast_host_pipelined(c, r, s);
   RayPtrs rp;
   {
     int rc = ray_ptrs(c, r, s, &rp);
