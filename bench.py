@@ -401,9 +401,10 @@ def run_stream(args, rank, world, local):
 
 def run_history(args, rank, world, local):
     """Per-history moments: every step casts the slab256 rays in 16 calls of
-    2^20 rays through vrc_cast_histories (segment bound, cast into the
-    history table, fold into S1/S2), FP32 form, timed with CUDA events on the
-    calling stream; the plain tally cast of the same rays is timed beside it."""
+    2^20 rays through vrc_cast_histories (segment bound, sort of the rays
+    with their history ids, cast into the history table, fold into S1/S2),
+    FP32 form, timed with CUDA events on the calling stream; the plain tally
+    cast of the same calls (sorted too) is timed beside it."""
     import torch
     from paper_1706_07476_gb300 import vrc
     torch.cuda.set_device(local)
@@ -425,7 +426,7 @@ def run_history(args, rank, world, local):
     hdev = torch.from_numpy(hist.view(np.int32)).cuda()
     parts = [({k: v[a:b] for k, v in dev.items()}, hdev[a:b], int(hist[b - 1]) - int(hist[a]) + 1)
              for a, b in zip(cuts[:-1], cuts[1:])]
-    ctx = vrc.context_for(prob, vrc.vrc_default_options(form=vrc.VRC_FORM_FP32, sort=0, device=local))
+    ctx = vrc.context_for(prob, vrc.vrc_default_options(form=vrc.VRC_FORM_FP32, device=local))
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
 
@@ -470,7 +471,7 @@ def run_history(args, rank, world, local):
         "ms_per_step": H["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": HISTORY, "rays_per_step": prob.n_rays, "calls_per_step": len(parts),
-                   "histories_per_step": int(hist[-1]) + 1, "form": "fp32", "sort": 0},
+                   "histories_per_step": int(hist[-1]) + 1, "form": "fp32", "sort": "auto (each call)"},
         "history_over_tally_time": H["ms_per_step"] / out["tally"]["ms_per_step"],
         "modes": out, "histories_folded": samples, "gpu_launches": H["launches"],
     }

@@ -290,10 +290,12 @@ int vrc_moments_fold(vrc_ctx *c, void *cuda_stream);
  * n_histories is the number of histories the call completes, counting those
  * without rays (their score is zero); it is added to the sample count.
  * Scores go to S1/S2 only: the tally is untouched.  The tabulated cross
- * sections are used (not the surrogate) and the rays are not sorted.
+ * sections are used (not the surrogate); the rays are sorted as in
+ * vrc_cast_rays (options.sort), their history ids with them.
  * Needs (group count x cells) < 2^32 - 1.  Device scratch: a table of
- * 16-byte slots sized to twice an upper bound of the call's segments, kept
- * for later calls; VRC_ERR_OOM when it does not fit (split the call).  The
+ * 16-byte slots sized to twice an upper bound of the call's segments, with a
+ * bitmap of one bit per slot, kept for later calls; the sorted copy of the
+ * rays and of their ids (36 B per ray); VRC_ERR_OOM when it does not fit (split the call).  The
  * call waits for that bound (one small device-to-host read); the cast and
  * the fold into S1/S2 are then queued on cuda_stream (NULL = the context's
  * stream).  Host arrays may be reused on return; device arrays must stay

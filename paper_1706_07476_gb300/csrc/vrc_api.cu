@@ -146,6 +146,8 @@ struct vrc_ctx {
   DevBuf histTab;         // per-history table, histCap slots of 16 bytes, all zero between calls
   unsigned long long histCap = 0;
   DevBuf histIds;         // device copy of host history ids
+  DevBuf histSorted;      // history ids in sorted ray order
+  DevBuf histBits;        // claim bitmap of the table, histCap bits, all zero between calls
   DevBuf histBound;       // segment bound of the current call
 
   bool timing = false;
@@ -202,6 +204,8 @@ struct vrc_ctx {
     momS2.release();
     histTab.release();
     histIds.release();
+    histSorted.release();
+    histBits.release();
     histBound.release();
     rectDf.release();
     rectD.release();
@@ -350,7 +354,10 @@ int sync_streams(vrc_ctx *c, void *stream) {
 constexpr int64_t kAutoSortMin = 65536;
 
 // Sorts the batch into context scratch and points rp at the sorted copy.
-int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s) {
+// When carry_out is set, carry_in[i] (one uint32 per ray) goes to the sorted
+// position of ray i.
+int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in = nullptr,
+              uint32_t *carry_out = nullptr) {
   SortKeyArgs P;
   std::memset(&P, 0, sizeof P);
   for (int k = 0; k < 3; ++k) {
@@ -375,6 +382,8 @@ int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s) {
   RayOut out;
   std::memset(&out, 0, sizeof out);
   out.aos = static_cast<float4 *>(c->sortRays.p);  // sorted copy as 32-byte records
+  out.carry_in = carry_in;
+  out.carry_out = carry_out;
   TimedSpan span{nullptr, nullptr, 1};
   if (c->timing) {
     VRC_CUDA(c->get_event(&span.start), "creating a timing event");
@@ -1636,6 +1645,7 @@ int vrc_moments_enable(vrc_ctx *c, int32_t mode) {
     c->momS1.release();
     c->momS2.release();
     c->histTab.release();
+    c->histBits.release();
     c->histCap = 0;
     c->moments = false;
     return VRC_OK;
@@ -1718,21 +1728,33 @@ int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, i
   while (cap < 2 * bound) cap <<= 1;
   if (cap > c->histCap) {
     c->histTab.release();
+    c->histBits.release();
     c->histCap = 0;
     size_t free_b = 0, total_b = 0;
     VRC_CUDA(cudaMemGetInfo(&free_b, &total_b), "querying device memory");
-    const unsigned long long bytes = 16ull * cap;
+    const unsigned long long bytes = 16ull * cap + cap / 8ull;
     if (bytes > free_b / 10 * 9)
       return fail(VRC_ERR_OOM, "this call's histories need a %.1f GB table (%.1f GB free); split the call",
                   bytes / 1e9, free_b / 1e9);
-    VRC_CUDA(c->histTab.ensure(bytes), "allocating the per-history table");
-    VRC_CUDA(cudaMemsetAsync(c->histTab.p, 0, bytes, s), "clearing the per-history table");
+    VRC_CUDA(c->histTab.ensure(16ull * cap), "allocating the per-history table");
+    VRC_CUDA(c->histBits.ensure(cap / 8ull), "allocating the per-history table");
+    VRC_CUDA(cudaMemsetAsync(c->histTab.p, 0, 16ull * cap, s), "clearing the per-history table");
+    VRC_CUDA(cudaMemsetAsync(c->histBits.p, 0, cap / 8ull, s), "clearing the per-history table");
     c->histCap = cap;
+  }
+  // sort the rays as vrc_cast_rays does, the history ids with them
+  if (c->opt.sort == 1 || (c->opt.sort == -1 && rp.n >= kAutoSortMin)) {
+    VRC_CUDA(c->histSorted.ensure(sizeof(uint32_t) * (size_t)rp.n), "allocating the sorted history ids");
+    uint32_t *sorted = static_cast<uint32_t *>(c->histSorted.p);
+    int rc = sort_rays(c, rp, s, hist, sorted);
+    if (rc) return rc;
+    hist = sorted;
   }
   CastArgs a = make_args(c, rp);
   a.hist = hist;
   a.htab.e = static_cast<unsigned long long *>(c->histTab.p);
   a.htab.mask = cap - 1;
+  a.htab.bits = static_cast<unsigned int *>(c->histBits.p);
   const int form = c->opt.form;
   const int block = c->opt.block > 0 ? c->opt.block : 256;
   int bps = c->opt.blocks_per_sm;

@@ -281,7 +281,8 @@ __device__ __forceinline__ void cas128(unsigned long long *slot, unsigned long l
 // mix64(key).  Every access is a 128-bit compare-and-swap on the whole slot:
 // the first, expecting an empty slot, claims it with the score in one step;
 // a slot that already holds the key is updated by compare-and-swap from the
-// contents that the failed claim returned.  Each failed update means another
+// contents that the failed claim returned.  A claim also sets the slot's bit
+// in the table's bitmap, so the fold visits only claimed slots.  Each failed update means another
 // thread's update went in; after kMaxCasRetries of them, or after probing the
 // whole table, kStatusTableFull is set and the score dropped (the host sizes
 // the table at twice an upper bound of the segments, so a full table does not
@@ -300,7 +301,10 @@ struct HistSink {
       unsigned long long *slot = t.e + 2 * i;
       unsigned long long ok, ov;
       cas128(slot, 0ull, 0ull, key, vb, ok, ov);
-      if (ok == 0ull && ov == 0ull) return;  // claimed with the score
+      if (ok == 0ull && ov == 0ull) {  // claimed with the score
+        atomicOr(t.bits + (i >> 5), 1u << (unsigned)(i & 31ull));
+        return;
+      }
       if (ok == key) {
         for (int it = 0; it < kMaxCasRetries; ++it) {
           const unsigned long long nv =

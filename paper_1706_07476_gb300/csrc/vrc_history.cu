@@ -83,18 +83,26 @@ __global__ void k_segment_bound(BoundGeom G, RayPtrs R, unsigned long long *boun
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(bound, acc);
 }
 
-// Every occupied slot (key + 1, x): S1[bin] += x, S2[bin] += x^2, slot = 0.
-__global__ void k_hist_drain(ulonglong2 *e, unsigned long long cap, double *__restrict__ s1,
-                             double *__restrict__ s2) {
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
-    const ulonglong2 v = e[i];
-    if (v.x == 0ull) continue;
-    const unsigned bin = (unsigned)((v.x - 1ull) & 0xffffffffull);
-    const double x = __longlong_as_double((long long)v.y);
-    atomicAdd(s1 + bin, x);
-    atomicAdd(s2 + bin, x * x);
-    e[i] = make_ulonglong2(0ull, 0ull);
+// Every claimed slot (key + 1, x), found from the bitmap: S1[bin] += x,
+// S2[bin] += x^2, slot = 0, bitmap word = 0.
+__global__ void k_hist_drain(ulonglong2 *e, unsigned int *bits, unsigned long long words,
+                             double *__restrict__ s1, double *__restrict__ s2) {
+  for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < words;
+       j += (unsigned long long)gridDim.x * blockDim.x) {
+    unsigned w = bits[j];
+    if (w == 0u) continue;
+    bits[j] = 0u;
+    while (w) {
+      const int b = __ffs(w) - 1;
+      w &= w - 1u;
+      ulonglong2 *slot = e + 32ull * j + (unsigned)b;
+      const ulonglong2 v = *slot;
+      const unsigned bin = (unsigned)((v.x - 1ull) & 0xffffffffull);
+      const double x = __longlong_as_double((long long)v.y);
+      atomicAdd(s1 + bin, x);
+      atomicAdd(s2 + bin, x * x);
+      *slot = make_ulonglong2(0ull, 0ull);
+    }
   }
 }
 
@@ -111,10 +119,10 @@ cudaError_t launch_segment_bound(const BoundGeom &g, const RayPtrs &rays, unsign
 }
 
 cudaError_t launch_hist_drain(const HistTable &t, double *s1, double *s2, int num_sms, cudaStream_t s) {
-  const unsigned long long cap = t.mask + 1ull;
+  const unsigned long long words = (t.mask + 1ull) / 32ull;
   const int block = 256;
-  const int grid = (int)std::min<unsigned long long>((cap + block - 1) / block, (unsigned long long)num_sms * 8);
-  k_hist_drain<<<grid, block, 0, s>>>(reinterpret_cast<ulonglong2 *>(t.e), cap, s1, s2);
+  const int grid = (int)std::min<unsigned long long>((words + block - 1) / block, (unsigned long long)num_sms * 8);
+  k_hist_drain<<<grid, block, 0, s>>>(reinterpret_cast<ulonglong2 *>(t.e), t.bits, words, s1, s2);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -66,6 +66,7 @@ struct RayPtrs {
 struct HistTable {
   unsigned long long *e;       // [cap][2]
   unsigned long long mask;     // cap - 1
+  unsigned int *bits;          // [cap / 32] one bit per slot, set when the slot is claimed
 };
 
 struct CastArgs {

@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(kSortBlock) k_sort_scatter(RayPtrs R, SortKeyA
       O.x[pos] = f[0]; O.y[pos] = f[1]; O.z[pos] = f[2]; O.u[pos] = f[3];
       O.v[pos] = f[4]; O.w[pos] = f[5]; O.E[pos] = f[6]; O.wt[pos] = f[7];
     }
+    if (O.carry_out) O.carry_out[pos] = O.carry_in[r];
   }
 }
 

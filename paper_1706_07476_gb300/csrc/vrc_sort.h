@@ -25,6 +25,10 @@ struct SortKeyArgs {
 struct RayOut {
   float *x, *y, *z, *u, *v, *w, *E, *wt;
   float4 *aos;  // when set, the sorted rays are written as 32-byte records here
+  // optional 32-bit value per ray (input order) carried to the ray's sorted
+  // position (single-problem sort only)
+  const uint32_t *carry_in;
+  uint32_t *carry_out;
 };
 
 struct SortPlan {

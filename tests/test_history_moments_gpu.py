@@ -39,8 +39,9 @@ def _sigma_bound(s1, s2, want_sigma, n_with_rays, N):
     return np.minimum(dv / np.maximum(want_sigma, 1e-300), np.sqrt(dv))
 
 
+@pytest.mark.parametrize("sort", [0, 1], ids=["unsorted", "sorted"])
 @pytest.mark.parametrize("form", [0, 1], ids=["plain", "fp32"])
-def test_history_moments_match_oracle(vrc, form):
+def test_history_moments_match_oracle(vrc, form, sort):
     import torch
     prob = W.slab_room(seed=9, n=16, n_rays=12000, n_points=400, n_resonances=6, n_groups=3)
     hist, n_hist = _histories(prob.n_rays, seed=10)
@@ -51,7 +52,7 @@ def test_history_moments_match_oracle(vrc, form):
     first = np.flatnonzero(hist % 2 == 0)
     second = np.flatnonzero(hist % 2 == 1)
     n_first = len(np.unique(hist[first]))
-    ctx = vrc.context_for(prob, vrc.vrc_default_options(form=form))
+    ctx = vrc.context_for(prob, vrc.vrc_default_options(form=form, sort=sort))
     try:
         with pytest.raises(vrc.VrcError) as ei:
             vrc.vrc_cast_histories(ctx, prob.rays, hist, N)
@@ -80,7 +81,7 @@ def test_history_moments_match_oracle(vrc, form):
         big = (want_sigma > 1e-2 * want_total) & (want_total >= 1e-30)
         assert big.sum() > 1000
         rel = err[big] / want_sigma[big]
-        print(f"history sigma form={form}: max rel {rel.max():.2e} over {int(big.sum())} cells")
+        print(f"history sigma form={form} sort={sort}: max rel {rel.max():.2e} over {int(big.sum())} cells")
         assert rel.max() <= 1e-3
     finally:
         ctx.close()
