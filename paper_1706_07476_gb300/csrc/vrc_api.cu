@@ -334,6 +334,8 @@ CastArgs make_args(const vrc_ctx *c, const RayPtrs &rays) {
 }
 
 int status_code(unsigned st) {
+  if (st & kStatusTimeout)
+    return fail(VRC_ERR_CUDA, "a bounded wait on the tensor cores gave up; results are incomplete");
   if (st & kStatusTableFull)
     return fail(VRC_ERR_OOM, "the per-history table overflowed; its scores are incomplete");
   if (st & kStatusTraversal)
@@ -430,6 +432,7 @@ int cast_device(vrc_ctx *c, RayPtrs rp, cudaStream_t s) {
     aa.e_first = c->mlp_lo;
     aa.e_last = c->mlp_hi;
     aa.emb = mlp::make_embed(c->mlp_lo, c->mlp_hi);
+    aa.status = c->d_status;
     VRC_CUDA(mlp::launch_apply(aa, c->num_sms, s), "launching the surrogate");
     sig_ray = aa.out;
   }
@@ -1438,6 +1441,7 @@ int vrc_train_surrogate(vrc_ctx *c, const vrc_surrogate_options *opt, vrc_surrog
   aa.mode = 0;
   aa.mat_mask = mask;
   aa.emb = ta.emb;
+  aa.status = c->d_status;
   VRC_CUDA(mlp::launch_apply(aa, c->num_sms, s), "launching the validation pass");
   std::vector<float> Y((size_t)n_va * mlp::kOut), L((size_t)o.steps + 1, 0.f);
   VRC_CUDA(cudaStreamSynchronize(s), "training the surrogate");

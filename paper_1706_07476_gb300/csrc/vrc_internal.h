@@ -14,6 +14,7 @@ constexpr int kMaxGroups = 1024;
 constexpr unsigned kStatusNonfinite = 1u;
 constexpr unsigned kStatusTraversal = 2u;
 constexpr unsigned kStatusTableFull = 4u;  // a per-history table insert found no free slot
+constexpr unsigned kStatusTimeout = 8u;    // a bounded wait on the tensor cores gave up
 
 // Device counters (unsigned long long each).
 enum Counter { kCntSegments = 0, kCntRays = 1, kCntRejected = 2, kCntOverflow = 3, kNumCounters = 4 };

@@ -1,14 +1,15 @@
-// Learned cross-section surrogate on the tensor cores: training step
-// (forward, loss, backward in one kernel), Adam, and the per-ray forward
-// pass used by the cast.  All matrix products are warp-level
-// mma.sync.m16n8k16 with bfloat16 operands and float32 accumulation;
-// operand tiles come from shared memory through ldmatrix (.trans where the
-// stored layout is the transpose of the operand).
+// Learned cross-section surrogate: training step (forward, loss, backward in
+// one kernel) and Adam.  The training step's matrix products are warp-level
+// mma.sync.m16n8k16 with bfloat16 operands and float32 accumulation; operand
+// tiles come from shared memory through ldmatrix (.trans where the stored
+// layout is the transpose of the operand).  The per-ray forward pass used by
+// the cast runs on tcgen05 (vrc_mlp_tc.cu).
 #include <cuda_bf16.h>
 #include <math.h>
 
 #include "vrc_internal.h"
 #include "vrc_mlp.h"
+#include "vrc_mlp_dev.cuh"
 
 namespace vrc {
 namespace mlp {
@@ -55,12 +56,6 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t *>(&v);
-}
-
-__device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
 __device__ __forceinline__ float silu_grad(float z) {
   const float s = 1.f / (1.f + expf(-z));
   return s * (1.f + z * (1.f - s));
@@ -93,11 +88,6 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
   x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
   return x ^ (x >> 31);
-}
-
-__device__ __forceinline__ void embed_pair(const Embed &em, float E, int f, float *s, float *c) {
-  const float x = (log10f(E) - em.l0) * em.inv_range;
-  sincospif(em.freq[f] * x, s, c);
 }
 
 // Column sums over a warp's 16 rows of an accumulator tile, added to dst[col].
@@ -392,143 +382,6 @@ __global__ void k_adam(float *p, const float *g, float *m1, float *m2, int n, fl
 // pair of one layer is the m16k16 A operand of the next).  Block = 4 warps,
 // each warp 16 rays per pass; weights staged once per block.
 // ---------------------------------------------------------------------------
-constexpr int kApplyThreads = 128;
-constexpr size_t kApplySmem =
-    sizeof(bf16) * (size_t)(kHid * LD64 + kHid * LD128) + sizeof(float) * (kOut * kHid + 2 * kHid + kOut);
-
-__global__ void __launch_bounds__(kApplyThreads) k_mlp_apply(ApplyArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  bf16 *W1s = reinterpret_cast<bf16 *>(smem);
-  bf16 *W2s = W1s + kHid * LD64;
-  float *W3f = reinterpret_cast<float *>(W2s + kHid * LD128);  // [16][128] bf16-valued, float32
-  float *bs = W3f + kOut * kHid;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const float *P = a.params;
-  for (int i = tid; i < kHid * kEmb; i += kApplyThreads) W1s[(i / kEmb) * LD64 + i % kEmb] = __float2bfloat16_rn(P[kOffW1 + i]);
-  for (int i = tid; i < kHid * kHid; i += kApplyThreads) W2s[(i / kHid) * LD128 + i % kHid] = __float2bfloat16_rn(P[kOffW2 + i]);
-  for (int i = tid; i < kOut * kHid; i += kApplyThreads) W3f[i] = __bfloat162float(__float2bfloat16_rn(P[kOffW3 + i]));
-  for (int i = tid; i < kHid; i += kApplyThreads) { bs[i] = P[kOffB1 + i]; bs[kHid + i] = P[kOffB2 + i]; }
-  if (tid < kOut) bs[2 * kHid + tid] = P[kOffB3 + tid];
-  __syncthreads();
-
-  const int64_t tiles = (a.n + 15) / 16;
-  for (int64_t tile = (int64_t)blockIdx.x * 4 + warp; tile < tiles; tile += (int64_t)gridDim.x * 4) {
-    const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
-    const float E0 = r0 < a.n ? (a.aos ? __ldg(a.aos + 2 * r0 + 1).z : a.E[r0]) : 1.0f;
-    const float E1 = r1 < a.n ? (a.aos ? __ldg(a.aos + 2 * r1 + 1).z : a.E[r1]) : 1.0f;
-    // layer 1 A operand: features k = 16j + 2t (+1) and 16j + 8 + 2t (+1),
-    // i.e. frequencies 8j + t and 8j + 4 + t, for rows g and g + 8
-    uint32_t x[4][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      float s, c;
-      embed_pair(a.emb, E0, 8 * j + t, &s, &c);
-      x[j][0] = pack2(s, c);
-      embed_pair(a.emb, E1, 8 * j + t, &s, &c);
-      x[j][1] = pack2(s, c);
-      embed_pair(a.emb, E0, 8 * j + 4 + t, &s, &c);
-      x[j][2] = pack2(s, c);
-      embed_pair(a.emb, E1, 8 * j + 4 + t, &s, &c);
-      x[j][3] = pack2(s, c);
-    }
-    uint32_t h[8][4];  // next layer's A operand, 8 k-tiles of 16
-    {
-      float acc[16][4] = {};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-#pragma unroll
-        for (int np = 0; np < 8; ++np) {
-          uint32_t bf[4];
-          ldm_x4(bf, b_rows(W1s, LD64, np * 16, j * 16, lane));
-          mma_bf16(acc[2 * np], x[j], bf[0], bf[1]);
-          mma_bf16(acc[2 * np + 1], x[j], bf[2], bf[3]);
-        }
-      }
-#pragma unroll
-      for (int nt = 0; nt < 16; ++nt) {
-        const int c = nt * 8 + 2 * t;
-        const uint32_t lo = pack2(silu(acc[nt][0] + bs[c]), silu(acc[nt][1] + bs[c + 1]));
-        const uint32_t hi = pack2(silu(acc[nt][2] + bs[c]), silu(acc[nt][3] + bs[c + 1]));
-        // n-tile nt is the low (even nt) or high (odd nt) k half of k-tile nt/2
-        h[nt >> 1][(nt & 1) * 2 + 0] = lo;
-        h[nt >> 1][(nt & 1) * 2 + 1] = hi;
-      }
-    }
-    // layer 2 on the tensor cores; h2 stays float32 for the output layer
-    float p[2][kOut];  // output partial sums over this thread's 32 hidden units, rows g and g + 8
-    {
-      float acc[16][4] = {};
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-#pragma unroll
-        for (int np = 0; np < 8; ++np) {
-          uint32_t bf[4];
-          ldm_x4(bf, b_rows(W2s, LD128, np * 16, j * 16, lane));
-          mma_bf16(acc[2 * np], h[j], bf[0], bf[1]);
-          mma_bf16(acc[2 * np + 1], h[j], bf[2], bf[3]);
-        }
-      }
-      // layer 3 in float32 (CUDA cores): y = W3 h2 + b3
-#pragma unroll
-      for (int m = 0; m < kOut; ++m) p[0][m] = p[1][m] = 0.f;
-#pragma unroll
-      for (int nt = 0; nt < 16; ++nt) {
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int k = nt * 8 + 2 * t + e;
-          const float h0 = silu(acc[nt][e] + bs[kHid + k]);
-          const float h1 = silu(acc[nt][2 + e] + bs[kHid + k]);
-#pragma unroll
-          for (int m = 0; m < kOut; ++m) {
-            const float w = W3f[m * kHid + k];
-            p[0][m] = fmaf(w, h0, p[0][m]);
-            p[1][m] = fmaf(w, h1, p[1][m]);
-          }
-        }
-      }
-#pragma unroll
-      for (int m = 0; m < kOut; ++m) {
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          p[hh][m] += __shfl_xor_sync(0xffffffffu, p[hh][m], 1);
-          p[hh][m] += __shfl_xor_sync(0xffffffffu, p[hh][m], 2);
-        }
-      }
-    }
-    // epilogue: rows r0 (g) and r1 (g + 8); lane t writes outputs 4t .. 4t+3
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      const int64_t row = hh ? r1 : r0;
-      if (row >= a.n) continue;
-      const float E = hh ? E1 : E0;
-      bool flagged = false;
-      if (a.mode == 1) {
-        const double e = (double)E;
-        if (!(e >= a.e_first && e <= a.e_last)) {
-          flagged = true;
-        } else if (a.flags) {
-          int b = (int)((__log2f(E) - a.l2min) * a.inv_bw);
-          b = min(max(b, 0), a.n_hash - 1);
-          flagged = a.flags[b] != 0;
-        }
-      }
-      float v4[4];
-#pragma unroll
-      for (int m = 0; m < kOut; ++m) {
-        if ((m >> 2) != t) continue;
-        float v = p[hh][m] + bs[2 * kHid + m];
-        if (a.mode == 1) {
-          v = ((a.mat_mask >> m) & 1u) ? expf(v) : 0.f;
-          if (m == 0 && flagged) v = __int_as_float(0x7fc00000);
-        }
-        v4[m & 3] = v;
-      }
-      *reinterpret_cast<float4 *>(a.out + row * kOut + 4 * t) = make_float4(v4[0], v4[1], v4[2], v4[3]);
-    }
-  }
-}
-
 }  // namespace
 
 cudaError_t launch_train(const TrainArgs &a, cudaStream_t s) {
@@ -546,21 +399,6 @@ cudaError_t launch_adam(float *params, const float *grad, float *m1, float *m2, 
   const float c1 = 1.f / (1.f - powf(beta1, (float)step));
   const float c2 = 1.f / (1.f - powf(beta2, (float)step));
   k_adam<<<(n + 255) / 256, 256, 0, s>>>(params, grad, m1, m2, n, lr, beta1, beta2, eps, c1, c2);
-  note_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_apply(const ApplyArgs &a, int num_sms, cudaStream_t s) {
-  if (a.n <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplySmem);
-  if (e != cudaSuccess) return e;
-  int bps = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_mlp_apply, kApplyThreads, kApplySmem);
-  if (e != cudaSuccess) return e;
-  const int64_t tiles = (a.n + 15) / 16;
-  const int64_t want = (tiles + 3) / 4;
-  const int grid = (int)(want < (int64_t)num_sms * (bps > 0 ? bps : 1) ? want : (int64_t)num_sms * (bps > 0 ? bps : 1));
-  k_mlp_apply<<<grid, kApplyThreads, kApplySmem, s>>>(a);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -9,10 +9,10 @@
 // Parameters are float32 masters in one array: W1 [128][64], b1, W2
 // [128][128], b2, W3 [16][128], b3.  Kernels round every weight to bfloat16.
 // The two 128-wide layers run on the tensor cores (bfloat16 operands,
-// float32 accumulation); the 128 -> 16 output layer runs in float32 on the
-// CUDA cores from float32 h2 (2,048 FMAs per ray), because rounding h2 to
-// bfloat16 would put about 1e-2 of noise on log sigma, ten times the
-// accepted error of the surrogate.
+// float32 accumulation: tcgen05 in the forward pass, mma.sync in training);
+// the 128 -> 16 output layer runs in float32 on the CUDA cores from float32
+// h2 (2,048 FMAs per ray), because rounding h2 to bfloat16 would put about
+// 1e-2 of noise on log sigma, ten times the accepted error of the surrogate.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -84,8 +84,12 @@ struct ApplyArgs {
   float l2min, inv_bw;
   double e_first, e_last;
   Embed emb;
+  unsigned int *status;    // kStatusTimeout is set here if a tensor-core wait gives up (may be nullptr)
 };
 
+// The two 128-wide layers run on tcgen05 (vrc_mlp_tc.cu).  A bounded wait
+// on the tensor cores that gives up sets kStatusTimeout in *status and leaves
+// the rest of the outputs unwritten.
 cudaError_t launch_apply(const ApplyArgs &a, int num_sms, cudaStream_t s);
 
 }  // namespace mlp

@@ -1,0 +1,40 @@
+// Device helpers shared by the surrogate kernels (vrc_mlp.cu, vrc_mlp_tc.cu):
+// the sinusoidal embedding of log10 E, bfloat16 packing and SiLU.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "vrc_mlp.h"
+
+namespace vrc {
+namespace mlp {
+
+// x = (log10 E - l0) * inv_range and the pair sin(pi f x), cos(pi f x) for
+// frequency index f (features 2f and 2f + 1 of the embedding).
+__device__ __forceinline__ float embed_x(const Embed &em, float E) {
+  return (log10f(E) - em.l0) * em.inv_range;
+}
+
+__device__ __forceinline__ void embed_pair_x(const Embed &em, float x, int f, float *s, float *c) {
+  sincospif(em.freq[f] * x, s, c);
+}
+
+__device__ __forceinline__ void embed_pair(const Embed &em, float E, int f, float *s, float *c) {
+  embed_pair_x(em, embed_x(em, E), f, s, c);
+}
+
+// Two floats rounded to bfloat16, lo in the low half.
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// SiLU z / (1 + e^-z) from the hardware exponential and division
+// approximations (a few ulp, about 1e-6 relative), far below the bfloat16
+// rounding of the activations it feeds; for z below about -88, e^-z is +inf
+// and the quotient the correct limit 0.
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.f + __expf(-z)); }
+
+}  // namespace mlp
+}  // namespace vrc

@@ -1,0 +1,319 @@
+// Per-ray forward pass of the learned cross-section surrogate on the
+// fifth-generation tensor cores (tcgen05, accumulators in tensor memory).
+//
+// One persistent block per SM holds the bfloat16 weights once and runs three
+// independent groups of 128 threads (four warps each), each on its own tiles
+// of 128 rays with its own operand buffers, mbarrier, named barrier and 128
+// tensor-memory columns.  Thread t of a group owns ray t of the tile, which
+// is row t of every matrix and lane t of the tensor memory (warp j of the
+// group reads lane quarter j).  Per tile:
+//   1. each thread writes its ray's 64 embedding features (bfloat16) to A0;
+//   2. one thread issues D = A0 W1^T (M = N = 128, K = 64, four K = 16
+//      steps) into the group's columns and commits to the group's mbarrier;
+//   3. each thread loads its row of D, adds b1, applies SiLU, rounds to
+//      bfloat16 and writes the row to A1;
+//   4. D = A1 W2^T (K = 128, eight steps) into the same columns;
+//   5. each thread loads its row, h2 = SiLU(D + b2) in float32, and forms the
+//      128 -> 16 output layer on the CUDA cores (2,048 FMAs), then writes
+//      log sigma or sigma.
+// Operands live in shared memory in the canonical K-major layout without
+// swizzle: 8-row x 16-byte core matrices, consecutive along K 128 bytes
+// apart (leading byte offset) and along rows K*16 bytes apart (stride byte
+// offset).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "vrc_internal.h"
+#include "vrc_mlp.h"
+#include "vrc_mlp_dev.cuh"
+
+namespace vrc {
+namespace mlp {
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kTile = 128;            // rays per tile: the MMA's M and the tensor-memory lanes
+constexpr int kGroups = 3;            // independent groups of 128 threads per block
+constexpr int kTcThreads = 128 * kGroups;
+constexpr uint32_t kTmemCols = 512;   // allocated once per block; group g uses columns 128 g ..
+constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before a wait gives up
+
+// shared memory (bytes from the block's base)
+constexpr uint32_t kSW1 = 0;          // W1 [128][64] bfloat16, 16 KiB
+constexpr uint32_t kSW2 = 16384;      // W2 [128][128], 32 KiB
+constexpr uint32_t kSW3 = 49152;      // W3 [16][128] float32 (bfloat16 values), 8 KiB
+constexpr uint32_t kSB = 57344;       // b1, b2, b3 float32 (272 values)
+constexpr uint32_t kSBar = 58432;     // per group an mbarrier (8 B); then the tensor-memory address
+constexpr uint32_t kSGroup = 59392;   // per group: A0 [128][64] (16 KiB), A1 [128][128] (32 KiB)
+constexpr uint32_t kGroupBytes = 49152;
+constexpr uint32_t kSmemTc = kSGroup + kGroups * kGroupBytes;  // 206,848
+
+// Byte offset of element (r, k) of a K-column matrix in the core-matrix layout.
+__device__ __forceinline__ uint32_t cm_off(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (all in 16-byte units), the fixed version bits 46-48 = 0b001, base
+// offset 0, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: float32 D (bits 4-5 = 1), bfloat16 A
+// and B (bits 7-9 and 10-12 = 1), both K-major, N / 8 at bits 17-22, M / 16
+// at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16_tc(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      :: "r"(tmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Polls the mbarrier for completion of the phase with the given parity, at
+// most kWaitLimit times.  Returns false if it gave up.
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < kWaitLimit && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  }
+  return done != 0;
+}
+
+// 32 consecutive float32 columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t (&r)[32], uint32_t taddr) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Stages a [128][K] float32 weight block as bfloat16 core matrices.
+__device__ __forceinline__ void stage_weights(unsigned char *smem, uint32_t off, const float *W, int K) {
+  const int chunks = kTile * K / 8;
+  for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
+    const int r = i / (K / 8), k = (i % (K / 8)) * 8;
+    const float *w = W + r * K + k;
+    const uint4 v = make_uint4(pack2(w[0], w[1]), pack2(w[2], w[3]), pack2(w[4], w[5]), pack2(w[6], w[7]));
+    *reinterpret_cast<uint4 *>(smem + off + cm_off(r, k, K)) = v;
+  }
+}
+
+// Barrier of the 128 threads of one group (named barrier 1 + g); returns
+// nonzero in every thread of the group if any thread passed nonzero.
+__device__ __forceinline__ uint32_t group_sync_or(int g, uint32_t v) {
+  uint32_t any;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
+      "bar.red.popc.u32 %0, %1, 128, p;\n\t}"
+      : "=r"(any) : "r"(1 + g), "r"(v) : "memory");
+  return any;
+}
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, 128;" :: "r"(1 + g) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int g = tid >> 7, gt = tid & 127;  // group, thread (= row) within the group
+  float *W3f = reinterpret_cast<float *>(smem + kSW3);
+  float *bs = reinterpret_cast<float *>(smem + kSB);
+  const uint32_t bar = smem_u32(smem + kSBar + 8 * g);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + kSBar + 8 * kGroups);
+  unsigned char *A0 = smem + kSGroup + g * kGroupBytes;
+  unsigned char *A1 = A0 + 16384;
+  const float *P = a.params;
+
+  stage_weights(smem, kSW1, P + kOffW1, kEmb);
+  stage_weights(smem, kSW2, P + kOffW2, kHid);
+  for (int i = tid; i < kOut * kHid; i += kTcThreads) W3f[i] = __bfloat162float(__float2bfloat16_rn(P[kOffW3 + i]));
+  for (int i = tid; i < kHid; i += kTcThreads) { bs[i] = P[kOffB1 + i]; bs[kHid + i] = P[kOffB2 + i]; }
+  if (tid < kOut) bs[2 * kHid + tid] = P[kOffB3 + tid];
+  if (gt == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(tslot)), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot + 128u * (uint32_t)g;                     // the group's columns
+  const uint32_t tmem_row = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lane quarter
+  const uint32_t sA0 = smem_u32(A0), sA1 = smem_u32(A1);
+  const uint32_t sW1 = smem_u32(smem + kSW1), sW2 = smem_u32(smem + kSW2);
+
+  const int64_t tiles = (a.n + kTile - 1) / kTile;
+  for (int64_t tile = (int64_t)blockIdx.x * kGroups + g; tile < tiles; tile += (int64_t)gridDim.x * kGroups) {
+    const int64_t row = tile * kTile + gt;
+    const float E = row < a.n ? (a.aos ? __ldg(a.aos + 2 * row + 1).z : a.E[row]) : 1.0f;
+
+    // 1. embedding row: features 2f, 2f + 1 = sin, cos of pi f_f x
+    const float x = embed_x(a.emb, E);
+#pragma unroll
+    for (int kc = 0; kc < kEmb / 8; ++kc) {
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float sn, cs;
+        embed_pair_x(a.emb, x, kc * 4 + q, &sn, &cs);
+        w[q] = pack2(sn, cs);
+      }
+      *reinterpret_cast<uint4 *>(A0 + cm_off(gt, kc * 8, kEmb)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    fence_async_smem();
+    fence_before();
+    group_sync(g);
+
+    // 2. D = A0 W1^T
+    if (gt == 0) {
+      fence_after();
+#pragma unroll
+      for (int kk = 0; kk < kEmb / 16; ++kk)
+        mma_bf16_tc(tmem, smem_desc(sA0 + kk * 256, 128, kEmb * 16), smem_desc(sW1 + kk * 256, 128, kEmb * 16),
+                    kk > 0);
+      mma_commit(bar);
+    }
+    if (group_sync_or(g, !wait_phase(bar, 0))) {
+      if (gt == 0 && a.status) atomicOr(a.status, kStatusTimeout);
+      break;
+    }
+    fence_after();
+
+    // 3. h1 = SiLU(D + b1) as bfloat16 into A1
+#pragma unroll
+    for (int c = 0; c < kHid / 32; ++c) {
+      uint32_t r[32];
+      tmem_ld32(r, tmem_row + c * 32);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = q * 8 + 2 * e, k = c * 32 + j;
+          w[e] = pack2(silu(__uint_as_float(r[j]) + bs[k]), silu(__uint_as_float(r[j + 1]) + bs[k + 1]));
+        }
+        *reinterpret_cast<uint4 *>(A1 + cm_off(gt, c * 32 + q * 8, kHid)) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    fence_async_smem();
+    fence_before();
+    group_sync(g);
+
+    // 4. D = A1 W2^T
+    if (gt == 0) {
+      fence_after();
+#pragma unroll
+      for (int kk = 0; kk < kHid / 16; ++kk)
+        mma_bf16_tc(tmem, smem_desc(sA1 + kk * 256, 128, kHid * 16), smem_desc(sW2 + kk * 256, 128, kHid * 16),
+                    kk > 0);
+      mma_commit(bar);
+    }
+    if (group_sync_or(g, !wait_phase(bar, 1))) {
+      if (gt == 0 && a.status) atomicOr(a.status, kStatusTimeout);
+      break;
+    }
+    fence_after();
+
+    // 5. h2 = SiLU(D + b2) in float32, y = W3 h2 + b3 on the CUDA cores
+    float p[kOut];
+#pragma unroll
+    for (int m = 0; m < kOut; ++m) p[m] = bs[2 * kHid + m];
+#pragma unroll
+    for (int c = 0; c < kHid / 32; ++c) {
+      uint32_t r[32];
+      tmem_ld32(r, tmem_row + c * 32);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int k = c * 32 + j;
+        const float h = silu(__uint_as_float(r[j]) + bs[kHid + k]);
+#pragma unroll
+        for (int m = 0; m < kOut; ++m) p[m] = fmaf(W3f[m * kHid + k], h, p[m]);
+      }
+    }
+    fence_before();
+
+    if (row < a.n) {
+      if (a.mode == 1) {
+        bool flagged = false;
+        const double e = (double)E;
+        if (!(e >= a.e_first && e <= a.e_last)) {
+          flagged = true;
+        } else if (a.flags) {
+          int b = (int)((__log2f(E) - a.l2min) * a.inv_bw);
+          b = min(max(b, 0), a.n_hash - 1);
+          flagged = a.flags[b] != 0;
+        }
+#pragma unroll
+        for (int m = 0; m < kOut; ++m) p[m] = ((a.mat_mask >> m) & 1u) ? expf(p[m]) : 0.f;
+        if (flagged) p[0] = __int_as_float(0x7fc00000);
+      }
+      float4 *o = reinterpret_cast<float4 *>(a.out + row * kOut);
+#pragma unroll
+      for (int q = 0; q < kOut / 4; ++q) o[q] = make_float4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+    }
+  }
+  // every tensor-memory read has completed (tcgen05.wait::ld) before the barrier
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(*tslot), "r"(kTmemCols) : "memory");
+}
+
+}  // namespace
+
+cudaError_t launch_apply(const ApplyArgs &a, int num_sms, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTc);
+  if (e != cudaSuccess) return e;
+  // one resident block per SM (its shared memory allows no second one), so
+  // its 512 tensor-memory columns are free when it allocates them
+  int bps = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_mlp_apply_tc, kTcThreads, kSmemTc);
+  if (e != cudaSuccess) return e;
+  if (bps != 1) return cudaErrorInvalidConfiguration;
+  const int64_t tiles = (a.n + kTile - 1) / kTile;
+  const int64_t want = (tiles + kGroups - 1) / kGroups;
+  const int grid = (int)(want < (int64_t)num_sms ? want : (int64_t)num_sms);
+  k_mlp_apply_tc<<<grid, kTcThreads, kSmemTc, s>>>(a);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace mlp
+}  // namespace vrc
