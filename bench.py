@@ -45,6 +45,10 @@ HISTORY = ("history: the slab256 rays grouped into histories of 1..15 consecutiv
 DETECTORS = ("detectors: the slab256 rays as collision events, each scored at 8 detector "
              "points (a 2x2x2 lattice at 1/4 and 3/4 of the box) by the next-event estimator "
              "wt exp(-tau)/(4 pi R^2), tau by the grid walk from the event to the detector")
+SURROGATE = ("surrogate32: 32^3 mesh of 1 cm cells, 16 materials (layout uniform-random) with "
+             "20,000-point tables of 200 resonances, 2^24 rays, FP32 form; cross sections from the "
+             "learned 64 -> 128 -> 128 -> 16 network (sinusoidal embedding of log10 E, SiLU) or the "
+             "table, seed 4")
 METRIC = "ray-cell segments/s at <=1e-4 tally rel. err vs FP64 oracle; % HBM roofline"
 UNIT = "segments/s"
 # Algorithmic bytes: per segment 8 B tally read + 8 B tally write + 1 B material
@@ -64,7 +68,7 @@ def parse():
     ap.add_argument("--n-rays", type=int, default=1 << 24)
     ap.add_argument("--mesh", type=int, default=256)
     ap.add_argument("--workload", choices=["slab256", "batched", "stream", "graded", "history",
-                                           "detectors"],
+                                           "detectors", "surrogate"],
                     default="slab256")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -530,6 +534,89 @@ def run_detectors(args, rank, world, local):
     return 0
 
 
+# --------------------------------------------------------------------------- learned cross sections
+
+def run_surrogate(args, rank, world, local):
+    """The surrogate workload: trains the network (vrc_train_surrogate, outside
+    the timed regions), then times with CUDA events (a) the cast with table
+    cross sections, (b) the cast with the surrogate where validation accepts
+    it (table elsewhere), (c) the cast with the network on every ray, and
+    (d) the network's forward pass alone (vrc_mlp_forward on the 2^24 ray
+    energies), whose two 128-wide layers run on tcgen05."""
+    import torch
+    from paper_1706_07476_gb300 import vrc
+    torch.cuda.set_device(local)
+    prob = W.surrogate_mesh(seed=4, n_rays=args.n_rays)
+    ctx = vrc.context_for(prob, vrc.vrc_default_options(form=vrc.VRC_FORM_FP32, device=local))
+    dev = {k: torch.from_numpy(v).cuda() for k, v in prob.rays.items()}
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    steps = max(1, min(args.steps, 10))
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = vrc.vrc_launch_count()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / steps, vrc.vrc_launch_count() - l0
+
+    cast = lambda: vrc.vrc_cast_rays(ctx, dev, stream=stream)  # noqa: E731
+    rep = vrc.vrc_train_surrogate(ctx)
+    out = {}
+    for name, mode in (("table", vrc.VRC_XS_TABLE), ("surrogate_checked", vrc.VRC_XS_SURROGATE)):
+        vrc.vrc_set_xs_mode(ctx, mode)
+        vrc.vrc_reset_tally(ctx, stream)
+        dt, _ = timed(cast)
+        rc, st = vrc.vrc_sync(ctx, stream)
+        assert rc == vrc.VRC_OK, rc
+        seg = st["segments"] / (steps + args.warmup)
+        out[name] = {"segments_per_s": seg / dt, "ms_per_step": 1e3 * dt}
+    every = vrc.vrc_train_surrogate(ctx, vrc.vrc_default_surrogate_options(steps=0, tol=1e30))
+    vrc.vrc_reset_tally(ctx, stream)
+    dt, launches = timed(cast)
+    rc, st = vrc.vrc_sync(ctx, stream)
+    seg = st["segments"] / (steps + args.warmup)
+    out["network_everywhere"] = {"segments_per_s": seg / dt, "ms_per_step": 1e3 * dt,
+                                 "coverage": every["coverage"]}
+    params = torch.from_numpy(vrc.vrc_get_surrogate_params(ctx)).cuda()
+    E = dev["E"]
+    y = torch.empty((prob.n_rays, 16), dtype=torch.float32, device="cuda")
+    fwd = lambda: vrc.vrc_mlp_forward(params, E, W.E_MIN_EV, W.E_MAX_EV, y, stream=stream)  # noqa: E731
+    dt_mlp, _ = timed(fwd)
+    tensor_flop = 2.0 * prob.n_rays * (64 * 128 + 128 * 128)
+    achieved = tensor_flop / dt_mlp / 1e12
+    peaks, src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    H = out["network_everywhere"]
+    line = {
+        "metric": "ray-cell segments/s with the learned cross sections on every ray",
+        "value": H["segments_per_s"], "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": H["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network: bf16 tensor cores, f32 accumulate)",
+        "data": "synthetic", "config": {"workload": SURROGATE, "rays_per_step": prob.n_rays},
+        "modes": out,
+        "training": {"coverage_at_1e-3": rep["coverage"], "median_rel_err": rep["median_rel_err"],
+                     "final_loss": rep["final_loss"]},
+        "mlp_forward": {"ms": 1e3 * dt_mlp, "rays_per_s": prob.n_rays / dt_mlp,
+                        "kernel": "k_mlp_apply_tc (tcgen05.mma kind::f16, M = N = 128)"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"{src} bf16_tflops (cuBLAS bf16 GEMM, burst)",
+                     "algorithmic_flops": "2 x (64 x 128 + 128 x 128) per ray on the tensor cores",
+                     "kernel": "k_mlp_apply_tc"},
+        "gpu_launches": launches,
+    }
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -545,6 +632,8 @@ def main():
         return run_history(args, rank, world, local)
     if args.workload == "detectors":
         return run_detectors(args, rank, world, local)
+    if args.workload == "surrogate":
+        return run_surrogate(args, rank, world, local)
 
     import torch
     import torch.distributed as dist

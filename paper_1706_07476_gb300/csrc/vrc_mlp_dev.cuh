@@ -16,8 +16,14 @@ __device__ __forceinline__ float embed_x(const Embed &em, float E) {
   return (log10f(E) - em.l0) * em.inv_range;
 }
 
+// sin(pi t) and cos(pi t) for t = f_f x: t is reduced exactly to
+// r = t - 2 rint(t / 2) in [-1, 1] (period 2; exact in float32 for |t| < 2^23),
+// then the hardware sine and cosine approximations of pi r (about 1e-6
+// absolute on [-pi, pi], below the bfloat16 rounding of the features).
 __device__ __forceinline__ void embed_pair_x(const Embed &em, float x, int f, float *s, float *c) {
-  sincospif(em.freq[f] * x, s, c);
+  const float t = em.freq[f] * x;
+  const float r = fmaf(-2.f, rintf(0.5f * t), t);
+  __sincosf(3.14159265358979f * r, s, c);
 }
 
 __device__ __forceinline__ void embed_pair(const Embed &em, float E, int f, float *s, float *c) {

@@ -1,9 +1,9 @@
 // Per-ray forward pass of the learned cross-section surrogate on the
 // fifth-generation tensor cores (tcgen05, accumulators in tensor memory).
 //
-// One persistent block per SM holds the bfloat16 weights once and runs three
+// One persistent block per SM holds the bfloat16 weights once and runs four
 // independent groups of 128 threads (four warps each), each on its own tiles
-// of 128 rays with its own operand buffers, mbarrier, named barrier and 128
+// of 128 rays with its own operand buffer, mbarrier, named barrier and 128
 // tensor-memory columns.  Thread t of a group owns ray t of the tile, which
 // is row t of every matrix and lane t of the tensor memory (warp j of the
 // group reads lane quarter j).  Per tile:
@@ -35,7 +35,7 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 constexpr int kTile = 128;            // rays per tile: the MMA's M and the tensor-memory lanes
-constexpr int kGroups = 3;            // independent groups of 128 threads per block
+constexpr int kGroups = 4;            // independent groups of 128 threads per block
 constexpr int kTcThreads = 128 * kGroups;
 constexpr uint32_t kTmemCols = 512;   // allocated once per block; group g uses columns 128 g ..
 constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before a wait gives up
@@ -43,12 +43,16 @@ constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before a wait gives up
 // shared memory (bytes from the block's base)
 constexpr uint32_t kSW1 = 0;          // W1 [128][64] bfloat16, 16 KiB
 constexpr uint32_t kSW2 = 16384;      // W2 [128][128], 32 KiB
-constexpr uint32_t kSW3 = 49152;      // W3 [16][128] float32 (bfloat16 values), 8 KiB
+constexpr uint32_t kSW3 = 49152;      // W3 transposed, [128][16] float32 (bfloat16 values), 8 KiB
 constexpr uint32_t kSB = 57344;       // b1, b2, b3 float32 (272 values)
 constexpr uint32_t kSBar = 58432;     // per group an mbarrier (8 B); then the tensor-memory address
-constexpr uint32_t kSGroup = 59392;   // per group: A0 [128][64] (16 KiB), A1 [128][128] (32 KiB)
-constexpr uint32_t kGroupBytes = 49152;
-constexpr uint32_t kSmemTc = kSGroup + kGroups * kGroupBytes;  // 206,848
+// Per group one 32 KiB operand buffer: A1 [128][128], whose first 16 KiB also
+// hold A0 [128][64] (A0 is read only by the layer-1 MMA, which has completed
+// before A1 is written; A1 is read only by the layer-2 MMA, which has
+// completed before the next tile's A0 is written).
+constexpr uint32_t kSGroup = 59392;
+constexpr uint32_t kGroupBytes = 32768;
+constexpr uint32_t kSmemTc = kSGroup + kGroups * kGroupBytes;  // 190,464
 
 // Byte offset of element (r, k) of a K-column matrix in the core-matrix layout.
 __device__ __forceinline__ uint32_t cm_off(int r, int k, int K) {
@@ -154,12 +158,13 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
   const uint32_t bar = smem_u32(smem + kSBar + 8 * g);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + kSBar + 8 * kGroups);
   unsigned char *A0 = smem + kSGroup + g * kGroupBytes;
-  unsigned char *A1 = A0 + 16384;
+  unsigned char *A1 = A0;
   const float *P = a.params;
 
   stage_weights(smem, kSW1, P + kOffW1, kEmb);
   stage_weights(smem, kSW2, P + kOffW2, kHid);
-  for (int i = tid; i < kOut * kHid; i += kTcThreads) W3f[i] = __bfloat162float(__float2bfloat16_rn(P[kOffW3 + i]));
+  for (int i = tid; i < kOut * kHid; i += kTcThreads)  // W3[m][k] -> W3f[k][m]
+    W3f[(i % kHid) * kOut + i / kHid] = __bfloat162float(__float2bfloat16_rn(P[kOffW3 + i]));
   for (int i = tid; i < kHid; i += kTcThreads) { bs[i] = P[kOffB1 + i]; bs[kHid + i] = P[kOffB2 + i]; }
   if (tid < kOut) bs[2 * kHid + tid] = P[kOffB3 + tid];
   if (gt == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
@@ -261,8 +266,15 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
       for (int j = 0; j < 32; ++j) {
         const int k = c * 32 + j;
         const float h = silu(__uint_as_float(r[j]) + bs[kHid + k]);
+        const float4 *w = reinterpret_cast<const float4 *>(W3f + k * kOut);  // 16 weights, 4 loads
 #pragma unroll
-        for (int m = 0; m < kOut; ++m) p[m] = fmaf(W3f[m * kHid + k], h, p[m]);
+        for (int q = 0; q < kOut / 4; ++q) {
+          const float4 wq = w[q];
+          p[4 * q] = fmaf(wq.x, h, p[4 * q]);
+          p[4 * q + 1] = fmaf(wq.y, h, p[4 * q + 1]);
+          p[4 * q + 2] = fmaf(wq.z, h, p[4 * q + 2]);
+          p[4 * q + 3] = fmaf(wq.w, h, p[4 * q + 3]);
+        }
       }
     }
     fence_before();
