@@ -72,6 +72,11 @@ typedef struct {
   int32_t block;          /* threads per block of the cast kernel; 0 auto */
   int32_t blocks_per_sm;  /* resident blocks per SM for the cast grid; 0 auto */
   int32_t device;         /* CUDA device ordinal for this context; -1 = current device */
+  int32_t stop_at_zero;   /* 1: a ray's walk ends once its transmitted fraction exp(-tau) is
+                             exactly 0 in the form's precision (every later score would be +0,
+                             so the tally is bit for bit the same up to summation order); the
+                             segment counter then counts only the walked segments.  0 (default):
+                             every ray is walked to the mesh exit, as the paper casts it */
 } vrc_options;
 
 /* A uniform 3-D Cartesian mesh (Sec. 3: 3-D Cartesian mesh geometry).

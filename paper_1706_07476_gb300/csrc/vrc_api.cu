@@ -227,6 +227,7 @@ int check_options(const vrc_options *o) {
   if (o->sort < -1 || o->sort > 1) return fail(VRC_ERR_ARG, "options.sort must be -1, 0 or 1");
   if (o->sort_len_buckets != -1 && (o->sort_len_buckets < 1 || o->sort_len_buckets > 256))
     return fail(VRC_ERR_ARG, "options.sort_len_buckets must be -1 or 1..256");
+  if (o->stop_at_zero != 0 && o->stop_at_zero != 1) return fail(VRC_ERR_ARG, "options.stop_at_zero must be 0 or 1");
   return VRC_OK;
 }
 
@@ -328,6 +329,7 @@ CastArgs make_args(const vrc_ctx *c, const RayPtrs &rays) {
   a.n_groups = c->n_groups;
   a.rays = rays;
   a.tally = c->d_tally;
+  a.stop_zero = c->opt.stop_at_zero;
   a.counters = c->d_counters;
   a.status = c->d_status;
   return a;
@@ -547,6 +549,7 @@ void vrc_default_options(vrc_options *opt) {
   opt->block = 0;
   opt->blocks_per_sm = 0;
   opt->device = -1;
+  opt->stop_at_zero = 0;
 }
 
 int vrc_create_mesh(const vrc_mesh_desc *d, const vrc_options *opt, vrc_ctx **out) {

@@ -354,7 +354,7 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &M, float px, float p
                                              float u, float v, float w, float wt, float dn,
                                              const Sink &sink, const float *sg,
                                              const typename Attenuation<FORM>::inv_t *inv,
-                                             int stride, bool *overflow) {
+                                             int stride, bool stop_zero, bool *overflow) {
   const float p[3] = {px, py, pz};
   const float d[3] = {u, v, w};
   const df inf = {INFINITY, 0.f};
@@ -414,6 +414,7 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &M, float px, float p
   uint32_t nseg = 0;
   const int max_steps = M.n[0] + M.n[1] + M.n[2] + 3;
   for (int step = 0;; ++step) {
+    if (stop_zero && att.dead()) break;  // every later score is +0 (opt-in)
     // axis of the nearest crossing (ties resolved x, then y, then z)
     const bool y_first = df_lt(S[1], S[0]);
     df Sk = y_first ? S[1] : S[0];
@@ -487,7 +488,7 @@ __device__ __forceinline__ uint32_t cast_ray_rect(const MeshDev &M, float px, fl
                                                   float u, float v, float w, float wt, float dn,
                                                   const Sink &sink, const float *sg,
                                                   const typename Attenuation<FORM>::inv_t *inv,
-                                                  int stride, bool *overflow) {
+                                                  int stride, bool stop_zero, bool *overflow) {
   const float p[3] = {px, py, pz};
   const float d[3] = {u, v, w};
   const df inf = {INFINITY, 0.f};
@@ -542,6 +543,7 @@ __device__ __forceinline__ uint32_t cast_ray_rect(const MeshDev &M, float px, fl
   uint32_t nseg = 0;
   const int max_steps = M.n[0] + M.n[1] + M.n[2] + 3;
   for (int step = 0;; ++step) {
+    if (stop_zero && att.dead()) break;  // every later score is +0 (opt-in)
     const bool y_first = df_lt(S[1], S[0]);
     df Sk = y_first ? S[1] : S[0];
     const bool z_first = df_lt(S[2], Sk);
@@ -642,10 +644,10 @@ __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int
   bool ovf = false;
   if constexpr (RECT)
     c.seg += cast_ray_rect<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, Maker::make(a, r, g), sig_s, inv_s,
-                                 stride, &ovf);
+                                 stride, a.stop_zero != 0, &ovf);
   else
     c.seg += cast_ray<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, Maker::make(a, r, g), sig_s, inv_s,
-                            stride, &ovf);
+                            stride, a.stop_zero != 0, &ovf);
   c.ovf += ovf;
 }
 

@@ -80,6 +80,7 @@ struct CastArgs {
   double *tally;        // [n_groups][ncells]
   const uint32_t *hist; // [n] history id of each ray (per-history cast only)
   HistTable htab;       // per-history cast only
+  int32_t stop_zero;    // end a walk once its transmitted fraction is exactly 0
   unsigned long long *counters;
   unsigned int *status;
 };

@@ -41,7 +41,8 @@ class VrcError(RuntimeError):
 
 class vrc_options(C.Structure):
     _fields_ = [("form", C.c_int32), ("sort", C.c_int32), ("sort_len_buckets", C.c_int32),
-                ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("device", C.c_int32)]
+                ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("device", C.c_int32),
+                ("stop_at_zero", C.c_int32)]
 
 
 class vrc_mesh_desc(C.Structure):

@@ -19,7 +19,7 @@ static int failures = 0;
 int main(void) {
   vrc_options o;
   vrc_default_options(&o);
-  EXPECT(o.form == VRC_FORM_PLAIN && o.sort == -1 && o.block == 0 && o.device == -1);
+  EXPECT(o.form == VRC_FORM_PLAIN && o.sort == -1 && o.block == 0 && o.device == -1 && o.stop_at_zero == 0);
   vrc_default_options(NULL); /* must not crash */
 
   uint8_t mat[8] = {0, 1, 0, 1, 0, 1, 0, 1};
@@ -60,6 +60,8 @@ int main(void) {
   bad = o; bad.sort_len_buckets = 0;
   EXPECT(vrc_create_mesh(&d, &bad, &c) == VRC_ERR_ARG);
   bad = o; bad.sort_len_buckets = 300;
+  EXPECT(vrc_create_mesh(&d, &bad, &c) == VRC_ERR_ARG);
+  bad = o; bad.stop_at_zero = 2;
   EXPECT(vrc_create_mesh(&d, &bad, &c) == VRC_ERR_ARG);
 
   /* calls on a NULL context */
