@@ -485,7 +485,10 @@ int64_t vrc_launch_count(void);
 /* Number of CUDA devices visible (0 when none or on failure). */
 int vrc_device_count(void);
 
-/* Library version as major*10000 + minor*100 + patch. */
+/* Library version as major*10000 + minor*100 + patch (0.2.0: vrc_options
+ * gained stop_at_zero; rectilinear meshes, per-history moments, the
+ * next-event estimator and streaming buffers were added). */
+#define VRC_VERSION 200
 int vrc_version(void);
 
 #ifdef __cplusplus

@@ -916,7 +916,7 @@ int vrc_device_count(void) {
   return n;
 }
 
-int vrc_version(void) { return 100; }
+int vrc_version(void) { return VRC_VERSION; }
 
 }  // extern "C"
 

@@ -118,7 +118,7 @@ int main(void) {
   EXPECT(vrc_moments_fold(NULL, NULL) == VRC_ERR_ARG);
   EXPECT(vrc_cast_histories(NULL, &r, hist, 1, NULL) == VRC_ERR_ARG);
   EXPECT(vrc_context_stream(NULL) == NULL);
-  EXPECT(vrc_version() >= 100);
+  EXPECT(vrc_version() == VRC_VERSION);
   EXPECT(vrc_device_count() >= 0);
 
   if (failures) return 1;
