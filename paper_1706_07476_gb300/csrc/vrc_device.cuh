@@ -245,10 +245,19 @@ struct Attenuation<kFormFp32> {
 // ---------------------------------------------------------------------------
 // Score sinks: where the walk puts each segment's score.
 // ---------------------------------------------------------------------------
-// The tally: one float64 atomic add into the ray's group slice.
+// The tally: one float64 reduction (fire-and-forget red) into the ray's
+// group slice, with an L2 evict-last cache policy.  One group's slice of a
+// large tally (128 MiB at 256^3) is about the size of the L2; the hint keeps
+// tally lines resident ahead of the streamed ray records (measured 5 % less
+// time at 256^3 x 16 groups).
 struct TallySink {
   double *tal;
-  __device__ __forceinline__ void add(int cell, double v) const { atomicAdd(tal + cell, v); }
+  __device__ __forceinline__ void add(int cell, double v) const {
+    uint64_t policy;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
+    asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.f64 [%0], %1, %2;"
+                 :: "l"(tal + cell), "d"(v), "l"(policy) : "memory");
+  }
 };
 
 // Finalizer of SplitMix64 (Steele, Lea and Flood, "Fast splittable
