@@ -1,0 +1,185 @@
+// C ABI of the tally moments (the sigma of Eqs. 5 and 8): batch folds,
+// per-history casts and the read-back of total and sigma.
+#include "vrc_host.h"
+
+using namespace vrc;
+using namespace vrc::host;
+
+// ---------------------------------------------------------------------------
+// Batch moments of the tally.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int vrc_moments_enable(vrc_ctx *c, int32_t mode) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  if (mode != VRC_MOMENTS_OFF && mode != VRC_MOMENTS_BATCH && mode != VRC_MOMENTS_HISTORY)
+    return fail(VRC_ERR_ARG, "unknown moments mode %d", mode);
+  DeviceGuard g(c->device);
+  VRC_CUDA(cudaStreamSynchronize(c->stream), "synchronizing");
+  c->batches = 0;
+  c->moment_mode = mode;
+  if (mode == VRC_MOMENTS_OFF) {
+    c->momS1.release();
+    c->momS2.release();
+    c->histTab.release();
+    c->histBits.release();
+    c->histCap = 0;
+    c->moments = false;
+    return VRC_OK;
+  }
+  const size_t bytes = sizeof(double) * (size_t)(c->ncells * c->n_groups);
+  VRC_CUDA(c->momS1.ensure(bytes), "allocating tally moments");
+  VRC_CUDA(c->momS2.ensure(bytes), "allocating tally moments");
+  VRC_CUDA(cudaMemsetAsync(c->momS1.p, 0, bytes, c->stream), "zeroing tally moments");
+  VRC_CUDA(cudaMemsetAsync(c->momS2.p, 0, bytes, c->stream), "zeroing tally moments");
+  c->moments = true;
+  return VRC_OK;
+}
+
+int vrc_moments_fold(vrc_ctx *c, void *cuda_stream) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  if (!c->moments) return fail(VRC_ERR_STATE, "moments are not enabled");
+  if (c->moment_mode != VRC_MOMENTS_BATCH) return fail(VRC_ERR_STATE, "moments are per history, not per batch");
+  DeviceGuard g(c->device);
+  cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+  VRC_CUDA(launch_fold_moments(c->d_tally, static_cast<double *>(c->momS1.p),
+                               static_cast<double *>(c->momS2.p), c->ncells * c->n_groups, s),
+           "launching the moment fold");
+  c->batches += 1;
+  return VRC_OK;
+}
+
+int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, int64_t n_histories,
+                       void *cuda_stream) {
+  if (!c) return fail(VRC_ERR_ARG, "context is NULL");
+  if (!r) return fail(VRC_ERR_ARG, "rays is NULL");
+  if (r->n < 0 || n_histories < 0) return fail(VRC_ERR_ARG, "negative ray or history count");
+  if (!c->moments || c->moment_mode != VRC_MOMENTS_HISTORY)
+    return fail(VRC_ERR_STATE, "per-history moments are not enabled");
+  if (c->ncells * c->n_groups >= (int64_t)0xffffffff)
+    return fail(VRC_ERR_ARG, "per-history moments need fewer than 2^32 - 1 (group, cell) bins");
+  if (r->n > 0 && (!history || !r->x || !r->y || !r->z || !r->u || !r->v || !r->w || !r->E || !r->wt))
+    return fail(VRC_ERR_ARG, "a ray or history array is NULL");
+  if (r->n == 0) {
+    c->batches += n_histories;
+    return VRC_OK;
+  }
+  DeviceGuard g(c->device);
+  if (!g.ok) return fail(VRC_ERR_CUDA, "cannot select CUDA device %d", c->device);
+  if (c->xs_dirty) {
+    int rc = build_xs(c);
+    if (rc) {
+      c->xs_dirty = true;
+      return rc;
+    }
+  }
+  cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
+  RayPtrs rp;
+  {
+    int rc = ray_ptrs(c, r, s, &rp);
+    if (rc) return rc;
+  }
+  const uint32_t *hist = history;
+  if (!r->on_device) {
+    VRC_CUDA(c->histIds.ensure(sizeof(uint32_t) * (size_t)r->n), "allocating history staging");
+    VRC_CUDA(cudaMemcpyAsync(c->histIds.p, history, sizeof(uint32_t) * (size_t)r->n, cudaMemcpyHostToDevice, s),
+             "copying history ids to the device");
+    hist = static_cast<const uint32_t *>(c->histIds.p);
+  }
+  // table size: twice an upper bound of the call's segments, a power of two
+  BoundGeom G;
+  for (int k = 0; k < 3; ++k) {
+    G.lo[k] = c->org[k];
+    G.h[k] = c->h[k];
+    G.n[k] = c->n[k];
+    G.e[k] = c->rect ? static_cast<const double *>(c->rectD.p) + c->rect_off[k] : nullptr;
+  }
+  VRC_CUDA(c->histBound.ensure(sizeof(unsigned long long)), "allocating the segment bound");
+  unsigned long long *d_bound = static_cast<unsigned long long *>(c->histBound.p);
+  VRC_CUDA(cudaMemsetAsync(d_bound, 0, sizeof(unsigned long long), s), "zeroing the segment bound");
+  VRC_CUDA(launch_segment_bound(G, rp, d_bound, c->num_sms, s), "launching the segment bound");
+  unsigned long long bound = 0;
+  VRC_CUDA(cudaMemcpyAsync(&bound, d_bound, sizeof bound, cudaMemcpyDeviceToHost, s), "reading the segment bound");
+  VRC_CUDA(cudaStreamSynchronize(s), "waiting for the segment bound");  // host arrays are free from here
+  unsigned long long cap = 1024;
+  while (cap < 2 * bound) cap <<= 1;
+  if (cap > c->histCap) {
+    c->histTab.release();
+    c->histBits.release();
+    c->histCap = 0;
+    size_t free_b = 0, total_b = 0;
+    VRC_CUDA(cudaMemGetInfo(&free_b, &total_b), "querying device memory");
+    const unsigned long long bytes = 16ull * cap + cap / 8ull;
+    if (bytes > free_b / 10 * 9)
+      return fail(VRC_ERR_OOM, "this call's histories need a %.1f GB table (%.1f GB free); split the call",
+                  bytes / 1e9, free_b / 1e9);
+    VRC_CUDA(c->histTab.ensure(16ull * cap), "allocating the per-history table");
+    VRC_CUDA(c->histBits.ensure(cap / 8ull), "allocating the per-history table");
+    VRC_CUDA(cudaMemsetAsync(c->histTab.p, 0, 16ull * cap, s), "clearing the per-history table");
+    VRC_CUDA(cudaMemsetAsync(c->histBits.p, 0, cap / 8ull, s), "clearing the per-history table");
+    c->histCap = cap;
+  }
+  // sort the rays as vrc_cast_rays does, the history ids with them
+  if (c->opt.sort == 1 || (c->opt.sort == -1 && rp.n >= kAutoSortMin)) {
+    VRC_CUDA(c->histSorted.ensure(sizeof(uint32_t) * (size_t)rp.n), "allocating the sorted history ids");
+    uint32_t *sorted = static_cast<uint32_t *>(c->histSorted.p);
+    int rc = sort_rays(c, rp, s, hist, sorted);
+    if (rc) return rc;
+    hist = sorted;
+  }
+  CastArgs a = make_args(c, rp);
+  a.hist = hist;
+  a.htab.e = static_cast<unsigned long long *>(c->histTab.p);
+  a.htab.mask = cap - 1;
+  a.htab.bits = static_cast<unsigned int *>(c->histBits.p);
+  const int form = c->opt.form;
+  const int block = c->opt.block > 0 ? c->opt.block : 256;
+  int bps = c->opt.blocks_per_sm;
+  if (bps <= 0) {
+    VRC_CUDA(cast_hist_occupancy(form, a, block, &bps), "querying occupancy");
+    if (bps <= 0) return fail(VRC_ERR_ARG, "cast kernel does not fit on an SM with %d materials", c->n_materials);
+  }
+  const int grid = (int)std::min<int64_t>((rp.n + block - 1) / block, (int64_t)c->num_sms * bps);
+  VRC_CUDA(launch_cast_hist(form, a, grid, block, s), "launching the per-history cast");
+  VRC_CUDA(launch_hist_drain(a.htab, static_cast<double *>(c->momS1.p), static_cast<double *>(c->momS2.p),
+                             c->num_sms, s),
+           "launching the per-history fold");
+  c->batches += n_histories;
+  return VRC_OK;
+}
+
+int vrc_moments_read(vrc_ctx *c, double *total, double *sigma, int64_t n, int64_t *batches,
+                     void *cuda_stream) {
+  if (!c || !total) return fail(VRC_ERR_ARG, "bad arguments");
+  if (!c->moments) return fail(VRC_ERR_STATE, "moments are not enabled");
+  const int64_t N = c->ncells * c->n_groups;
+  if (n != N) return fail(VRC_ERR_ARG, "moment arrays have %lld entries, caller gave %lld", (long long)N, (long long)n);
+  DeviceGuard g(c->device);
+  int rc = sync_streams(c, cuda_stream);
+  if (rc) return rc;
+  VRC_CUDA(cudaMemcpy(total, c->momS1.p, sizeof(double) * N, cudaMemcpyDeviceToHost), "reading S1");
+  if (sigma) {
+    if (c->batches < 2) {
+      std::memset(sigma, 0, sizeof(double) * N);
+    } else {
+      const int64_t chunk = std::min<int64_t>(N, (int64_t)8 << 20);
+      VRC_CUDA(c->scratch.ensure(sizeof(double) * chunk), "allocating moment staging");
+      for (int64_t off = 0; off < N; off += chunk) {
+        const int64_t m = std::min(chunk, N - off);
+        VRC_CUDA(launch_moment_sigma(static_cast<double *>(c->momS1.p) + off,
+                                     static_cast<double *>(c->momS2.p) + off,
+                                     static_cast<double *>(c->scratch.p), m, (double)c->batches, c->stream),
+                 "launching the moment finalize");
+        VRC_CUDA(cudaMemcpyAsync(sigma + off, c->scratch.p, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream),
+                 "reading sigma");
+        VRC_CUDA(cudaStreamSynchronize(c->stream), "reading sigma");
+      }
+    }
+  }
+  if (batches) *batches = c->batches;
+  unsigned st = 0;
+  VRC_CUDA(cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost), "reading status");
+  return (st & kStatusTableFull) ? status_code(kStatusTableFull) : VRC_OK;
+}
+
+}  // extern "C"

@@ -28,7 +28,6 @@ namespace {
 typedef __nv_bfloat16 bf16;
 constexpr int LD64 = kEmb + 8;   // padded row strides (elements): 16-byte aligned
 constexpr int LD128 = kHid + 8;  // rows, conflict-free ldmatrix
-constexpr int LD16 = kOut + 8;
 constexpr int BM = 64;           // rows per training block (16 per warp)
 constexpr int kTrainThreads = 128;
 
