@@ -305,8 +305,10 @@ void vrc::note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relax
 
 namespace {
 
-// Host batches above this many rays are uploaded and cast chunk by chunk.
-constexpr int64_t kUploadChunk = (int64_t)1 << 22;
+// Host batches above kUploadChunk rays are uploaded and cast chunk by chunk:
+// a small first chunk (only its upload is not overlapped), then full ones.
+constexpr int64_t kUploadChunk = (int64_t)1 << 23;
+constexpr int64_t kFirstChunk = (int64_t)1 << 21;
 
 // Cast of a large host batch with the upload overlapped: chunk i+1 is copied
 // on the context's copy stream while chunk i is sorted and cast on stream s.
@@ -326,9 +328,9 @@ int cast_host_pipelined(vrc_ctx *c, const vrc_rays *r, cudaStream_t s) {
   for (int i = 0; i < 2; ++i) VRC_CUDA(c->up_slot[i].ensure(slot_bytes), "allocating upload slots");
   const float *src[8] = {r->x, r->y, r->z, r->u, r->v, r->w, r->E, r->wt};
   int last = 0;
-  for (int64_t off = 0, i = 0; off < r->n; off += kUploadChunk, ++i) {
+  for (int64_t off = 0, i = 0, m = 0; off < r->n; off += m, ++i) {
     const int slot = (int)(i & 1);
-    const int64_t m = std::min(kUploadChunk, r->n - off);
+    m = std::min(i == 0 ? kFirstChunk : kUploadChunk, r->n - off);
     float *base = static_cast<float *>(c->up_slot[slot].p);
     VRC_CUDA(cudaStreamWaitEvent(c->up_stream, c->up_freed[slot], 0), "ordering an upload");
     RayPtrs rp;
