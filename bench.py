@@ -170,10 +170,10 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def profiled_traffic(kernel_tag: str, workload_tag: str):
-    """DRAM bytes per launch from a committed ncu summary of this kernel on
-    this workload, if it was taken on the current cast kernel source (matched
-    by the recorded source hash)."""
+def profiled_field(kernel_tag: str, workload_tag: str, field: str):
+    """A number from a committed ncu summary of this kernel on this workload
+    (e.g. DRAM bytes per launch), if the summary was taken on the current
+    cast kernel source (matched by the recorded source hash)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}_{workload_tag}.md")
     try:
@@ -183,13 +183,17 @@ def profiled_traffic(kernel_tag: str, workload_tag: str):
     h = hashlib.sha256()
     for f in ("vrc_device.cuh", "vrc_cast.cu"):
         h.update(open(os.path.join(ROOT, "paper_1706_07476_gb300", "csrc", f), "rb").read())
-    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("source_sha256:", "traffic_bytes_per_launch:")))
+    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("source_sha256:", field + ":")))
     if fields.get("source_sha256", "").strip() != h.hexdigest():
         return None
     try:
-        return float(fields["traffic_bytes_per_launch"])
+        return float(fields[field])
     except (KeyError, ValueError):
         return None
+
+
+def profiled_traffic(kernel_tag: str, workload_tag: str):
+    return profiled_field(kernel_tag, workload_tag, "traffic_bytes_per_launch")
 
 
 def cpu_baseline(prob, target_s: float, oracle):
@@ -781,6 +785,18 @@ def main():
             "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)",
             "algorithmic_bytes": f"{BYTES_PER_SEGMENT} B/segment + {BYTES_PER_RAY} B/ray",
             "kernel": f"k_cast<{head}>", "kernel_ms": R["kernel_ms"]}
+    # the kernel's binding limit is instruction issue: warp instructions per
+    # segment from the committed profile, against 4 schedulers x SMs x clock
+    wips = profiled_field(f"k_cast_{head}", args.workload, "warp_instructions_per_segment")
+    if wips:
+        props = torch.cuda.get_device_properties(local)
+        sm_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        cap = props.multi_processor_count * 4 * sm_hz / wips
+        kernel_rate = R["segments_per_step"] / (R["kernel_ms"] / 1e3)
+        roof["issue_roof"] = {"warp_instructions_per_segment": wips, "cap_segments_per_s": cap,
+                              "kernel_segments_per_s": kernel_rate, "frac": kernel_rate / cap,
+                              "basis": "SMs x 4 schedulers x max SM clock / (warp instructions per "
+                                       "segment from the committed ncu profile)"}
 
     extra = {}
     if not args.no_micro and rank == 0:
