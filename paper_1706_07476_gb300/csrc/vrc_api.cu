@@ -170,7 +170,8 @@ int sync_streams(vrc_ctx *c, void *stream) {
 }
 
 
-int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in, uint32_t *carry_out) {
+int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in, uint32_t *carry_out,
+              bool spatial) {
   SortKeyArgs P;
   std::memset(&P, 0, sizeof P);
   for (int k = 0; k < 3; ++k) {
@@ -186,6 +187,12 @@ int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in,
   const int max_cells = c->n[0] + c->n[1] + c->n[2] + 1;
   P.len_width = std::max(1, (max_cells + nl - 1) / nl);
   P.n_keys = c->n_groups * nl + 1;
+  if (spatial) {  // (group, block) keys on at most 8^3 blocks
+    int nb = 8;
+    while (nb > 1 && (int64_t)c->n_groups * nb * nb * nb + 1 > 16384) nb >>= 1;
+    P.blocks_axis = nb;
+    P.n_keys = c->n_groups * nb * nb * nb + 1;
+  }
   SortPlan plan = make_sort_plan(rp.n, P.n_keys);
   VRC_CUDA(c->sortKeys.ensure(plan.bytes_keys), "allocating sort scratch");
   VRC_CUDA(c->sortTable.ensure(plan.bytes_table), "allocating sort scratch");

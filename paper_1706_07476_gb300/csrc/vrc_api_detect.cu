@@ -53,6 +53,12 @@ int vrc_detector_flux(vrc_ctx *c, const vrc_rays *r, const double *det_xyz, int3
       }
       rp.u = rp.v = rp.w = rp.x;  // directions are not used
     }
+    // events sorted by (group, spatial block): the 32 lanes of a warp then
+    // walk from nearby points at similar cross sections
+    if (c->opt.sort == 1 || (c->opt.sort == -1 && rp.n >= kAutoSortMin)) {
+      int rc = sort_rays(c, rp, s, nullptr, nullptr, true);
+      if (rc) return rc;
+    }
     CastArgs a = make_args(c, rp);
     VRC_CUDA(launch_detectors(c->opt.form, a, static_cast<const float *>(c->detPos.p), n_det,
                               static_cast<double *>(c->detOut.p), c->num_sms, s),

@@ -229,8 +229,10 @@ constexpr int64_t kAutoSortMin = 65536;
 // Sorts the batch into context scratch and points rp at the sorted copy.
 // When carry_out is set, carry_in[i] (one uint32 per ray) goes to the sorted
 // position of ray i.
+// With spatial set, the key is (group, spatial block of the start point)
+// instead, for point events (the direction is not used).
 int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in = nullptr,
-              uint32_t *carry_out = nullptr);
+              uint32_t *carry_out = nullptr, bool spatial = false);
 // Sort (optional), surrogate (optional) and cast of a device batch on stream s.
 int cast_device(vrc_ctx *c, RayPtrs rp, cudaStream_t s);
 // Device view of a ray batch: device arrays as given, host arrays copied

@@ -65,6 +65,20 @@ __device__ __forceinline__ uint32_t ray_key(const SortKeyArgs &P, const double *
   const float x = f[0], y = f[1], z = f[2], u = f[3], v = f[4], w = f[5], E = f[6], wt = f[7];
   const float dn = sqrtf(u * u + v * v + w * w);
   const uint32_t reject = (uint32_t)(P.n_keys - 1);
+  if (P.blocks_axis > 0) {  // point events: position, energy and weight only
+    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(E) && isfinite(wt) && E > 0.f)) return reject;
+    const int g = group_of(edges, P.n_groups, (double)E);
+    if (g < 0) return reject;
+    const float p[3] = {x, y, z};
+    int b = 0;
+#pragma unroll
+    for (int k = 2; k >= 0; --k) {
+      const float f = (p[k] - P.lo[k]) / (P.hi[k] - P.lo[k]) * (float)P.blocks_axis;
+      const int bk = f >= 0.f ? min((int)f, P.blocks_axis - 1) : 0;  // also clamps NaN-free outside starts
+      b = b * P.blocks_axis + bk;
+    }
+    return (uint32_t)(g * P.blocks_axis * P.blocks_axis * P.blocks_axis + b);
+  }
   if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(u) && isfinite(v) && isfinite(w) &&
         isfinite(E) && isfinite(wt) && E > 0.f && dn > 0.f && isfinite(dn)))
     return reject;

@@ -20,6 +20,10 @@ struct SortKeyArgs {
   int32_t n_keys;     // n_groups * n_len + 1 (the last key holds rejected rays)
   int32_t chunk;      // rays per block (set by launch_sort)
   int32_t edges_off;  // smem byte offset of the staged group edges (set by launch_sort)
+  // 0: key = (group, crossed-cell bucket).  B > 0: key = (group, spatial
+  // block of the ray's start point on a B x B x B grid over the mesh box);
+  // the direction is not used (point events of the next-event estimator).
+  int32_t blocks_axis;
 };
 
 struct RayOut {
