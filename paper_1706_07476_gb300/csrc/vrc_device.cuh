@@ -6,6 +6,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "vrc_expd.h"
 #include "vrc_internal.h"
 
 namespace vrc {
@@ -174,9 +175,11 @@ template <int FORM>
 struct Attenuation;
 
 // Plain form: optical depth carried as the transmitted fraction T =
-// exp(-tau_in) in float64; every factor exp(-Sigma l) comes from the same
-// expm1 that gives the path term (exp directly once Sigma l >= 8, where
-// 1 + expm1 would lose digits).  score() returns the float64 contribution.
+// exp(-tau_in) in float64.  The cell's factor e^-x, x = Sigma l, and the path
+// term's e^-x - 1 both come from one float64 range reduction (vrc_expd.h:
+// within 1.1 and 1.4 ulp of the exact values).  A void cell (Sigma = 0) has
+// x = 0, factor exactly 1 and path term l.  score() returns the float64
+// contribution.
 template <>
 struct Attenuation<kFormPlain> {
   typedef double inv_t;
@@ -186,17 +189,11 @@ struct Attenuation<kFormPlain> {
   __device__ __forceinline__ explicit Attenuation(float w) : wt((double)w) {}
   __device__ __forceinline__ double score(float sig, double inv, float l) {
     if (T == 0.0) return 0.0;
-    double path, factor;
-    if (sig > 0.f) {
-      double x = (double)sig * (double)l;  // exact: a float product fits a double
-      double em = expm1(-x);
-      path = -em * inv;
-      factor = x < 8.0 ? 1.0 + em : exp(-x);
-    } else {
-      path = (double)l;
-      factor = 1.0;
-    }
-    double s = wt * T * path;
+    const double x = (double)sig * (double)l;  // exact: a float product fits a double
+    double factor, em;
+    expd::exp_expm1(-x, &factor, &em);
+    const double path = sig > 0.f ? -em * inv : (double)l;
+    const double s = wt * T * path;
     T *= factor;
     return s;
   }
