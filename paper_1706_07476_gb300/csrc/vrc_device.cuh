@@ -174,30 +174,32 @@ __device__ __forceinline__ double f2d_bits(float f) {
 template <int FORM>
 struct Attenuation;
 
-// Plain form: optical depth carried as the transmitted fraction T =
-// exp(-tau_in) in float64.  The cell's factor e^-x, x = Sigma l, and the path
-// term's e^-x - 1 both come from one float64 range reduction (vrc_expd.h:
-// within 1.1 and 1.4 ulp of the exact values).  A void cell (Sigma = 0) has
-// x = 0, factor exactly 1 and path term l.  score() returns the float64
+// Plain form: the ray's weight times its transmitted fraction, W = wt
+// exp(-tau_in), carried in float64.  The cell's factor e^-x, x = Sigma l, and
+// the path term's e^-x - 1 both come from one float64 range reduction
+// (vrc_expd.h: within 0.52 and 1.9 ulp of the exact values), indexed from the
+// float32 product Sigma l.  A void cell (Sigma = 0) has x = 0, factor exactly
+// 1 and path term l.  The float32 inputs are widened and W is tested for zero
+// with integer operations, which leaves the FP64 pipe to the 18 float64
+// arithmetic operations of a segment.  score() returns the float64
 // contribution.
 template <>
 struct Attenuation<kFormPlain> {
   typedef double inv_t;
   typedef double score_t;
-  double T = 1.0;
-  double wt;
-  __device__ __forceinline__ explicit Attenuation(float w) : wt((double)w) {}
+  double T;  // wt exp(-tau) at the entry of the current cell (never -0)
+  __device__ __forceinline__ explicit Attenuation(float w) : T(f2d_bits(w)) {}
+  __device__ __forceinline__ bool dead() const { return __double_as_longlong(T) == 0; }
   __device__ __forceinline__ double score(float sig, double inv, float l) {
-    if (T == 0.0) return 0.0;
-    const double x = (double)sig * (double)l;  // exact: a float product fits a double
+    if (dead()) return 0.0;
+    const double ld = f2d_bits(l);
+    const double x = f2d_bits(sig) * ld;  // exact: a float product fits a double
     double factor, em;
-    expd::exp_expm1(-x, &factor, &em);
-    const double path = sig > 0.f ? -em * inv : (double)l;
-    const double s = wt * T * path;
+    expd::exp_expm1(-x, -(sig * l), &factor, &em);
+    const double s = T * (sig > 0.f ? -em * inv : ld);
     T *= factor;
     return s;
   }
-  __device__ __forceinline__ bool dead() const { return T == 0.0; }
   __device__ __forceinline__ static double to_double(double s) { return s; }
 };
 

@@ -1,9 +1,11 @@
-"""The float64 exp / expm1 pair of the plain form (Cody-Waite reduction plus
-a degree-13 Taylor series), built for the host from the same header the
-kernels include, held to 2 ulp of long-double expl / expm1l over y in
-[-760, 0] (about 4e6 points, including both sides of every reduction
-boundary), with (0, -1) below the normal range and exact results at y = 0
-and y = -1e-300."""
+"""The float64 exp / expm1 pair of the plain form (Tang's table-driven
+reduction with 64 entries, a degree-6 Taylor series), built for the host from
+the same header the kernels include: e^y held to 0.6 ulp and e^y - 1 to 2 ulp
+of long-double expl / expm1l over y in [-760, 0] (about 1.8e7 points,
+including both sides of every reduction boundary, each with the float32
+estimate of y the kernels pass and one float32 ulp either side), (0, -1)
+below the normal range, exact results at y = 0 and y = -1e-300; and the
+table's rows against 2^(j/64) from exact decimal arithmetic."""
 from __future__ import annotations
 
 import os
@@ -26,3 +28,23 @@ def test_exp_pair_error_bound(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
     print(r.stdout)
     assert r.returncode == 0, r.stdout + r.stderr
+
+
+def test_exp2_table_is_exact():
+    """Every kExp2Tab row is (nearest float64 to 2^(j/64), nearest float64 to
+    the remainder), checked against 2^(j/64) from exact decimal arithmetic
+    written here, and head + tail is within 2^-104 of it."""
+    import re
+    from decimal import Decimal, getcontext
+    src = open(os.path.join(ROOT, "paper_1706_07476_gb300", "csrc", "vrc_expd.h")).read()
+    body = src[src.index("kExp2Tab[64][2] = {"):]
+    body = body[:body.index("};")]
+    rows = re.findall(r"\{\s*([-0-9a-fx.p+]+)\s*,\s*([-0-9a-fx.p+]+)\s*\}", body)
+    assert len(rows) == 64
+    getcontext().prec = 60
+    for j, (h, l) in enumerate(rows):
+        hi, lo = float.fromhex(h), float.fromhex(l)
+        exact = Decimal(2) ** (Decimal(j) / 64)
+        assert hi == float(exact), j
+        assert lo == float(exact - Decimal(hi)), j
+        assert abs(Decimal(hi) + Decimal(lo) - exact) <= exact * Decimal(2) ** -104, j
