@@ -12,8 +12,12 @@ namespace {
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct SmemLayout {
-  size_t hash, edges, sig, inv, total;
+  size_t hash, edges, sig, inv, queue, total;
 };
+
+// Bytes of one warp's queue for the warp-batched plain walk: (double2 io,
+// int cell) per slot, then 32 ints.
+constexpr size_t kWarpQueueBytes = 32 * kPlainBatch * (sizeof(double2) + sizeof(int32_t)) + 32 * sizeof(int32_t);
 
 SmemLayout smem_layout(int form, const CastArgs &a, int block) {
   SmemLayout L;
@@ -34,12 +38,15 @@ SmemLayout smem_layout(int form, const CastArgs &a, int block) {
     L.inv = off + sizeof(float);
     off += 2 * sizeof(float) * (size_t)a.xs.n_mat * block;
   }
+  off = align_up(off, 16);
+  L.queue = off;
+  if (form == kFormPlain) off += kWarpQueueBytes * (size_t)(block / 32);
   L.total = align_up(off, 16);
   return L;
 }
 
 template <int FORM, bool SURR, typename Maker = TallyMaker, bool RECT = false>
-__global__ void __launch_bounds__(256, 4) k_cast(CastArgs a, SmemLayout L) {
+__global__ void __launch_bounds__(256, FORM == kFormPlain ? 2 : 4) k_cast(CastArgs a, SmemLayout L) {
   typedef typename Attenuation<FORM>::inv_t inv_t;
   extern __shared__ __align__(16) unsigned char smem[];
   int32_t *hash_s = reinterpret_cast<int32_t *>(smem + L.hash);
@@ -57,9 +64,22 @@ __global__ void __launch_bounds__(256, 4) k_cast(CastArgs a, SmemLayout L) {
   const int stride = lanes * blockDim.x;
 
   RayCounts cnt;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.rays.n;
-       r += (int64_t)gridDim.x * blockDim.x)
-    cast_one<FORM, SURR, Maker, RECT>(a, r, hash_s, edges, sig_s, inv_s, stride, cnt);
+  if constexpr (FORM == kFormPlain) {
+    // warp-uniform trip count: the batched walk is warp-collective
+    unsigned char *qb = smem + L.queue + kWarpQueueBytes * (threadIdx.x / 32);
+    const WarpQueue Q = {reinterpret_cast<double2 *>(qb),
+                         reinterpret_cast<int32_t *>(qb + 32 * kPlainBatch * sizeof(double2)),
+                         reinterpret_cast<int32_t *>(qb + 32 * kPlainBatch * (sizeof(double2) + sizeof(int32_t)))};
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < a.rays.n;
+         base += (int64_t)gridDim.x * blockDim.x)
+      cast_one_plain_warp<SURR, Maker, RECT>(a, base + lane, base + lane < a.rays.n, hash_s, edges, sig_s,
+                                       inv_s, stride, Q, cnt);
+  } else {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.rays.n;
+         r += (int64_t)gridDim.x * blockDim.x)
+      cast_one<FORM, SURR, Maker, RECT>(a, r, hash_s, edges, sig_s, inv_s, stride, cnt);
+  }
   flush_counts(cnt, a.counters, a.status);
 }
 

@@ -6,7 +6,9 @@
 #include <math.h>
 #include <stdint.h>
 
-#include "vrc_expd.h"
+#include <type_traits>
+
+#include "vrc_math64.h"
 #include "vrc_internal.h"
 
 namespace vrc {
@@ -109,6 +111,15 @@ __device__ __forceinline__ int group_of(const double *edges, int G, double e) {
 // float32 (the paper's single-precision cross sections).
 // Writes sigma to sg[m*stride] and its reciprocal to inv[m*stride].
 // ---------------------------------------------------------------------------
+// 1/s for s > 0 (0 for s <= 0) in the form's precision: the correctly
+// rounded float32 reciprocal, or the float64 one from m64::rcp.
+template <typename InvT>
+__device__ __forceinline__ InvT recip(float s);
+template <>
+__device__ __forceinline__ float recip<float>(float s) { return s > 0.f ? __frcp_rn(s) : 0.f; }
+template <>
+__device__ __forceinline__ double recip<double>(float s) { return s > 0.f ? m64::rcp(s) : 0.0; }
+
 template <typename InvT>
 __device__ __forceinline__ void xs_lookup(const XsDev &xs, const int32_t *hash_s, float E,
                                           float *sg, InvT *inv, int stride) {
@@ -144,7 +155,7 @@ __device__ __forceinline__ void xs_lookup(const XsDev &xs, const int32_t *hash_s
     float a = __ldg(r0 + m), b = __ldg(r1 + m);
     float s = fmaf(f, b - a, a);
     sg[m * stride] = s;
-    inv[m * stride] = s > 0.f ? InvT(1) / InvT(s) : InvT(0);
+    inv[m * stride] = recip<InvT>(s);
   }
 }
 
@@ -177,7 +188,7 @@ struct Attenuation;
 // Plain form: the ray's weight times its transmitted fraction, W = wt
 // exp(-tau_in), carried in float64.  The cell's factor e^-x, x = Sigma l, and
 // the path term's e^-x - 1 both come from one float64 range reduction
-// (vrc_expd.h: within 0.52 and 1.9 ulp of the exact values), indexed from the
+// (vrc_math64.h: within 0.52 and 1.9 ulp of the exact values), indexed from the
 // float32 product Sigma l.  A void cell (Sigma = 0) has x = 0, factor exactly
 // 1 and path term l.  The float32 inputs are widened and W is tested for zero
 // with integer operations, which leaves the FP64 pipe to the 18 float64
@@ -195,7 +206,7 @@ struct Attenuation<kFormPlain> {
     const double ld = f2d_bits(l);
     const double x = f2d_bits(sig) * ld;  // exact: a float product fits a double
     double factor, em;
-    expd::exp_expm1(-x, -(sig * l), &factor, &em);
+    m64::exp_expm1(-x, -(sig * l), &factor, &em);
     const double s = T * (sig > 0.f ? -em * inv : ld);
     T *= factor;
     return s;
@@ -344,125 +355,161 @@ struct HistMaker {
   }
 };
 
-// Walks one ray through the mesh and adds its Eq. 4 score to every crossed
-// cell through `sink` (the ray's group slice of the tally, or its history's
-// slots).  The ray is the half-line p + s d,
-// s >= 0, with d not necessarily unit: crossing parameters are in units of
-// |d| and lengths are scaled by |d| at the end.  The crossing parameter of
-// plane j on axis k, ((org_k - p_k) + j h_k) * (1/d_k), is re-evaluated in
-// double-float from the integer plane index at every step (never
-// accumulated).  The sum is formed before the product, so a start exactly
-// on a plane gives an exactly zero first segment, as in exact arithmetic.
-// A start
-// outside the box is clipped to it (vacuum outside); the walk ends when the
-// ray leaves the mesh or after max_steps steps (then *overflow is set).
-// Returns the number of positive-length segments scored.
+// The walk of one ray through a uniform mesh, one cell per step.  The ray
+// is the half-line p + s d, s >= 0, with d not necessarily unit: crossing
+// parameters are in units of |d| and lengths are scaled by |d| at the end.
+// The crossing parameter of plane j on axis k, ((org_k - p_k) + j h_k) *
+// (1/d_k), is evaluated in double-float; the sum is formed before the
+// product, so a start exactly on a plane gives an exactly zero first segment,
+// as in exact arithmetic.  A start outside the box is clipped to it (vacuum
+// outside).  Per axis: S0 = first crossing ahead of the start; B = h |1/d|,
+// the spacing of later crossings, which are S0 + m B after m steps on that
+// axis (a sum of two positive terms: about 2^-46 relative, no
+// cancellation); cnt = planes that axis crosses before the ray leaves the
+// mesh.
+struct UniformWalk {
+  df S[3], S0[3], B[3];
+  float m[3], cnt[3];
+  int cst[3];
+  int cell;
+  unsigned mat;  // material of `cell`
+  df s_cur;      // crossing parameter of the current cell's entry
+
+  // The nearest crossing ahead: the segment's exit and the next cell.
+  struct Next {
+    df Sk;
+    int k;
+    float mk;
+    bool leaving;  // the crossing is the mesh boundary
+    int ncell;
+  };
+
+  // Sets up the walk; false if the ray misses the mesh.
+  __device__ __forceinline__ bool init(const MeshDev &M, float px, float py, float pz, float u,
+                                       float v, float w) {
+    const float p[3] = {px, py, pz};
+    const float d[3] = {u, v, w};
+    const df inf = {INFINITY, 0.f};
+    df D[3], R[3];  // org - p and 1/d per axis
+    df s_in = {0.f, 0.f}, s_out = inf;
+    bool miss = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      D[k] = df_add_f(M.org[k], -p[k]);
+      const df Dn = df_add(D[k], df_mul_f(M.h[k], (float)M.n[k]));
+      if (d[k] == 0.f) {
+        R[k] = {0.f, 0.f};
+        if (df_pos(D[k]) || !df_pos(Dn)) miss = true;  // p < lo or p >= hi
+      } else {
+        R[k] = df_rcp(d[k]);
+        df a = df_mul(D[k], R[k]);
+        df b = df_mul(Dn, R[k]);
+        if (d[k] < 0.f) { df t = a; a = b; b = t; }
+        if (df_lt(s_in, a)) s_in = a;
+        if (df_lt(b, s_out)) s_out = b;
+      }
+    }
+    if (miss || !df_lt(s_in, s_out)) return false;
+
+    cell = 0;
+    const int cstride[3] = {1, M.n[0], M.n[0] * M.n[1]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      df c = df_add_f(df_neg(M.org[k]), p[k]);  // p - org
+      if (s_in.hi > 0.f && d[k] != 0.f) c = df_add(c, df_mul_f(s_in, d[k]));
+      const int ik = df_floor_clamp(df_mul(c, M.inv_h[k]), M.n[k]);
+      cell += ik * cstride[k];
+      m[k] = 0.f;
+      if (d[k] == 0.f) {
+        S[k] = inf; S0[k] = inf; B[k] = {0.f, 0.f}; cnt[k] = -1.f; cst[k] = 0;
+      } else {
+        const bool fwd = d[k] > 0.f;
+        S0[k] = df_mul(df_add(D[k], df_mul_f(M.h[k], (float)(ik + (fwd ? 1 : 0)))), R[k]);
+        B[k] = df_mul(M.h[k], fwd ? R[k] : df_neg(R[k]));
+        S[k] = S0[k];
+        cnt[k] = (float)(fwd ? M.n[k] - 1 - ik : ik);
+        cst[k] = fwd ? cstride[k] : -cstride[k];
+      }
+    }
+    s_cur = s_in;
+    mat = __ldg(M.mat + cell);
+    return true;
+  }
+
+  // Axis of the nearest crossing (ties resolved x, then y, then z).
+  __device__ __forceinline__ Next next() const {
+    Next t;
+    const bool y_first = df_lt(S[1], S[0]);
+    t.Sk = y_first ? S[1] : S[0];
+    const bool z_first = df_lt(S[2], t.Sk);
+    if (z_first) t.Sk = S[2];
+    t.k = z_first ? 2 : (y_first ? 1 : 0);
+    t.mk = t.k == 0 ? m[0] : t.k == 1 ? m[1] : m[2];
+    t.leaving = t.mk == (t.k == 0 ? cnt[0] : t.k == 1 ? cnt[1] : cnt[2]);
+    t.ncell = cell + (t.k == 0 ? cst[0] : t.k == 1 ? cst[1] : cst[2]);
+    return t;
+  }
+
+  // Length of the current cell's segment, ending at crossing t.
+  __device__ __forceinline__ float length(const Next &t, float dn) const {
+    return fmaxf(df_diff(t.Sk, s_cur), 0.f) * dn;
+  }
+
+  // Steps into t's cell, whose material is nmat.
+  __device__ __forceinline__ void advance(const MeshDev &, const Next &t, unsigned nmat) {
+    s_cur = t.Sk;
+    cell = t.ncell;
+    mat = nmat;
+    const float mn = t.mk + 1.f;
+    const df Sn = df_add(t.k == 0 ? S0[0] : t.k == 1 ? S0[1] : S0[2],
+                         df_mul_f(t.k == 0 ? B[0] : t.k == 1 ? B[1] : B[2], mn));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a == t.k) { m[a] = mn; S[a] = Sn; }
+    }
+  }
+};
+
+// Walks one ray through a uniform mesh (UniformWalk) and adds its Eq. 4
+// score to every crossed cell through `sink` (the ray's group slice of the
+// tally, or its history's slots).  The walk ends when the ray leaves the
+// mesh or after max_steps steps (then *overflow is set).  Returns the number
+// of positive-length segments scored.
 template <int FORM, typename Sink>
 __device__ __forceinline__ uint32_t cast_ray(const MeshDev &M, float px, float py, float pz,
                                              float u, float v, float w, float wt, float dn,
                                              const Sink &sink, const float *sg,
                                              const typename Attenuation<FORM>::inv_t *inv,
                                              int stride, bool stop_zero, bool *overflow) {
-  const float p[3] = {px, py, pz};
-  const float d[3] = {u, v, w};
-  const df inf = {INFINITY, 0.f};
-  df D[3], R[3];  // org - p and 1/d per axis
-  df s_in = {0.f, 0.f}, s_out = inf;
-  bool miss = false;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    D[k] = df_add_f(M.org[k], -p[k]);
-    const df Dn = df_add(D[k], df_mul_f(M.h[k], (float)M.n[k]));
-    if (d[k] == 0.f) {
-      R[k] = {0.f, 0.f};
-      if (df_pos(D[k]) || !df_pos(Dn)) miss = true;  // p < lo or p >= hi
-    } else {
-      R[k] = df_rcp(d[k]);
-      df a = df_mul(D[k], R[k]);
-      df b = df_mul(Dn, R[k]);
-      if (d[k] < 0.f) { df t = a; a = b; b = t; }
-      if (df_lt(s_in, a)) s_in = a;
-      if (df_lt(b, s_out)) s_out = b;
-    }
-  }
-  if (miss || !df_lt(s_in, s_out)) return 0;
-
-  // Per axis: S0 = first crossing ahead of the start, from the exact
-  // formula above (a start exactly on a plane gives S0 = 0); B = h |1/d|, the
-  // spacing of later crossings, which are S0 + m B after m steps on that axis
-  // (a sum of two positive terms: about 2^-46 relative, no cancellation);
-  // cnt = planes that axis crosses before the ray leaves the mesh.
-  df S[3], S0[3], B[3];
-  float m[3], cnt[3];
-  int cst[3];
-  int cell = 0;
-  const int cstride[3] = {1, M.n[0], M.n[0] * M.n[1]};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    df c = df_add_f(df_neg(M.org[k]), p[k]);  // p - org
-    if (s_in.hi > 0.f && d[k] != 0.f) c = df_add(c, df_mul_f(s_in, d[k]));
-    const int ik = df_floor_clamp(df_mul(c, M.inv_h[k]), M.n[k]);
-    cell += ik * cstride[k];
-    m[k] = 0.f;
-    if (d[k] == 0.f) {
-      S[k] = inf; S0[k] = inf; B[k] = {0.f, 0.f}; cnt[k] = -1.f; cst[k] = 0;
-    } else {
-      const bool fwd = d[k] > 0.f;
-      S0[k] = df_mul(df_add(D[k], df_mul_f(M.h[k], (float)(ik + (fwd ? 1 : 0)))), R[k]);
-      B[k] = df_mul(M.h[k], fwd ? R[k] : df_neg(R[k]));
-      S[k] = S0[k];
-      cnt[k] = (float)(fwd ? M.n[k] - 1 - ik : ik);
-      cst[k] = fwd ? cstride[k] : -cstride[k];
-    }
-  }
-
+  UniformWalk W;
+  if (!W.init(M, px, py, pz, u, v, w)) return 0;
   Attenuation<FORM> att(wt);
-  df s_cur = s_in;
-  unsigned mat = __ldg(M.mat + cell);
   uint32_t nseg = 0;
   const int max_steps = M.n[0] + M.n[1] + M.n[2] + 3;
   for (int step = 0;; ++step) {
     if (stop_zero && att.dead()) break;  // every later score is +0 (opt-in)
-    // axis of the nearest crossing (ties resolved x, then y, then z)
-    const bool y_first = df_lt(S[1], S[0]);
-    df Sk = y_first ? S[1] : S[0];
-    const bool z_first = df_lt(S[2], Sk);
-    if (z_first) Sk = S[2];
-    const int k = z_first ? 2 : (y_first ? 1 : 0);
-    const float mk = k == 0 ? m[0] : k == 1 ? m[1] : m[2];
-    const bool leaving = mk == (k == 0 ? cnt[0] : k == 1 ? cnt[1] : cnt[2]);
-    const int ncell = cell + (k == 0 ? cst[0] : k == 1 ? cst[1] : cst[2]);
+    const UniformWalk::Next t = W.next();
     // FP32 form: once every score is +0 the walk skips the loads of the next
     // cell's material and of sigma (the plain form measured faster keeping them)
     const bool live = FORM == kFormFp32 ? !att.dead() : true;
-    const unsigned nmat = (leaving || !live) ? 0u : __ldg(M.mat + ncell);  // prefetch the next cell
+    const unsigned nmat = (t.leaving || !live) ? 0u : __ldg(M.mat + t.ncell);  // prefetch the next cell
 
-    const float l = fmaxf(df_diff(Sk, s_cur), 0.f) * dn;
+    const float l = W.length(t, dn);
     if (live) {
       typename Attenuation<FORM>::score_t sc;
       if constexpr (FORM == kFormFp32) {  // sigma and 1/sigma interleaved: one 8-byte load
-        const float2 si = *reinterpret_cast<const float2 *>(sg + mat * stride);
+        const float2 si = *reinterpret_cast<const float2 *>(sg + W.mat * stride);
         sc = att.score(si.x, si.y, l);
       } else {
-        sc = att.score(sg[mat * stride], inv[mat * stride], l);
+        sc = att.score(sg[W.mat * stride], inv[W.mat * stride], l);
       }
-      if (sc != 0) sink.add(cell, Attenuation<FORM>::to_double(sc));
+      if (sc != 0) sink.add(W.cell, Attenuation<FORM>::to_double(sc));
     }
     nseg += l > 0.f;
 
-    if (leaving) break;
+    if (t.leaving) break;
     if (step >= max_steps) { *overflow = true; break; }
-    s_cur = Sk;
-    cell = ncell;
-    mat = nmat;
-    // next crossing on the stepped axis
-    const float mn = mk + 1.f;
-    const df Sn = df_add(k == 0 ? S0[0] : k == 1 ? S0[1] : S0[2],
-                         df_mul_f(k == 0 ? B[0] : k == 1 ? B[1] : B[2], mn));
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (a == k) { m[a] = mn; S[a] = Sn; }
-    }
+    W.advance(M, t, nmat);
   }
   return nseg;
 }
@@ -487,106 +534,263 @@ __device__ __forceinline__ int locate_rect(const MeshDev &M, int k, df c) {
   return lo;
 }
 
-// cast_ray on a rectilinear mesh (planes at given positions per axis).  The
-// crossing of plane j on axis k, (edge_k[j] - p_k) * (1/d_k), is evaluated
-// in double-float from the plane index at every step (never accumulated);
-// the walk leaves the mesh when the stepped axis crosses its last plane.
+// The walk of one ray through a rectilinear mesh (planes at given positions
+// per axis).  The crossing of plane j on axis k, (edge_k[j] - p_k) * (1/d_k),
+// is evaluated in double-float from the plane index at every step (never
+// accumulated); the walk leaves the mesh when the stepped axis crosses its
+// last plane.  Per axis: J = index of the next plane ahead, last = the plane
+// that leaves the mesh, js = +-1 plane step.
+struct RectWalk {
+  float p[3];
+  df R[3];  // 1/d per axis
+  df S[3];
+  int J[3], last[3], js[3], cst[3];
+  int cell;
+  unsigned mat;  // material of `cell`
+  df s_cur;      // crossing parameter of the current cell's entry
+
+  struct Next {
+    df Sk;
+    int k;
+    int Jk;
+    bool leaving;  // the crossing is the mesh boundary
+    int ncell;
+  };
+
+  // Sets up the walk; false if the ray misses the mesh.
+  __device__ __forceinline__ bool init(const MeshDev &M, float px, float py, float pz, float u,
+                                       float v, float w) {
+    p[0] = px; p[1] = py; p[2] = pz;
+    const float d[3] = {u, v, w};
+    const df inf = {INFINITY, 0.f};
+    df s_in = {0.f, 0.f}, s_out = inf;
+    bool miss = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const df D0 = df_add_f(mesh_plane(M, k, 0), -p[k]);
+      const df Dn = df_add_f(mesh_plane(M, k, M.n[k]), -p[k]);
+      if (d[k] == 0.f) {
+        R[k] = {0.f, 0.f};
+        if (df_pos(D0) || !df_pos(Dn)) miss = true;  // p < lo or p >= hi
+      } else {
+        R[k] = df_rcp(d[k]);
+        df a = df_mul(D0, R[k]);
+        df b = df_mul(Dn, R[k]);
+        if (d[k] < 0.f) { df t = a; a = b; b = t; }
+        if (df_lt(s_in, a)) s_in = a;
+        if (df_lt(b, s_out)) s_out = b;
+      }
+    }
+    if (miss || !df_lt(s_in, s_out)) return false;
+
+    cell = 0;
+    const int cstride[3] = {1, M.n[0], M.n[0] * M.n[1]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      df c = {p[k], 0.f};
+      if (s_in.hi > 0.f && d[k] != 0.f) c = df_add(c, df_mul_f(s_in, d[k]));
+      const int ik = locate_rect(M, k, c);
+      cell += ik * cstride[k];
+      if (d[k] == 0.f) {
+        S[k] = inf; J[k] = 0; last[k] = -1; js[k] = 0; cst[k] = 0;
+      } else {
+        const bool fwd = d[k] > 0.f;
+        J[k] = fwd ? ik + 1 : ik;
+        last[k] = fwd ? M.n[k] : 0;
+        js[k] = fwd ? 1 : -1;
+        cst[k] = fwd ? cstride[k] : -cstride[k];
+        S[k] = df_mul(df_add_f(mesh_plane(M, k, J[k]), -p[k]), R[k]);
+      }
+    }
+    s_cur = s_in;
+    mat = __ldg(M.mat + cell);
+    return true;
+  }
+
+  // Axis of the nearest crossing (ties resolved x, then y, then z).
+  __device__ __forceinline__ Next next() const {
+    Next t;
+    const bool y_first = df_lt(S[1], S[0]);
+    t.Sk = y_first ? S[1] : S[0];
+    const bool z_first = df_lt(S[2], t.Sk);
+    if (z_first) t.Sk = S[2];
+    t.k = z_first ? 2 : (y_first ? 1 : 0);
+    t.Jk = t.k == 0 ? J[0] : t.k == 1 ? J[1] : J[2];
+    t.leaving = t.Jk == (t.k == 0 ? last[0] : t.k == 1 ? last[1] : last[2]);
+    t.ncell = cell + (t.k == 0 ? cst[0] : t.k == 1 ? cst[1] : cst[2]);
+    return t;
+  }
+
+  // Length of the current cell's segment, ending at crossing t.
+  __device__ __forceinline__ float length(const Next &t, float dn) const {
+    return fmaxf(df_diff(t.Sk, s_cur), 0.f) * dn;
+  }
+
+  // Steps into t's cell, whose material is nmat.
+  __device__ __forceinline__ void advance(const MeshDev &M, const Next &t, unsigned nmat) {
+    s_cur = t.Sk;
+    cell = t.ncell;
+    mat = nmat;
+    const int Jn = t.Jk + (t.k == 0 ? js[0] : t.k == 1 ? js[1] : js[2]);
+    const float pk = t.k == 0 ? p[0] : t.k == 1 ? p[1] : p[2];
+    const df Sn = df_mul(df_add_f(mesh_plane(M, t.k, Jn), -pk),
+                         t.k == 0 ? R[0] : t.k == 1 ? R[1] : R[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a == t.k) { J[a] = Jn; S[a] = Sn; }
+    }
+  }
+};
+
+// cast_ray on a rectilinear mesh (RectWalk).
 template <int FORM, typename Sink>
 __device__ __forceinline__ uint32_t cast_ray_rect(const MeshDev &M, float px, float py, float pz,
                                                   float u, float v, float w, float wt, float dn,
                                                   const Sink &sink, const float *sg,
                                                   const typename Attenuation<FORM>::inv_t *inv,
                                                   int stride, bool stop_zero, bool *overflow) {
-  const float p[3] = {px, py, pz};
-  const float d[3] = {u, v, w};
-  const df inf = {INFINITY, 0.f};
-  df R[3];
-  df s_in = {0.f, 0.f}, s_out = inf;
-  bool miss = false;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const df D0 = df_add_f(mesh_plane(M, k, 0), -p[k]);
-    const df Dn = df_add_f(mesh_plane(M, k, M.n[k]), -p[k]);
-    if (d[k] == 0.f) {
-      R[k] = {0.f, 0.f};
-      if (df_pos(D0) || !df_pos(Dn)) miss = true;  // p < lo or p >= hi
-    } else {
-      R[k] = df_rcp(d[k]);
-      df a = df_mul(D0, R[k]);
-      df b = df_mul(Dn, R[k]);
-      if (d[k] < 0.f) { df t = a; a = b; b = t; }
-      if (df_lt(s_in, a)) s_in = a;
-      if (df_lt(b, s_out)) s_out = b;
-    }
-  }
-  if (miss || !df_lt(s_in, s_out)) return 0;
-
-  // per axis: J = index of the next plane ahead, last = the plane that
-  // leaves the mesh, js = +-1 plane step
-  df S[3];
-  int J[3], last[3], js[3], cst[3];
-  int cell = 0;
-  const int cstride[3] = {1, M.n[0], M.n[0] * M.n[1]};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    df c = {p[k], 0.f};
-    if (s_in.hi > 0.f && d[k] != 0.f) c = df_add(c, df_mul_f(s_in, d[k]));
-    const int ik = locate_rect(M, k, c);
-    cell += ik * cstride[k];
-    if (d[k] == 0.f) {
-      S[k] = inf; J[k] = 0; last[k] = -1; js[k] = 0; cst[k] = 0;
-    } else {
-      const bool fwd = d[k] > 0.f;
-      J[k] = fwd ? ik + 1 : ik;
-      last[k] = fwd ? M.n[k] : 0;
-      js[k] = fwd ? 1 : -1;
-      cst[k] = fwd ? cstride[k] : -cstride[k];
-      S[k] = df_mul(df_add_f(mesh_plane(M, k, J[k]), -p[k]), R[k]);
-    }
-  }
-
+  RectWalk W;
+  if (!W.init(M, px, py, pz, u, v, w)) return 0;
   Attenuation<FORM> att(wt);
-  df s_cur = s_in;
-  unsigned mat = __ldg(M.mat + cell);
   uint32_t nseg = 0;
   const int max_steps = M.n[0] + M.n[1] + M.n[2] + 3;
   for (int step = 0;; ++step) {
     if (stop_zero && att.dead()) break;  // every later score is +0 (opt-in)
-    const bool y_first = df_lt(S[1], S[0]);
-    df Sk = y_first ? S[1] : S[0];
-    const bool z_first = df_lt(S[2], Sk);
-    if (z_first) Sk = S[2];
-    const int k = z_first ? 2 : (y_first ? 1 : 0);
-    const int Jk = k == 0 ? J[0] : k == 1 ? J[1] : J[2];
-    const bool leaving = Jk == (k == 0 ? last[0] : k == 1 ? last[1] : last[2]);
-    const int ncell = cell + (k == 0 ? cst[0] : k == 1 ? cst[1] : cst[2]);
+    const RectWalk::Next t = W.next();
     const bool live = FORM == kFormFp32 ? !att.dead() : true;
-    const unsigned nmat = (leaving || !live) ? 0u : __ldg(M.mat + ncell);
+    const unsigned nmat = (t.leaving || !live) ? 0u : __ldg(M.mat + t.ncell);
 
-    const float l = fmaxf(df_diff(Sk, s_cur), 0.f) * dn;
+    const float l = W.length(t, dn);
     if (live) {
       typename Attenuation<FORM>::score_t sc;
       if constexpr (FORM == kFormFp32) {
-        const float2 si = *reinterpret_cast<const float2 *>(sg + mat * stride);
+        const float2 si = *reinterpret_cast<const float2 *>(sg + W.mat * stride);
         sc = att.score(si.x, si.y, l);
       } else {
-        sc = att.score(sg[mat * stride], inv[mat * stride], l);
+        sc = att.score(sg[W.mat * stride], inv[W.mat * stride], l);
       }
-      if (sc != 0) sink.add(cell, Attenuation<FORM>::to_double(sc));
+      if (sc != 0) sink.add(W.cell, Attenuation<FORM>::to_double(sc));
     }
     nseg += l > 0.f;
 
-    if (leaving) break;
+    if (t.leaving) break;
     if (step >= max_steps) { *overflow = true; break; }
-    s_cur = Sk;
-    cell = ncell;
-    mat = nmat;
-    const int Jn = Jk + (k == 0 ? js[0] : k == 1 ? js[1] : js[2]);
-    const df Sn = df_mul(df_add_f(mesh_plane(M, k, Jn), -p[k]), k == 0 ? R[0] : k == 1 ? R[1] : R[2]);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (a == k) { J[a] = Jn; S[a] = Sn; }
+    W.advance(M, t, nmat);
+  }
+  return nseg;
+}
+
+// ---------------------------------------------------------------------------
+// Plain form, with the float64 work shared by the warp.
+// A float64 operation occupies GB300's FP64 pipe for a whole warp however
+// few of its lanes are active, and the lanes of a warp reach the ends of
+// their rays' live stretches at different steps.  So the walk and the score
+// are split: in rounds, every lane walks up to kPlainBatch steps of its ray
+// and queues each positive-length segment that can still score (sigma,
+// length, 1/sigma, cell) in the warp's shared-memory queue; the warp then
+// computes e^-x and the path term (-(e^-x - 1)/Sigma, or l in void) for all
+// queued segments, 32 at a time, each lane taking any lane's segment; last,
+// each lane applies its own segments in order: score = W * path term, W *=
+// e^-x, tally add.  The result is the unbatched walk's, operation for
+// operation.  A segment is queued only while the ray's float32 optical
+// depth is below 760 + max(0, ln wt): beyond that W = wt e^-tau is exactly
+// 0 in float64 (e^-745.2 is below half the smallest subnormal), so the
+// segment's score is +0; the float32 depth is accurate to far better than
+// the margin.  Warp-collective: all 32 lanes call it, `active` false for a
+// lane without a ray.  Every lane's walk ends within max_steps + 1 steps, so
+// the rounds end.
+// ---------------------------------------------------------------------------
+constexpr int kPlainBatch = 8;
+
+// A warp's queue: io[32 kPlainBatch] holds (sigma, length, 1/sigma) and then
+// (e^-x, path term) per segment, lane-major; cell[32 kPlainBatch]; pre[32]
+// holds each lane's first index in the compacted order.
+struct WarpQueue {
+  double2 *io;
+  int32_t *cell;
+  int32_t *pre;
+};
+
+template <typename Walk, typename Sink>
+__device__ __forceinline__ uint32_t cast_ray_plain_warp(const MeshDev &M, bool active, float px,
+                                                        float py, float pz, float u, float v, float w,
+                                                        float wt, float dn, const Sink &sink,
+                                                        const float *sg, const double *inv,
+                                                        int stride, bool stop_zero, bool *overflow,
+                                                        const WarpQueue &Q) {
+  const unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  Walk W;
+  if (active) active = W.init(M, px, py, pz, u, v, w);
+  double T = f2d_bits(wt);  // wt exp(-tau) at the entry of the next segment to apply
+  float tau = 0.f;          // float32 optical depth walked so far
+  const float tau_dead = 760.f + (wt > 1.f ? __logf(wt) : 0.f);
+  uint32_t nseg = 0;
+  const int max_steps = M.n[0] + M.n[1] + M.n[2] + 3;
+  int step = 0;
+  for (;;) {
+    // 1. walk: queue up to kPlainBatch segments of this lane's ray
+    int nq = 0;
+    if (active && stop_zero && __double_as_longlong(T) == 0) active = false;
+    for (int j = 0; j < kPlainBatch && active; ++j) {
+      const typename Walk::Next t = W.next();
+      const unsigned nmat = t.leaving ? 0u : __ldg(M.mat + t.ncell);  // prefetch the next cell
+      const float l = W.length(t, dn);
+      if (l > 0.f) {
+        ++nseg;
+        if (tau < tau_dead) {
+          const float sig = sg[W.mat * stride];
+          const int slot = lane * kPlainBatch + nq;
+          Q.io[slot] = make_double2(__hiloint2double(__float_as_int(l), __float_as_int(sig)),
+                                    inv[W.mat * stride]);
+          Q.cell[slot] = W.cell;
+          ++nq;
+          tau = fmaf(sig, l, tau);
+        }
+      }
+      if (t.leaving) { active = false; break; }
+      if (step >= max_steps) { *overflow = true; active = false; break; }
+      ++step;
+      W.advance(M, t, nmat);
     }
+    // 2. e^-x and path terms of every queued segment, 32 at a time
+    __syncwarp(kAll);
+    int incl = nq;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kAll, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(kAll, incl, 31);
+    Q.pre[lane] = incl - nq;
+    __syncwarp(kAll);
+    for (int gi = lane; gi < total; gi += 32) {
+      int o = 0;  // owner: the last lane whose first index is <= gi
+#pragma unroll
+      for (int b = 16; b > 0; b >>= 1)
+        if (Q.pre[o + b] <= gi) o += b;
+      const int slot = o * kPlainBatch + (gi - Q.pre[o]);
+      const double2 in = Q.io[slot];
+      const float sig = __int_as_float(__double2loint(in.x));
+      const float l = __int_as_float(__double2hiint(in.x));
+      const double ld = f2d_bits(l);
+      const double x = f2d_bits(sig) * ld;  // exact: a float product fits a double
+      double factor, em;
+      m64::exp_expm1(-x, -(sig * l), &factor, &em);
+      Q.io[slot] = make_double2(factor, sig > 0.f ? -em * in.y : ld);
+    }
+    __syncwarp(kAll);
+    // 3. this lane's scores, in walk order
+    for (int j = 0; j < nq; ++j) {
+      const int slot = lane * kPlainBatch + j;
+      const double2 fp = Q.io[slot];
+      if (__double_as_longlong(T) != 0) {
+        const double sc = T * fp.y;
+        T *= fp.x;
+        if (sc != 0.0) sink.add(Q.cell[slot], sc);
+      }
+    }
+    if (!__any_sync(kAll, active)) break;
   }
   return nseg;
 }
@@ -608,12 +812,21 @@ struct RayCounts {
   uint32_t seg = 0, rays = 0, rej = 0, ovf = 0;
 };
 
-// One ray of a cast: validation, group, cross sections, walk and score.
-template <int FORM, bool SURR = false, typename Maker = TallyMaker, bool RECT = false>
-__device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int32_t *hash_s,
-                                         const double *edges, float *sig_s,
-                                         typename Attenuation<FORM>::inv_t *inv_s, int stride,
-                                         RayCounts &c) {
+// A validated ray: position, direction (and its norm), weight, group.
+struct RayIn {
+  float x, y, z, u, v, w, wt, dn;
+  int g;
+};
+
+// Loads ray r, validates it, finds its group and writes the cross sections
+// of every material at its energy (and their reciprocals) to this thread's
+// columns of sig_s / inv_s.  False for a rejected ray (counted) or one
+// outside the group structure.
+template <int FORM, bool SURR>
+__device__ __forceinline__ bool ray_setup(const CastArgs &a, int64_t r, const int32_t *hash_s,
+                                          const double *edges, float *sig_s,
+                                          typename Attenuation<FORM>::inv_t *inv_s, int stride,
+                                          RayCounts &c, RayIn &ray) {
   float f[8];
   load_ray(a.rays, r, f);
   const float x = f[0], y = f[1], z = f[2], u = f[3], v = f[4], w = f[5], E = f[6], wt = f[7];
@@ -622,10 +835,10 @@ __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int
   if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(u) && isfinite(v) && isfinite(w) &&
         isfinite(E) && isfinite(wt) && E > 0.f && dn > 0.f && isfinite(dn))) {
     ++c.rej;
-    return;
+    return false;
   }
   const int g = group_of(edges, a.n_groups, (double)E);
-  if (g < 0) return;
+  if (g < 0) return false;
   bool from_table = true;
   if (SURR) {  // surrogate sigma, unless this ray's energy bin is flagged
     const float4 *q = reinterpret_cast<const float4 *>(a.sig_ray + r * 16);
@@ -640,22 +853,53 @@ __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int
           const int m = 4 * m4 + e;
           if (m < a.xs.n_mat) {
             sig_s[m * stride] = s4[e];
-            inv_s[m * stride] = s4[e] > 0.f ? typename Attenuation<FORM>::inv_t(1) /
-                                                  typename Attenuation<FORM>::inv_t(s4[e])
-                                            : typename Attenuation<FORM>::inv_t(0);
+            inv_s[m * stride] = recip<typename Attenuation<FORM>::inv_t>(s4[e]);
           }
         }
       }
     }
   }
   if (from_table) xs_lookup(a.xs, hash_s, E, sig_s, inv_s, stride);
+  ray = {x, y, z, u, v, w, wt, dn, g};
+  return true;
+}
+
+// One ray of a cast: validation, group, cross sections, walk and score.
+template <int FORM, bool SURR = false, typename Maker = TallyMaker, bool RECT = false>
+__device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int32_t *hash_s,
+                                         const double *edges, float *sig_s,
+                                         typename Attenuation<FORM>::inv_t *inv_s, int stride,
+                                         RayCounts &c) {
+  RayIn q;
+  if (!ray_setup<FORM, SURR>(a, r, hash_s, edges, sig_s, inv_s, stride, c, q)) return;
   bool ovf = false;
   if constexpr (RECT)
-    c.seg += cast_ray_rect<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, Maker::make(a, r, g), sig_s, inv_s,
-                                 stride, a.stop_zero != 0, &ovf);
+    c.seg += cast_ray_rect<FORM>(a.mesh, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn,
+                                 Maker::make(a, r, q.g), sig_s, inv_s, stride, a.stop_zero != 0, &ovf);
   else
-    c.seg += cast_ray<FORM>(a.mesh, x, y, z, u, v, w, wt, dn, Maker::make(a, r, g), sig_s, inv_s,
-                            stride, a.stop_zero != 0, &ovf);
+    c.seg += cast_ray<FORM>(a.mesh, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn, Maker::make(a, r, q.g),
+                            sig_s, inv_s, stride, a.stop_zero != 0, &ovf);
+  c.ovf += ovf;
+}
+
+// One ray per lane of a warp, plain form, through the warp-batched walk
+// (cast_ray_plain_warp) on a uniform or rectilinear mesh.  Warp-collective:
+// every lane calls it, with has_ray false where its index is past the last
+// ray.
+template <bool SURR, typename Maker, bool RECT>
+__device__ __forceinline__ void cast_one_plain_warp(const CastArgs &a, int64_t r, bool has_ray,
+                                                    const int32_t *hash_s, const double *edges,
+                                                    float *sig_s, double *inv_s, int stride,
+                                                    const WarpQueue &Q, RayCounts &c) {
+  typedef typename std::conditional<RECT, RectWalk, UniformWalk>::type Walk;
+  RayIn q = {};
+  const bool ok =
+      has_ray && ray_setup<kFormPlain, SURR>(a, r, hash_s, edges, sig_s, inv_s, stride, c, q);
+  bool ovf = false;
+  // a lane without a ray builds its (unused) sink from ray 0 of group 0
+  c.seg += cast_ray_plain_warp<Walk>(a.mesh, ok, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn,
+                                     Maker::make(a, ok ? r : 0, ok ? q.g : 0), sig_s, inv_s, stride,
+                                     a.stop_zero != 0, &ovf, Q);
   c.ovf += ovf;
 }
 

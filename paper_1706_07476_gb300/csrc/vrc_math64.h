@@ -1,3 +1,6 @@
+// Float64 helpers of the plain form: exp(y) and exp(y) - 1 for y <= 0 from
+// one argument reduction, and 1/s for a float32 s.
+//
 // exp(y) and exp(y) - 1 in float64 for y <= 0, both from one argument
 // reduction.  Used by the plain (float64) form of Eq. 4, where every segment
 // needs the cell's transmitted factor e^-x and the path term's e^-x - 1.
@@ -28,7 +31,7 @@
 // and the pair returns (0, -1): every score that depends on it is below
 // 1e-300.  The float32 estimate is clamped at -1000 before n is formed.
 //
-// kExp2Tab is written by vrc_expd_table.py (exact decimal arithmetic).  The
+// kExp2Tab is written by vrc_math64_table.py (exact decimal arithmetic).  The
 // host build of this header (no __CUDACC__) serves the CPU test that holds
 // both results to 2 ulp of a long-double reference.
 #pragma once
@@ -36,17 +39,17 @@
 #include <stdint.h>
 
 #ifdef __CUDACC__
-#define VRC_EXPD_FN __host__ __device__ __forceinline__
+#define VRC_M64_FN __host__ __device__ __forceinline__
 #else
 #include <math.h>
 #include <string.h>
-#define VRC_EXPD_FN static inline
+#define VRC_M64_FN static inline
 #endif
 
 namespace vrc {
-namespace expd {
+namespace m64 {
 
-VRC_EXPD_FN double bits_to_double(uint64_t b) {
+VRC_M64_FN double bits_to_double(uint64_t b) {
 #ifdef __CUDA_ARCH__
   return __longlong_as_double((long long)b);
 #else
@@ -56,7 +59,7 @@ VRC_EXPD_FN double bits_to_double(uint64_t b) {
 #endif
 }
 
-VRC_EXPD_FN uint32_t float_bits(float f) {
+VRC_M64_FN uint32_t float_bits(float f) {
 #ifdef __CUDA_ARCH__
   return __float_as_uint(f);
 #else
@@ -66,7 +69,7 @@ VRC_EXPD_FN uint32_t float_bits(float f) {
 #endif
 }
 
-VRC_EXPD_FN double fmad(double a, double b, double c) {
+VRC_M64_FN double fmad(double a, double b, double c) {
 #ifdef __CUDA_ARCH__
   return __fma_rn(a, b, c);
 #else
@@ -74,7 +77,7 @@ VRC_EXPD_FN double fmad(double a, double b, double c) {
 #endif
 }
 
-VRC_EXPD_FN float fmaf_rn(float a, float b, float c) {
+VRC_M64_FN float fmaf_rn(float a, float b, float c) {
 #ifdef __CUDA_ARCH__
   return __fmaf_rn(a, b, c);
 #else
@@ -167,7 +170,7 @@ static const double kExp2Tab[64][2] = {
     {0x1.fa7c1819e90d8p+0, 0x1.74853f3a5931ep-55},
 };
 
-VRC_EXPD_FN void table_entry(uint32_t j, double *hi, double *lo) {
+VRC_M64_FN void table_entry(uint32_t j, double *hi, double *lo) {
 #ifdef __CUDA_ARCH__
   const double2 v = __ldg(reinterpret_cast<const double2 *>(kExp2Tab[j]));
   *hi = v.x;
@@ -180,7 +183,7 @@ VRC_EXPD_FN void table_entry(uint32_t j, double *hi, double *lo) {
 
 // Writes e^y to *ey and e^y - 1 to *em1, for y <= 0 (not NaN); yf is y
 // rounded to float32 (or any float32 within 2^-23 |y| of it).
-VRC_EXPD_FN void exp_expm1(double y, float yf, double *ey, double *em1) {
+VRC_M64_FN void exp_expm1(double y, float yf, double *ey, double *em1) {
   yf = yf > -1000.f ? yf : -1000.f;
   const float tf = fmaf_rn(yf, kInvCf, kRoundF);
   const int32_t n = (int32_t)(float_bits(tf) - kRoundFBits);  // nearest(64 yf / ln2)
@@ -205,5 +208,25 @@ VRC_EXPD_FN void exp_expm1(double y, float yf, double *ey, double *em1) {
   *em1 = in_range ? fmad(s, c, a - 1.0) : -1.0;
 }
 
-}  // namespace expd
+// 1/s in float64 for a float32 s > 0, from the float32 reciprocal r0 =
+// 1/s (1 + d), |d| <= 2^-24 (correctly rounded), and one Newton-Raphson step
+// taken to third order: with e = 1 - s r0 = -d (exact: s r0 is a 48-bit
+// product), 1/s = r0 (1 + e + e^2 + ...), so r = r0 + r0 (e + e^2) has
+// relative error d^3 <= 2^-72 before its final rounding (within 0.51 ulp).
+// Three float64 operations in place of a division.  Inputs outside
+// [2^-125, 2^125] (whose float32 reciprocal would overflow or lose bits to
+// the subnormal range), infinities and NaN take the division.
+VRC_M64_FN double rcp(float s) {
+  if (!(s >= 0x1p-125f && s <= 0x1p125f)) return 1.0 / (double)s;
+#ifdef __CUDA_ARCH__
+  const float r0f = __frcp_rn(s);
+#else
+  const float r0f = 1.0f / s;
+#endif
+  const double sd = (double)s, r0 = (double)r0f;
+  const double e = fmad(-sd, r0, 1.0);
+  return fmad(r0, fmad(e, e, e), r0);
+}
+
+}  // namespace m64
 }  // namespace vrc

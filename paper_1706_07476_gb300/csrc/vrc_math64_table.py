@@ -1,4 +1,4 @@
-"""Prints kExp2Tab of vrc_expd.h: 2^(j/64) for j = 0..63 as the nearest
+"""Prints kExp2Tab of vrc_math64.h: 2^(j/64) for j = 0..63 as the nearest
 float64 (head) and the nearest float64 to the remainder (tail), from exact
 decimal arithmetic at 80 digits."""
 from decimal import Decimal, getcontext

@@ -7,8 +7,9 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <string.h>
 
-#include "vrc_expd.h"
+#include "vrc_math64.h"
 
 static uint64_t state = 0x9e3779b97f4a7c15ull;
 static double uniform01() {  // xorshift64* (Vigna 2016), 53-bit mantissa
@@ -32,7 +33,7 @@ static long n_checked = 0, n_bad_range = 0;
 // or one float32 ulp either side of it.
 static void check_one(double y, float yf) {
   double ey, em;
-  vrc::expd::exp_expm1(y, yf, &ey, &em);
+  vrc::m64::exp_expm1(y, yf, &ey, &em);
   const bool zero_pair = ey == 0.0 && em == -1.0;
   if (y < -709.5 || (y < -708.3 && zero_pair)) {
     if (!zero_pair && n_bad_range++ < 5) printf("below range y=%.17g: got (%.17g, %.17g)\n", y, ey, em);
@@ -68,12 +69,28 @@ int main() {
     }
   }
   double ey, em;
-  vrc::expd::exp_expm1(0.0, 0.0f, &ey, &em);
+  vrc::m64::exp_expm1(0.0, 0.0f, &ey, &em);
   const bool exact0 = ey == 1.0 && em == 0.0;
-  vrc::expd::exp_expm1(-1e-300, -0.0f, &ey, &em);
+  vrc::m64::exp_expm1(-1e-300, -0.0f, &ey, &em);
   const bool tiny = ey == 1.0 && em == -1e-300;
+  // reciprocal: normal float32 s from 2^-126 to 2^128 on a stride of 997 bit
+  // patterns, against the long-double quotient and the float64 division
+  long n_rcp = 0, rcp_off = 0;
+  double worst_rcp = 0;
+  for (uint32_t b = 0x00800000u; b <= 0x7f7fffffu; b += 997u) {
+    float f;
+    memcpy(&f, &b, sizeof f);
+    const double got = vrc::m64::rcp(f), want = 1.0 / (double)f;
+    const double u = ulps(got, 1.0L / (long double)f);
+    if (u > worst_rcp) worst_rcp = u;
+    rcp_off += got != want;
+    ++n_rcp;
+  }
+  printf("rcp: %ld floats, worst %.3f ulp, %ld differ from the rounded quotient\n", n_rcp, worst_rcp,
+         rcp_off);
   printf("checked %ld: worst exp %.3f ulp at y=%.17g, worst expm1 %.3f ulp at y=%.17g; "
          "below-range failures %ld; exact at 0: %d; tiny: %d\n",
          n_checked, worst_ey, at_ey, worst_em, at_em, n_bad_range, exact0, tiny);
-  return (worst_ey <= 0.6 && worst_em <= 2.0 && n_bad_range == 0 && exact0 && tiny) ? 0 : 1;
+  return (worst_ey <= 0.6 && worst_em <= 2.0 && n_bad_range == 0 && exact0 && tiny &&
+          worst_rcp <= 0.51) ? 0 : 1;
 }
