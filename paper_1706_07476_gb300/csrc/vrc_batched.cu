@@ -2,7 +2,8 @@
 // sections, rays and tally) cast by one persistent kernel.  Work items are
 // chunks of one problem's rays; every block takes the next item from a
 // global counter until the list is exhausted.  The per-ray code is the same
-// cast_one as the single-problem kernel (Sec. 3: lookup, cast, Eq. 4 score).
+// as the single-problem kernel's (Sec. 3: lookup, cast, Eq. 4 score): cast_one,
+// or in the plain form the warp-batched cast_one_plain_warp.
 #include <algorithm>
 
 #include "vrc_device.cuh"
@@ -14,8 +15,9 @@ namespace {
 inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
 struct BatchSmem {
-  size_t hash, edges, sig, inv, total;
+  size_t hash, edges, sig, inv, queue, total;
 };
+
 
 BatchSmem batch_smem(int form, const BatchShape &sh, int block) {
   BatchSmem L;
@@ -33,12 +35,14 @@ BatchSmem batch_smem(int form, const BatchShape &sh, int block) {
     L.inv = off + sizeof(float);
     off = align16(off + 2 * sizeof(float) * (size_t)sh.max_mat * block);
   }
+  L.queue = off;
+  if (form == kFormPlain) off = align16(off + kWarpQueueBytes * (size_t)(block / 32));
   L.total = off;
   return L;
 }
 
 template <int FORM>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, FORM == kFormPlain ? 2 : 4)
     k_cast_batched(const CastArgs *__restrict__ probs, const BatchItem *__restrict__ items, int n_items,
                    unsigned int *queue, BatchSmem L) {
   typedef typename Attenuation<FORM>::inv_t inv_t;
@@ -72,8 +76,16 @@ __global__ void __launch_bounds__(256, 4)
     const double *edges = A.edges ? edges_s : nullptr;
     RayCounts cnt;
     const int64_t end = item.start + item.count;
-    for (int64_t r = item.start + threadIdx.x; r < end; r += blockDim.x)
-      cast_one<FORM>(A, r, hash_s, edges, sig_s, inv_s, stride, cnt);
+    if constexpr (FORM == kFormPlain) {  // warp-collective walk: warp-uniform trip count
+      const WarpQueue Q = warp_queue(smem + L.queue);
+      const int lane = threadIdx.x & 31;
+      for (int64_t base = item.start + (threadIdx.x & ~31); base < end; base += blockDim.x)
+        cast_one_plain_warp<false, TallyMaker, false>(A, base + lane, base + lane < end, hash_s, edges,
+                                                      sig_s, inv_s, stride, Q, cnt);
+    } else {
+      for (int64_t r = item.start + threadIdx.x; r < end; r += blockDim.x)
+        cast_one<FORM>(A, r, hash_s, edges, sig_s, inv_s, stride, cnt);
+    }
     flush_counts(cnt, A.counters, A.status);
     __syncthreads();  // s_item, A and the staged tables are reused next pass
   }

@@ -15,9 +15,6 @@ struct SmemLayout {
   size_t hash, edges, sig, inv, queue, total;
 };
 
-// Bytes of one warp's queue for the warp-batched plain walk: (double2 io,
-// int cell) per slot, then 32 ints.
-constexpr size_t kWarpQueueBytes = 32 * kPlainBatch * (sizeof(double2) + sizeof(int32_t)) + 32 * sizeof(int32_t);
 
 SmemLayout smem_layout(int form, const CastArgs &a, int block) {
   SmemLayout L;
@@ -66,15 +63,12 @@ __global__ void __launch_bounds__(256, FORM == kFormPlain ? 2 : 4) k_cast(CastAr
   RayCounts cnt;
   if constexpr (FORM == kFormPlain) {
     // warp-uniform trip count: the batched walk is warp-collective
-    unsigned char *qb = smem + L.queue + kWarpQueueBytes * (threadIdx.x / 32);
-    const WarpQueue Q = {reinterpret_cast<double2 *>(qb),
-                         reinterpret_cast<int32_t *>(qb + 32 * kPlainBatch * sizeof(double2)),
-                         reinterpret_cast<int32_t *>(qb + 32 * kPlainBatch * (sizeof(double2) + sizeof(int32_t)))};
+    const WarpQueue Q = warp_queue(smem + L.queue);
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < a.rays.n;
          base += (int64_t)gridDim.x * blockDim.x)
-      cast_one_plain_warp<SURR, Maker, RECT>(a, base + lane, base + lane < a.rays.n, hash_s, edges, sig_s,
-                                       inv_s, stride, Q, cnt);
+      cast_one_plain_warp<SURR, Maker, RECT>(a, base + lane, base + lane < a.rays.n, hash_s, edges,
+                                             sig_s, inv_s, stride, Q, cnt);
   } else {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.rays.n;
          r += (int64_t)gridDim.x * blockDim.x)

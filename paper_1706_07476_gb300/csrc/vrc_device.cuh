@@ -711,6 +711,19 @@ struct WarpQueue {
   int32_t *pre;
 };
 
+// Shared-memory bytes of one warp's queue (16-byte multiple).
+constexpr size_t kWarpQueueBytes =
+    32 * kPlainBatch * (sizeof(double2) + sizeof(int32_t)) + 32 * sizeof(int32_t);
+
+// The calling warp's queue in a block's queue area (kWarpQueueBytes per warp,
+// 16-byte aligned).
+__device__ __forceinline__ WarpQueue warp_queue(unsigned char *area) {
+  unsigned char *q = area + kWarpQueueBytes * (threadIdx.x / 32);
+  return {reinterpret_cast<double2 *>(q),
+          reinterpret_cast<int32_t *>(q + 32 * kPlainBatch * sizeof(double2)),
+          reinterpret_cast<int32_t *>(q + 32 * kPlainBatch * (sizeof(double2) + sizeof(int32_t)))};
+}
+
 template <typename Walk, typename Sink>
 __device__ __forceinline__ uint32_t cast_ray_plain_warp(const MeshDev &M, bool active, float px,
                                                         float py, float pz, float u, float v, float w,
