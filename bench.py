@@ -181,7 +181,7 @@ def profiled_field(kernel_tag: str, workload_tag: str, field: str):
     except OSError:
         return None
     h = hashlib.sha256()
-    for f in ("vrc_device.cuh", "vrc_cast.cu"):
+    for f in ("vrc_device.cuh", "vrc_math64.h", "vrc_cast.cu"):
         h.update(open(os.path.join(ROOT, "paper_1706_07476_gb300", "csrc", f), "rb").read())
     fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("source_sha256:", field + ":")))
     if fields.get("source_sha256", "").strip() != h.hexdigest():

@@ -703,17 +703,16 @@ __device__ __forceinline__ uint32_t cast_ray_rect(const MeshDev &M, float px, fl
 constexpr int kPlainBatch = 8;
 
 // A warp's queue: io[32 kPlainBatch] holds (sigma, length, 1/sigma) and then
-// (e^-x, path term) per segment, lane-major; cell[32 kPlainBatch]; pre[32]
-// holds each lane's first index in the compacted order.
+// (e^-x, path term) per segment, lane-major; cell[32 kPlainBatch]; slot[32
+// kPlainBatch] lists the io slots of the round's segments in compacted order.
 struct WarpQueue {
   double2 *io;
   int32_t *cell;
-  int32_t *pre;
+  int32_t *slot;
 };
 
 // Shared-memory bytes of one warp's queue (16-byte multiple).
-constexpr size_t kWarpQueueBytes =
-    32 * kPlainBatch * (sizeof(double2) + sizeof(int32_t)) + 32 * sizeof(int32_t);
+constexpr size_t kWarpQueueBytes = 32 * kPlainBatch * (sizeof(double2) + 2 * sizeof(int32_t));
 
 // The calling warp's queue in a block's queue area (kWarpQueueBytes per warp,
 // 16-byte aligned).
@@ -722,6 +721,18 @@ __device__ __forceinline__ WarpQueue warp_queue(unsigned char *area) {
   return {reinterpret_cast<double2 *>(q),
           reinterpret_cast<int32_t *>(q + 32 * kPlainBatch * sizeof(double2)),
           reinterpret_cast<int32_t *>(q + 32 * kPlainBatch * (sizeof(double2) + sizeof(int32_t)))};
+}
+
+// One queued segment's (e^-x, path term) from its (sigma, length, 1/sigma):
+// the float64 arithmetic of Attenuation<kFormPlain>::score.
+__device__ __forceinline__ double2 plain_terms(double2 in) {
+  const float sig = __int_as_float(__double2loint(in.x));
+  const float l = __int_as_float(__double2hiint(in.x));
+  const double ld = f2d_bits(l);
+  const double x = f2d_bits(sig) * ld;  // exact: a float product fits a double
+  double factor, em;
+  m64::exp_expm1(-x, -(sig * l), &factor, &em);
+  return make_double2(factor, sig > 0.f ? -em * in.y : ld);
 }
 
 template <typename Walk, typename Sink>
@@ -775,22 +786,11 @@ __device__ __forceinline__ uint32_t cast_ray_plain_warp(const MeshDev &M, bool a
       if (lane >= o) incl += t;
     }
     const int total = __shfl_sync(kAll, incl, 31);
-    Q.pre[lane] = incl - nq;
+    for (int j = 0; j < nq; ++j) Q.slot[incl - nq + j] = lane * kPlainBatch + j;
     __syncwarp(kAll);
     for (int gi = lane; gi < total; gi += 32) {
-      int o = 0;  // owner: the last lane whose first index is <= gi
-#pragma unroll
-      for (int b = 16; b > 0; b >>= 1)
-        if (Q.pre[o + b] <= gi) o += b;
-      const int slot = o * kPlainBatch + (gi - Q.pre[o]);
-      const double2 in = Q.io[slot];
-      const float sig = __int_as_float(__double2loint(in.x));
-      const float l = __int_as_float(__double2hiint(in.x));
-      const double ld = f2d_bits(l);
-      const double x = f2d_bits(sig) * ld;  // exact: a float product fits a double
-      double factor, em;
-      m64::exp_expm1(-x, -(sig * l), &factor, &em);
-      Q.io[slot] = make_double2(factor, sig > 0.f ? -em * in.y : ld);
+      const int slot = Q.slot[gi];
+      Q.io[slot] = plain_terms(Q.io[slot]);
     }
     __syncwarp(kAll);
     // 3. this lane's scores, in walk order
