@@ -172,10 +172,11 @@ int vrc_load_xs(vrc_ctx *c, int32_t material, const double *E_eV, const double *
  * context-owned scratch (36 B per ray plus a small table); the tally is the
  * same up to float64 summation order.
  * Host arrays (on_device == 0) are copied to the device before the call
- * returns.  A host batch of more than 2^23 rays is uploaded in chunks (2^21
- * rays, then 2^23) on a context-owned copy stream, each chunk sorted and cast
- * on cuda_stream while the next one uploads (two 256 MiB staging slots);
- * pinned host arrays make these copies asynchronous.  Rays with a non-finite field, E <= 0 or a zero direction score
+ * returns.  A host batch of more than 2^22 rays is uploaded in chunks (2^21
+ * rays, then up to 2^24) on a context-owned copy stream, each chunk sorted
+ * and cast on cuda_stream while the next one uploads (two 512 MiB staging
+ * slots); pinned host arrays make these copies asynchronous.  Rays with a
+ * non-finite field, E <= 0 or a zero direction score
  * nothing and are reported by the next vrc_sync / vrc_read_tally as
  * VRC_ERR_NONFINITE.  n == 0 is a no-op.
  * Errors: VRC_ERR_ARG, VRC_ERR_STATE (a material used by the mesh has no

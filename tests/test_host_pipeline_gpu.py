@@ -1,8 +1,9 @@
-"""Host ray batches larger than one upload chunk (2^23 rays) take the
-pipelined path of vrc_cast_rays (chunks of 2^21, then 2^23 rays): chunk i+1
-uploads while chunk i is sorted and cast.  Its tally must equal the device-array cast of the same rays up to
-float64 summation order, with the same segment count, also when the call is
-repeated (the staging slots are reused across calls)."""
+"""Host ray batches of more than 2^22 rays take the pipelined path of
+vrc_cast_rays (chunks of 2^21, then up to 2^24 rays): chunk i+1 uploads
+while chunk i is sorted and cast.  Its tally must equal the device-array
+cast of the same rays up to float64 summation order, with the same segment
+count, also when the call is repeated (the staging slots are reused across
+calls)."""
 from __future__ import annotations
 
 import numpy as np
@@ -17,7 +18,7 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("form", [1, 0], ids=["fp32", "plain"])
 def test_pipelined_host_cast_equals_device_cast(vrc, form):
     import torch
-    n = (1 << 23) + (1 << 21) + 12345  # three chunks (2^21, 2^23, ragged), both slots used
+    n = (1 << 24) + (1 << 21) + 12345  # three chunks (2^21, 2^24, ragged), both slots used
     prob = W.slab_room(seed=12, n=32, n_rays=n, n_points=300, n_resonances=6, n_groups=3)
     pinned = {k: torch.from_numpy(v).pin_memory() for k, v in prob.rays.items()}
     dev = {k: torch.from_numpy(v).cuda() for k, v in prob.rays.items()}

@@ -315,3 +315,34 @@ def test_sort_with_rejected_and_out_of_group_rays(vrc, torch_cuda):
         assert stats["rejected"] == 50 and stats["rays"] == n
         assert stats["segments"] == st["segments"]
         assert_parity(want, got)
+
+
+def test_plain_form_keeps_float64_range_deep_in_attenuation(vrc, torch_cuda):
+    """Rays along +x through 200 cells of flat Sigma = 2.5 /cm, weights up to
+    3e38: cell i's Eq. 4 score is wt e^{-Sigma (i - x0)} (1 - e^{-Sigma})/Sigma
+    down to optical depth 500 (2e-179 for the largest weight), far past the
+    float32 underflow at depth 104.  The plain form must hold every cell to
+    the closed form at 1e-11 (about 2 ulp per factor over 200 factors); the
+    ray count (37) leaves a partial warp."""
+    n_cells, sig = 200, 2.5
+    mat = np.zeros((1, 1, n_cells), np.uint8)
+    mesh = W.Mesh(n_cells, 1, 1, 0.0, 0.0, 0.0, 1.0, 1.0, 1.0, mat)
+    table = (np.array([1e-5, 2e7]), np.array([sig, sig]))
+    n = 37
+    x0 = np.float32(0.25)
+    wt = (np.float32(3e38) / np.float32(2.0) ** np.arange(n, dtype=np.float32)).astype(np.float32)
+    f = lambda v: np.full(n, v, np.float32)  # noqa: E731
+    rays = W.make_rays(f(x0), f(0.5), f(0.5), f(1.0), f(0.0), f(0.0), f(1.0e3), wt)
+    prob = W.Problem("deep", mesh, [table], None, rays)
+    got, rc, stats = run_gpu(vrc, torch_cuda, prob, FORMS["plain"])
+    assert rc == vrc.VRC_OK and stats["segments"] == n * n_cells
+    tau_in = sig * (np.arange(n_cells) - float(x0))
+    tau_in[0] = 0.0
+    length = np.ones(n_cells)
+    length[0] = 1.0 - float(x0)
+    per_unit = np.exp(-tau_in) * -np.expm1(-sig * length) / sig
+    want = per_unit * wt.astype(np.float64).sum()
+    assert want[-1] > 1e-190
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=0)
+    fp32, _, _ = run_gpu(vrc, torch_cuda, prob, FORMS["fp32"])
+    assert not fp32[60:].any()  # the float32 form underflows past depth ~104
