@@ -280,9 +280,10 @@ int vrc_detector_flux(vrc_ctx *c, const vrc_rays *r, const double *det_xyz, int3
 #define VRC_MOMENTS_BATCH 1
 #define VRC_MOMENTS_HISTORY 2
 
-/* Allocates (mode BATCH or HISTORY) or frees (OFF) the two float64 moment
- * arrays (tally size each) and zeroes them and the sample count.  Waits for
- * the context's stream.  VRC_ERR_ARG for another mode. */
+/* Allocates (mode BATCH or HISTORY) or frees (OFF) the moment array, one
+ * float64 (S1, S2) pair per tally entry (twice the tally's size), and zeroes
+ * it and the sample count.  Waits for the context's stream.  VRC_ERR_ARG for
+ * another mode. */
 int vrc_moments_enable(vrc_ctx *c, int32_t mode);
 
 /* S1 += tally, S2 += tally^2, tally = 0, sample count + 1 (stream-ordered).

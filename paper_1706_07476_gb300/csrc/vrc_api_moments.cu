@@ -19,19 +19,16 @@ int vrc_moments_enable(vrc_ctx *c, int32_t mode) {
   c->batches = 0;
   c->moment_mode = mode;
   if (mode == VRC_MOMENTS_OFF) {
-    c->momS1.release();
-    c->momS2.release();
+    c->mom.release();
     c->histTab.release();
     c->histBits.release();
     c->histCap = 0;
     c->moments = false;
     return VRC_OK;
   }
-  const size_t bytes = sizeof(double) * (size_t)(c->ncells * c->n_groups);
-  VRC_CUDA(c->momS1.ensure(bytes), "allocating tally moments");
-  VRC_CUDA(c->momS2.ensure(bytes), "allocating tally moments");
-  VRC_CUDA(cudaMemsetAsync(c->momS1.p, 0, bytes, c->stream), "zeroing tally moments");
-  VRC_CUDA(cudaMemsetAsync(c->momS2.p, 0, bytes, c->stream), "zeroing tally moments");
+  const size_t bytes = sizeof(double2) * (size_t)(c->ncells * c->n_groups);
+  VRC_CUDA(c->mom.ensure(bytes), "allocating tally moments");
+  VRC_CUDA(cudaMemsetAsync(c->mom.p, 0, bytes, c->stream), "zeroing tally moments");
   c->moments = true;
   return VRC_OK;
 }
@@ -42,8 +39,7 @@ int vrc_moments_fold(vrc_ctx *c, void *cuda_stream) {
   if (c->moment_mode != VRC_MOMENTS_BATCH) return fail(VRC_ERR_STATE, "moments are per history, not per batch");
   DeviceGuard g(c->device);
   cudaStream_t s = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : c->stream;
-  VRC_CUDA(launch_fold_moments(c->d_tally, static_cast<double *>(c->momS1.p),
-                               static_cast<double *>(c->momS2.p), c->ncells * c->n_groups, s),
+  VRC_CUDA(launch_fold_moments(c->d_tally, static_cast<double2 *>(c->mom.p), c->ncells * c->n_groups, s),
            "launching the moment fold");
   c->batches += 1;
   return VRC_OK;
@@ -141,8 +137,7 @@ int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, i
   }
   const int grid = (int)std::min<int64_t>((rp.n + block - 1) / block, (int64_t)c->num_sms * bps);
   VRC_CUDA(launch_cast_hist(form, a, grid, block, s), "launching the per-history cast");
-  VRC_CUDA(launch_hist_drain(a.htab, static_cast<double *>(c->momS1.p), static_cast<double *>(c->momS2.p),
-                             c->num_sms, s),
+  VRC_CUDA(launch_hist_drain(a.htab, static_cast<double2 *>(c->mom.p), c->num_sms, s),
            "launching the per-history fold");
   c->batches += n_histories;
   return VRC_OK;
@@ -157,24 +152,23 @@ int vrc_moments_read(vrc_ctx *c, double *total, double *sigma, int64_t n, int64_
   DeviceGuard g(c->device);
   int rc = sync_streams(c, cuda_stream);
   if (rc) return rc;
-  VRC_CUDA(cudaMemcpy(total, c->momS1.p, sizeof(double) * N, cudaMemcpyDeviceToHost), "reading S1");
-  if (sigma) {
-    if (c->batches < 2) {
-      std::memset(sigma, 0, sizeof(double) * N);
-    } else {
-      const int64_t chunk = std::min<int64_t>(N, (int64_t)8 << 20);
-      VRC_CUDA(c->scratch.ensure(sizeof(double) * chunk), "allocating moment staging");
-      for (int64_t off = 0; off < N; off += chunk) {
-        const int64_t m = std::min(chunk, N - off);
-        VRC_CUDA(launch_moment_sigma(static_cast<double *>(c->momS1.p) + off,
-                                     static_cast<double *>(c->momS2.p) + off,
-                                     static_cast<double *>(c->scratch.p), m, (double)c->batches, c->stream),
-                 "launching the moment finalize");
-        VRC_CUDA(cudaMemcpyAsync(sigma + off, c->scratch.p, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream),
-                 "reading sigma");
-        VRC_CUDA(cudaStreamSynchronize(c->stream), "reading sigma");
-      }
-    }
+  // S1 (and sigma) by chunks of 8 Mi bins through device staging
+  const bool want_sigma = sigma && c->batches >= 2;
+  if (sigma && !want_sigma) std::memset(sigma, 0, sizeof(double) * N);
+  const int64_t chunk = std::min<int64_t>(N, (int64_t)8 << 20);
+  VRC_CUDA(c->scratch.ensure(2 * sizeof(double) * chunk), "allocating moment staging");
+  double *st_total = static_cast<double *>(c->scratch.p), *st_sigma = st_total + chunk;
+  for (int64_t off = 0; off < N; off += chunk) {
+    const int64_t m = std::min(chunk, N - off);
+    VRC_CUDA(launch_moment_read(static_cast<const double2 *>(c->mom.p) + off, st_total,
+                                want_sigma ? st_sigma : nullptr, m, (double)c->batches, c->stream),
+             "launching the moment read");
+    VRC_CUDA(cudaMemcpyAsync(total + off, st_total, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream),
+             "reading S1");
+    if (want_sigma)
+      VRC_CUDA(cudaMemcpyAsync(sigma + off, st_sigma, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream),
+               "reading sigma");
+    VRC_CUDA(cudaStreamSynchronize(c->stream), "reading moments");
   }
   if (batches) *batches = c->batches;
   unsigned st = 0;

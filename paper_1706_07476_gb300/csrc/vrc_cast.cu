@@ -84,47 +84,7 @@ __global__ void k_scale_copy(const double *__restrict__ src, double *__restrict_
     dst[i] = src[i] * scale;
 }
 
-// Batch moments: S1 += t, S2 += t^2, t = 0.
-__global__ void k_fold_moments(double *__restrict__ t, double *__restrict__ s1, double *__restrict__ s2,
-                               int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = t[i];
-    s1[i] += v;
-    s2[i] = fma(v, v, s2[i]);
-    t[i] = 0.0;
-  }
-}
-
-// sigma = sqrt(B/(B-1) (S2 - S1^2/B)), clamped at 0 against rounding.
-__global__ void k_moment_sigma(const double *__restrict__ s1, const double *__restrict__ s2,
-                               double *__restrict__ sigma, int64_t n, double B) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double a = s1[i];
-    const double var = (s2[i] - a * a / B) * (B / (B - 1.0));
-    sigma[i] = var > 0.0 ? sqrt(var) : 0.0;
-  }
-}
-
 }  // namespace
-
-cudaError_t launch_fold_moments(double *tally, double *s1, double *s2, int64_t n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
-  k_fold_moments<<<grid, 256, 0, s>>>(tally, s1, s2, n);
-  note_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_moment_sigma(const double *s1, const double *s2, double *sigma, int64_t n, double B,
-                                cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
-  k_moment_sigma<<<grid, 256, 0, s>>>(s1, s2, sigma, n, B);
-  note_launches(1);
-  return cudaGetLastError();
-}
 
 size_t cast_smem_bytes(int form, const CastArgs &a, int block) {
   return smem_layout(form, a, block).total;

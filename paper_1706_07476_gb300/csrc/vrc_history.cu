@@ -1,7 +1,8 @@
-// Per-history tally moments: the segment bound that sizes the history table
-// and the drain that turns the table's per-(history, cell) sums x into
-// S1 += x and S2 += x^2 (the sums behind the tally's standard deviation in
-// Eqs. 5 and 8).
+// Tally moments (the sums behind the tally's standard deviation in Eqs. 5
+// and 8), kept as (S1, S2) pairs per (group, cell): the batch fold, the read
+// (S1 and sigma), and for per-history moments the segment bound that sizes
+// the history table and the drain that turns the table's per-(history,
+// cell) sums x into S1 += x, S2 += x^2.
 #include <algorithm>
 #include <math.h>
 
@@ -83,10 +84,12 @@ __global__ void k_segment_bound(BoundGeom G, RayPtrs R, unsigned long long *boun
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(bound, acc);
 }
 
-// Every claimed slot (key + 1, x), found from the bitmap: S1[bin] += x,
-// S2[bin] += x^2, slot = 0, bitmap word = 0.
+// Every claimed slot (key + 1, x), found from the bitmap: mom[bin] += (x,
+// x^2), slot = 0, bitmap word = 0.  S1 and S2 of a bin share a 16-byte pair,
+// so the two reductions of a slot touch one 32-byte sector: one DRAM
+// read-modify-write where separate S1 and S2 arrays took two.
 __global__ void k_hist_drain(ulonglong2 *e, unsigned int *bits, unsigned long long words,
-                             double *__restrict__ s1, double *__restrict__ s2) {
+                             double2 *__restrict__ mom) {
   for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < words;
        j += (unsigned long long)gridDim.x * blockDim.x) {
     unsigned w = bits[j];
@@ -99,14 +102,57 @@ __global__ void k_hist_drain(ulonglong2 *e, unsigned int *bits, unsigned long lo
       const ulonglong2 v = *slot;
       const unsigned bin = (unsigned)((v.x - 1ull) & 0xffffffffull);
       const double x = __longlong_as_double((long long)v.y);
-      atomicAdd(s1 + bin, x);
-      atomicAdd(s2 + bin, x * x);
+      atomicAdd(&mom[bin].x, x);
+      atomicAdd(&mom[bin].y, x * x);
       *slot = make_ulonglong2(0ull, 0ull);
     }
   }
 }
 
+// Batch moments: mom += (t, t^2), t = 0.
+__global__ void k_fold_moments(double *__restrict__ t, double2 *__restrict__ mom, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = t[i];
+    const double2 m = mom[i];
+    mom[i] = make_double2(m.x + v, fma(v, v, m.y));
+    t[i] = 0.0;
+  }
+}
+
+// total = S1; sigma = sqrt(B/(B-1) (S2 - S1^2/B)), clamped at 0 against
+// rounding (Eqs. 5 and 8 take the standard deviation of the tally).
+__global__ void k_moment_read(const double2 *__restrict__ mom, double *__restrict__ total,
+                              double *__restrict__ sigma, int64_t n, double B) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 m = mom[i];
+    total[i] = m.x;
+    if (sigma) {
+      const double var = (m.y - m.x * m.x / B) * (B / (B - 1.0));
+      sigma[i] = var > 0.0 ? sqrt(var) : 0.0;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_fold_moments(double *tally, double2 *mom, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  k_fold_moments<<<grid, 256, 0, s>>>(tally, mom, n);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moment_read(const double2 *mom, double *total, double *sigma, int64_t n, double B,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  k_moment_read<<<grid, 256, 0, s>>>(mom, total, sigma, n, B);
+  note_launches(1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_segment_bound(const BoundGeom &g, const RayPtrs &rays, unsigned long long *bound,
                                  int num_sms, cudaStream_t s) {
@@ -118,11 +164,11 @@ cudaError_t launch_segment_bound(const BoundGeom &g, const RayPtrs &rays, unsign
   return cudaGetLastError();
 }
 
-cudaError_t launch_hist_drain(const HistTable &t, double *s1, double *s2, int num_sms, cudaStream_t s) {
+cudaError_t launch_hist_drain(const HistTable &t, double2 *mom, int num_sms, cudaStream_t s) {
   const unsigned long long words = (t.mask + 1ull) / 32ull;
   const int block = 256;
   const int grid = (int)std::min<unsigned long long>((words + block - 1) / block, (unsigned long long)num_sms * 8);
-  k_hist_drain<<<grid, block, 0, s>>>(reinterpret_cast<ulonglong2 *>(t.e), t.bits, words, s1, s2);
+  k_hist_drain<<<grid, block, 0, s>>>(reinterpret_cast<ulonglong2 *>(t.e), t.bits, words, mom);
   note_launches(1);
   return cudaGetLastError();
 }

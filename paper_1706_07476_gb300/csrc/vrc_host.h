@@ -133,7 +133,7 @@ struct vrc_ctx {
   uint32_t mlp_mask = 0;          // outputs the surrogate models (non-void materials)
   double mlp_lo = 0, mlp_hi = 0;  // energy range of the tables
   DevBuf mlpParams, mlpFlags, sigBuf;
-  DevBuf momS1, momS2;  // moments of the tally: sums of samples and of their squares
+  DevBuf mom;  // moments of the tally: (S1, S2) per (group, cell), sums of samples and of their squares
   DevBuf detPos, detOut;  // next-event detectors and their flux
   bool moments = false;
   int moment_mode = VRC_MOMENTS_OFF;
@@ -195,8 +195,7 @@ struct vrc_ctx {
     mlpParams.release();
     mlpFlags.release();
     sigBuf.release();
-    momS1.release();
-    momS2.release();
+    mom.release();
     histTab.release();
     histIds.release();
     histSorted.release();

@@ -123,10 +123,13 @@ cudaError_t launch_scale_copy(const double *src, double *dst, int64_t n, double 
 cudaError_t launch_per_volume_rect(const double *src, double *dst, int64_t n, int64_t first, int32_t nx,
                                    int32_t ny, int64_t ncells, const double *wx, const double *wy,
                                    const double *wz, cudaStream_t s);
-cudaError_t launch_fold_moments(double *tally, double *s1, double *s2, int64_t n, cudaStream_t s);
-// Per-history moments (vrc_history.cu and vrc_cast.cu): an upper bound of
-// the segments of a ray batch (added to *bound), the cast that scores into
-// the history table, and the drain S1 += x, S2 += x^2 that also empties it.
+// Tally moments (vrc_history.cu): mom[bin] = (S1, S2), the sums of the
+// samples and of their squares per (group, cell).  Batch moments: the fold
+// mom += (t, t^2), t = 0.  Per-history moments: an upper bound of the
+// segments of a ray batch (added to *bound), the cast that scores into the
+// history table (vrc_cast.cu), and the drain mom[bin] += (x, x^2) that also
+// empties it.
+cudaError_t launch_fold_moments(double *tally, double2 *mom, int64_t n, cudaStream_t s);
 struct BoundGeom {
   double lo[3], h[3];
   int32_t n[3];
@@ -136,9 +139,9 @@ cudaError_t launch_segment_bound(const BoundGeom &g, const RayPtrs &rays, unsign
                                  int num_sms, cudaStream_t s);
 cudaError_t launch_cast_hist(int form, const CastArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t cast_hist_occupancy(int form, const CastArgs &a, int block, int *blocks_per_sm);
-cudaError_t launch_hist_drain(const HistTable &t, double *s1, double *s2, int num_sms, cudaStream_t s);
-
-cudaError_t launch_moment_sigma(const double *s1, const double *s2, double *sigma, int64_t n, double B,
-                                cudaStream_t s);
+cudaError_t launch_hist_drain(const HistTable &t, double2 *mom, int num_sms, cudaStream_t s);
+// total[i] = S1; sigma[i] = sqrt(B/(B-1) (S2 - S1^2/B)) if sigma is not null.
+cudaError_t launch_moment_read(const double2 *mom, double *total, double *sigma, int64_t n, double B,
+                               cudaStream_t s);
 
 }  // namespace vrc
