@@ -192,8 +192,10 @@ struct Attenuation;
 // float32 product Sigma l.  A void cell (Sigma = 0) has x = 0, factor exactly
 // 1 and path term l.  The float32 inputs are widened and W is tested for zero
 // with integer operations, which leaves the FP64 pipe to the 18 float64
-// arithmetic operations of a segment.  score() returns the float64
-// contribution.
+// arithmetic operations of a segment.  A segment's (e^-x, path term) needs
+// no ray state (terms); the score and the carry W *= e^-x do (apply), so the
+// warp-batched walk can compute the first for any lane's segment.  score()
+// returns the float64 contribution.
 template <>
 struct Attenuation<kFormPlain> {
   typedef double inv_t;
@@ -201,15 +203,24 @@ struct Attenuation<kFormPlain> {
   double T;  // wt exp(-tau) at the entry of the current cell (never -0)
   __device__ __forceinline__ explicit Attenuation(float w) : T(f2d_bits(w)) {}
   __device__ __forceinline__ bool dead() const { return __double_as_longlong(T) == 0; }
-  __device__ __forceinline__ double score(float sig, double inv, float l) {
-    if (dead()) return 0.0;
+  // (e^-x, path term): path term = -(e^-x - 1)/Sigma, or l in void
+  __device__ __forceinline__ static double2 terms(float sig, double inv, float l) {
     const double ld = f2d_bits(l);
     const double x = f2d_bits(sig) * ld;  // exact: a float product fits a double
     double factor, em;
     m64::exp_expm1(-x, -(sig * l), &factor, &em);
-    const double s = T * (sig > 0.f ? -em * inv : ld);
-    T *= factor;
+    return make_double2(factor, sig > 0.f ? -em * inv : ld);
+  }
+  // Score W * path term, then W *= e^-x (W = 0: score 0, nothing changes).
+  __device__ __forceinline__ double apply(double2 fp) {
+    if (dead()) return 0.0;
+    const double s = T * fp.y;
+    T *= fp.x;
     return s;
+  }
+  __device__ __forceinline__ double score(float sig, double inv, float l) {
+    if (dead()) return 0.0;
+    return apply(terms(sig, inv, l));
   }
   __device__ __forceinline__ static double to_double(double s) { return s; }
 };
@@ -723,16 +734,10 @@ __device__ __forceinline__ WarpQueue warp_queue(unsigned char *area) {
           reinterpret_cast<int32_t *>(q + 32 * kPlainBatch * (sizeof(double2) + sizeof(int32_t)))};
 }
 
-// One queued segment's (e^-x, path term) from its (sigma, length, 1/sigma):
-// the float64 arithmetic of Attenuation<kFormPlain>::score.
+// One queued segment's (e^-x, path term) from its (sigma, length, 1/sigma).
 __device__ __forceinline__ double2 plain_terms(double2 in) {
-  const float sig = __int_as_float(__double2loint(in.x));
-  const float l = __int_as_float(__double2hiint(in.x));
-  const double ld = f2d_bits(l);
-  const double x = f2d_bits(sig) * ld;  // exact: a float product fits a double
-  double factor, em;
-  m64::exp_expm1(-x, -(sig * l), &factor, &em);
-  return make_double2(factor, sig > 0.f ? -em * in.y : ld);
+  return Attenuation<kFormPlain>::terms(__int_as_float(__double2loint(in.x)),
+                                        in.y, __int_as_float(__double2hiint(in.x)));
 }
 
 template <typename Walk, typename Sink>
@@ -746,7 +751,7 @@ __device__ __forceinline__ uint32_t cast_ray_plain_warp(const MeshDev &M, bool a
   const int lane = threadIdx.x & 31;
   Walk W;
   if (active) active = W.init(M, px, py, pz, u, v, w);
-  double T = f2d_bits(wt);  // wt exp(-tau) at the entry of the next segment to apply
+  Attenuation<kFormPlain> att(wt);  // W at the entry of the next segment to apply
   float tau = 0.f;          // float32 optical depth walked so far
   const float tau_dead = 760.f + (wt > 1.f ? __logf(wt) : 0.f);
   uint32_t nseg = 0;
@@ -755,7 +760,7 @@ __device__ __forceinline__ uint32_t cast_ray_plain_warp(const MeshDev &M, bool a
   for (;;) {
     // 1. walk: queue up to kPlainBatch segments of this lane's ray
     int nq = 0;
-    if (active && stop_zero && __double_as_longlong(T) == 0) active = false;
+    if (active && stop_zero && att.dead()) active = false;
     for (int j = 0; j < kPlainBatch && active; ++j) {
       const typename Walk::Next t = W.next();
       const unsigned nmat = t.leaving ? 0u : __ldg(M.mat + t.ncell);  // prefetch the next cell
@@ -796,12 +801,8 @@ __device__ __forceinline__ uint32_t cast_ray_plain_warp(const MeshDev &M, bool a
     // 3. this lane's scores, in walk order
     for (int j = 0; j < nq; ++j) {
       const int slot = lane * kPlainBatch + j;
-      const double2 fp = Q.io[slot];
-      if (__double_as_longlong(T) != 0) {
-        const double sc = T * fp.y;
-        T *= fp.x;
-        if (sc != 0.0) sink.add(Q.cell[slot], sc);
-      }
+      const double sc = att.apply(Q.io[slot]);
+      if (sc != 0.0) sink.add(Q.cell[slot], sc);
     }
     if (!__any_sync(kAll, active)) break;
   }
