@@ -346,3 +346,17 @@ def test_plain_form_keeps_float64_range_deep_in_attenuation(vrc, torch_cuda):
     np.testing.assert_allclose(got, want, rtol=1e-11, atol=0)
     fp32, _, _ = run_gpu(vrc, torch_cuda, prob, FORMS["fp32"])
     assert not fp32[60:].any()  # the float32 form underflows past depth ~104
+
+
+@pytest.mark.parametrize("block", [32, 96, 224])
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_block_sizes_vs_oracle(vrc, torch_cuda, uniform32, form, block):
+    """Other thread-block shapes of the cast: one warp, and odd warp counts
+    per block (the plain form's per-warp queues are carved from the block's
+    shared memory by warp index)."""
+    prob, want, st = uniform32
+    opts = vrc.vrc_default_options(form=FORMS[form], block=block)
+    got, rc, stats = run_gpu(vrc, torch_cuda, prob, FORMS[form], options=opts)
+    assert rc == vrc.VRC_OK
+    assert stats["segments"] == st["segments"]
+    assert_parity(want, got)
