@@ -812,6 +812,10 @@ def main():
             }
             roof["atomic_roof_segments_per_s"] = red_hbm
             roof["frac_of_atomic_roof"] = R["value"] / world / red_hbm
+            roof["atomic_roof_basis"] = (
+                "one segment per random float64 red on a 2 GiB array (no locality), measured in "
+                "this run; the cast beats it because only segments whose transmitted fraction is "
+                "not yet 0 issue a red, and the ray sort gives those reds L2 locality")
         except Exception as e:  # measurement aid only
             extra["micro"] = {"error": str(e)}
 
