@@ -188,10 +188,10 @@ struct Attenuation;
 // Plain form: the ray's weight times its transmitted fraction, W = wt
 // exp(-tau_in), carried in float64.  The cell's factor e^-x, x = Sigma l, and
 // the path term's e^-x - 1 both come from one float64 range reduction
-// (vrc_math64.h: within 0.52 and 1.9 ulp of the exact values), indexed from the
+// (vrc_math64.h: within 0.51 and 1.8 ulp of the exact values), indexed from the
 // float32 product Sigma l.  A void cell (Sigma = 0) has x = 0, factor exactly
 // 1 and path term l.  The float32 inputs are widened and W is tested for zero
-// with integer operations, which leaves the FP64 pipe to the 18 float64
+// with integer operations, which leaves the FP64 pipe to the 17 float64
 // arithmetic operations of a segment.  A segment's (e^-x, path term) needs
 // no ray state (terms); the score and the carry W *= e^-x do (apply), so the
 // warp-batched walk can compute the first for any lane's segment.  score()

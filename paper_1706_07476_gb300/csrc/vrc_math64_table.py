@@ -1,10 +1,10 @@
-"""Prints kExp2Tab of vrc_math64.h: 2^(j/64) for j = 0..63 as the nearest
+"""Prints kExp2Tab of vrc_math64.h: 2^(j/256) for j = 0..255 as the nearest
 float64 (head) and the nearest float64 to the remainder (tail), from exact
 decimal arithmetic at 80 digits."""
 from decimal import Decimal, getcontext
 
 
-def exp2_table(n=64):
+def exp2_table(n=256):
     getcontext().prec = 80
     ln2 = Decimal(2).ln()
     rows = []

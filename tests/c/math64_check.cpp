@@ -59,13 +59,13 @@ int main() {
   for (int i = 0; i < 2000000; ++i) check(-760.0 * uniform01());       // whole range
   for (int i = 0; i < 1000000; ++i) check(-8.0 * uniform01());         // typical Sigma l
   for (int i = 0; i < 1000000; ++i) check(-pow(10.0, -300.0 + 302.0 * uniform01()));  // tiny to 100
-  // either side of every reduction boundary (y = (n + 1/2) ln2/64) and of
-  // every n ln2/64, down to the end of the range
-  const double c = 0.6931471805599453 / 64;
-  for (int n = 0; n < 65600; ++n) {
-    for (int d = -8; d <= 8; ++d) {
-      check(-(n + 0.5) * c + d * 4e-16 * (1.0 + n * c));
-      check(-n * c + d * 4e-16 * (1.0 + n * c));
+  // either side of every reduction boundary (y = (n + 1/2) ln2/256) and of
+  // every n ln2/256, down to the end of the range
+  const double c = 0.6931471805599453 / 256;
+  for (int n = 0; n < 262400; ++n) {
+    for (int d = -4; d <= 4; ++d) {
+      check(-(n + 0.5) * c + d * 2e-16 * (1.0 + n * c));
+      check(-n * c + d * 2e-16 * (1.0 + n * c));
     }
   }
   double ey, em;
