@@ -170,10 +170,14 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def profiled_field(kernel_tag: str, workload_tag: str, field: str):
+CAST_SOURCES = ("vrc_device.cuh", "vrc_math64.h", "vrc_cast.cu")
+BATCHED_SOURCES = ("vrc_device.cuh", "vrc_math64.h", "vrc_batched.cu", "vrc_sort.cu")
+
+
+def profiled_field(kernel_tag: str, workload_tag: str, field: str, sources=CAST_SOURCES):
     """A number from a committed ncu summary of this kernel on this workload
     (e.g. DRAM bytes per launch), if the summary was taken on the current
-    cast kernel source (matched by the recorded source hash)."""
+    kernel source (matched by the recorded hash of `sources`)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}_{workload_tag}.md")
     try:
@@ -181,7 +185,7 @@ def profiled_field(kernel_tag: str, workload_tag: str, field: str):
     except OSError:
         return None
     h = hashlib.sha256()
-    for f in ("vrc_device.cuh", "vrc_math64.h", "vrc_cast.cu"):
+    for f in sources:
         h.update(open(os.path.join(ROOT, "paper_1706_07476_gb300", "csrc", f), "rb").read())
     fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("source_sha256:", field + ":")))
     if fields.get("source_sha256", "").strip() != h.hexdigest():
@@ -314,7 +318,9 @@ def run_batched(args, rank, world, local):
                    "autotuned_options": best, "tuned_ms": tuned_ms,
                    "l2": "inputs larger than L2 (4.5 GB rays, 2.6 GB tallies); no flush"},
         "roofline": {"bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
-                     "frac": alg / hbm, "traffic": None,
+                     "frac": alg / hbm,
+                     "traffic": profiled_field("k_cast_batched", "batched", "traffic_bytes_per_step",
+                                               BATCHED_SOURCES),
                      "peak_source": f"{src} hbm_gbs", "kernel": "whole step (sort + k_cast_batched)"},
         "clocks": sampler.summary(), "gpu_launches": launches,
         "autotune_sweep": [{"options": o, "ms": ms} for o, ms in table],
