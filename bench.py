@@ -215,9 +215,18 @@ def cpu_baseline(prob, target_s: float, oracle):
         if dt >= 0.5 * target_s or n >= prob.n_rays:
             break
         n = int(min(prob.n_rays, n * min(64.0, 0.9 * target_s / max(dt, 1e-3))))
-    return dict(value=st["segments"] / dt, unit=UNIT, cores=st["threads"], kind="oracle",
-                sample=f"first {n} of the {prob.n_rays} rays of the {prob.name} workload "
-                       f"({st['segments']} segments, {dt:.1f} s)"), tally, n
+    out = dict(value=st["segments"] / dt, unit=UNIT, cores=st["threads"], kind="oracle",
+               sample=f"first {n} of the {prob.n_rays} rays of the {prob.name} workload "
+                      f"({st['segments']} segments, {dt:.1f} s)")
+    # the same oracle on one core, on a sample sized for about 3 s
+    n1 = max(1024, min(n, int(n * 3.0 / max(dt * st["threads"], 1e-3))))
+    t1 = np.zeros(prob.tally_size, np.float64)
+    t0 = time.perf_counter()
+    _, s1 = oracle.cast(prob, nthreads=1, rays=W.take_rays(prob, slice(0, n1)).rays, tally=t1)
+    d1 = time.perf_counter() - t0
+    out["value_one_core"] = s1["segments"] / d1
+    out["sample_one_core"] = f"first {n1} rays ({s1['segments']} segments, {d1:.1f} s)"
+    return out, tally, n
 
 
 # --------------------------------------------------------------------------- reference arm
