@@ -360,3 +360,24 @@ def test_block_sizes_vs_oracle(vrc, torch_cuda, uniform32, form, block):
     assert rc == vrc.VRC_OK
     assert stats["segments"] == st["segments"]
     assert_parity(want, got)
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_weight_extremes_vs_oracle(vrc, torch_cuda, uniform32, form):
+    """Weights are only a factor of Eq. 4: negative weights give the negated
+    tally, zero weights score nothing, and weights from 1e-30 to 1e30 scale
+    their rays' scores, all as in the oracle."""
+    prob, _, st = uniform32
+    n = prob.n_rays
+    rng = np.random.default_rng(31)
+    wt = (10.0 ** rng.uniform(-30, 30, n)).astype(np.float32)
+    wt[rng.random(n) < 0.1] = 0.0
+    wt = -wt
+    rays = dict(prob.rays, wt=wt)
+    p2 = W.Problem("weights", prob.mesh, prob.tables, prob.group_edges, rays)
+    want, st2 = oracle.cast(p2)
+    assert st2["segments"] == st["segments"]
+    got, rc, stats = run_gpu(vrc, torch_cuda, p2, FORMS[form])
+    assert rc == vrc.VRC_OK and stats["segments"] == st["segments"]
+    assert (want <= 0).all() and want.min() < -1e20
+    assert_parity(want, got)
