@@ -273,9 +273,8 @@ struct Attenuation<kFormFp32> {
 // time at 256^3 x 16 groups).
 struct TallySink {
   double *tal;
+  uint64_t policy;  // L2 evict-last access policy, created once per ray
   __device__ __forceinline__ void add(int cell, double v) const {
-    uint64_t policy;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
     asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.f64 [%0], %1, %2;"
                  :: "l"(tal + cell), "d"(v), "l"(policy) : "memory");
   }
@@ -355,7 +354,9 @@ struct HistSink {
 // Sink of ray r in group g for a plain cast and for a per-history cast.
 struct TallyMaker {
   __device__ __forceinline__ static TallySink make(const CastArgs &a, int64_t, int g) {
-    return {a.tally + (int64_t)g * a.mesh.ncells};
+    uint64_t policy;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
+    return {a.tally + (int64_t)g * a.mesh.ncells, policy};
   }
 };
 struct HistMaker {
