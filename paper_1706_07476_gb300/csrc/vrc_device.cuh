@@ -712,7 +712,7 @@ __device__ __forceinline__ uint32_t cast_ray_rect(const MeshDev &M, float px, fl
 // lane without a ray.  Every lane's walk ends within max_steps + 1 steps, so
 // the rounds end.
 // ---------------------------------------------------------------------------
-constexpr int kPlainBatch = 8;
+constexpr int kPlainBatch = 10;
 
 // A warp's queue: io[32 kPlainBatch] holds (sigma, length, 1/sigma) and then
 // (e^-x, path term) per segment, lane-major; cell[32 kPlainBatch]; slot[32
