@@ -703,12 +703,13 @@ __device__ __forceinline__ uint32_t cast_ray_rect(const MeshDev &M, float px, fl
 // computes e^-x and the path term (-(e^-x - 1)/Sigma, or l in void) for all
 // queued segments, 32 at a time, each lane taking any lane's segment; last,
 // each lane applies its own segments in order: score = W * path term, W *=
-// e^-x, tally add.  The result is the unbatched walk's, operation for
-// operation.  A segment is queued only while the ray's float32 optical
-// depth is below 760 + max(0, ln wt): beyond that W = wt e^-tau is exactly
-// 0 in float64 (e^-745.2 is below half the smallest subnormal), so the
-// segment's score is +0; the float32 depth is accurate to far better than
-// the margin.  Warp-collective: all 32 lanes call it, `active` false for a
+// e^-x, tally add.  Each score is Attenuation<kFormPlain>::score's,
+// operation for operation.  A segment is queued only while the ray's
+// float32 optical depth is below 760 + max(0, ln wt): beyond that W = wt
+// e^-tau is below 1e-322 (e^-745.2 is below half the smallest subnormal),
+// so its scores are 0, or below 1e-322 where rounding holds W at the
+// smallest subnormal; they are dropped.  The float32 depth is accurate to
+// far better than the margin.  Warp-collective: all 32 lanes call it, `active` false for a
 // lane without a ray.  Every lane's walk ends within max_steps + 1 steps, so
 // the rounds end.
 // ---------------------------------------------------------------------------
@@ -753,7 +754,7 @@ __device__ __forceinline__ uint32_t cast_ray_plain_warp(const MeshDev &M, bool a
   Walk W;
   if (active) active = W.init(M, px, py, pz, u, v, w);
   Attenuation<kFormPlain> att(wt);  // W at the entry of the next segment to apply
-  float tau = 0.f;          // float32 optical depth walked so far
+  float tau = 0.f;                   // float32 optical depth walked so far
   const float tau_dead = 760.f + (wt > 1.f ? __logf(wt) : 0.f);
   uint32_t nseg = 0;
   const int max_steps = M.n[0] + M.n[1] + M.n[2] + 3;
