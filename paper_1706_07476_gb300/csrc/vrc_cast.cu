@@ -2,6 +2,7 @@
 // lookup, the ray cast and the VRC score of Eq. 4) and the tally finalize
 // kernel.
 #include <algorithm>
+#include <type_traits>
 
 #include "vrc_device.cuh"
 
@@ -42,8 +43,12 @@ SmemLayout smem_layout(int form, const CastArgs &a, int block) {
   return L;
 }
 
+// Blocks per SM: 2 for the plain form (its warp queues and float64 state),
+// 3 for per-history casts (the compare-and-swap inserts need registers), 4
+// for the FP32 tally cast.
 template <int FORM, bool SURR, typename Maker = TallyMaker, bool RECT = false>
-__global__ void __launch_bounds__(256, FORM == kFormPlain ? 2 : 4) k_cast(CastArgs a, SmemLayout L) {
+__global__ void __launch_bounds__(256, FORM == kFormPlain ? 2 : (std::is_same<Maker, HistMaker>::value ? 3 : 4))
+    k_cast(CastArgs a, SmemLayout L) {
   typedef typename Attenuation<FORM>::inv_t inv_t;
   extern __shared__ __align__(16) unsigned char smem[];
   int32_t *hash_s = reinterpret_cast<int32_t *>(smem + L.hash);
