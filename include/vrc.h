@@ -49,7 +49,10 @@ extern "C" {
 /* ---- precision forms -------------------------------------------------- */
 /* PLAIN: the paper's arithmetic (Sec. 3): single-precision cross sections
  * and distances, Eq. 4 evaluated in double precision, float64 tally.
- * Distances are computed with double-float (two float32) arithmetic.
+ * Distances are computed with double-float (two float32) arithmetic; each
+ * segment's e^-x and e^-x - 1 are within 0.51 and 1.8 ulp of the exact
+ * values, and a ray's scores stop once wt e^-tau is below 1e-322 (a
+ * scored contribution is then at most the smallest float64 subnormal).
  * FP32: Eq. 4's exponentials and the optical depth in float32 (optical depth
  * kept as a compensated float32 pair); the tally sums stay float64. */
 #define VRC_FORM_PLAIN 0
