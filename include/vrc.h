@@ -51,8 +51,9 @@ extern "C" {
  * and distances, Eq. 4 evaluated in double precision, float64 tally.
  * Distances are computed with double-float (two float32) arithmetic; each
  * segment's e^-x and e^-x - 1 are within 0.51 and 1.8 ulp of the exact
- * values, and a ray's scores stop once wt e^-tau is below 1e-322 (a
- * scored contribution is then at most the smallest float64 subnormal).
+ * values.  A ray stops scoring once its optical depth passes
+ * 760 + ln(max(wt, 1)), where wt e^-tau is below the float64 range (any
+ * score dropped there is below 1e-322).
  * FP32: Eq. 4's exponentials and the optical depth in float32 (optical depth
  * kept as a compensated float32 pair); the tally sums stay float64. */
 #define VRC_FORM_PLAIN 0
