@@ -42,7 +42,7 @@
 #include <stdint.h>
 
 #ifdef __CUDACC__
-#define VRC_M64_FN __host__ __device__ __forceinline__
+#define VRC_M64_FN __device__ __forceinline__
 #else
 #include <math.h>
 #include <string.h>
