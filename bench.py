@@ -54,6 +54,8 @@ UNIT = "segments/s"
 # Algorithmic bytes: per segment 8 B tally read + 8 B tally write + 1 B material
 # id; per ray 32 B of ray data (x, y, z, u, v, w, E, wt as float32).
 BYTES_PER_SEGMENT = 17
+BYTES_PER_TALLY = 16
+BYTES_PER_MATERIAL = 1
 BYTES_PER_RAY = 32
 
 
@@ -74,6 +76,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity-sample", action="store_true")
     ap.add_argument("--no-micro", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the pin-lattice, batched and surrogate workloads of the default line")
+    ap.add_argument("--config-steps", type=int, default=5, help="timed steps of each extra workload")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target wall time of the CPU-baseline oracle sample")
     return ap.parse_args()
@@ -229,6 +234,66 @@ def cpu_baseline(prob, target_s: float, oracle):
     return out, tally, n
 
 
+def roofline_figures(seg_per_step, live_per_step, rays_per_step, kernel_s, hbm):
+    """Algorithmic HBM bytes per launch over the kernel time, two ways: every
+    segment charged 17 B (tally read and write, material id), and only the
+    segments that add a score charged the tally's 16 B (1 B material id for
+    every walked segment); 32 B per ray in both."""
+    alg = seg_per_step * BYTES_PER_SEGMENT + rays_per_step * BYTES_PER_RAY
+    live = live_per_step * BYTES_PER_TALLY + seg_per_step * BYTES_PER_MATERIAL + rays_per_step * BYTES_PER_RAY
+    return {"achieved_gbs": alg / kernel_s / 1e9, "frac": alg / kernel_s / 1e9 / hbm,
+            "live_achieved_gbs": live / kernel_s / 1e9, "live_frac": live / kernel_s / 1e9 / hbm,
+            "live_fraction_of_segments": live_per_step / max(seg_per_step, 1.0)}
+
+
+def time_cast(vrc, torch, ctx, dev_rays, stream, steps, warmup):
+    """Device-resident casts of one batch: CUDA events on the launching
+    stream around `steps` casts after `warmup`, the library's own kernel
+    timing, and the device counters of the timed casts."""
+    for _ in range(warmup):
+        vrc.vrc_cast_rays(ctx, dev_rays, stream=stream)
+    rc, _ = vrc.vrc_sync(ctx, stream)
+    assert rc == vrc.VRC_OK, rc
+    vrc.vrc_reset_tally(ctx, stream)
+    vrc.vrc_enable_timing(ctx, True)
+    vrc.vrc_get_timing(ctx, stream, reset=True)
+    torch.cuda.synchronize()
+    l0 = vrc.vrc_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        vrc.vrc_cast_rays(ctx, dev_rays, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    launches = vrc.vrc_launch_count() - l0
+    rc, st = vrc.vrc_sync(ctx, stream)
+    tm = vrc.vrc_get_timing(ctx, stream)
+    vrc.vrc_enable_timing(ctx, False)
+    assert rc == vrc.VRC_OK and st["overflow"] == 0, (rc, st)
+    dt = e0.elapsed_time(e1) / 1e3
+    return {"value": st["segments"] / dt, "ms_per_step": 1e3 * dt / steps,
+            "kernel_ms": tm["cast_ms"] / max(tm["cast_launches"], 1),
+            "sort_ms": tm["sort_ms"] / steps, "segments_per_step": st["segments"] / steps,
+            "live_per_step": st["live"] / steps, "launches": launches, "steps": steps}
+
+
+def parity_sample(vrc, ctx, prob, n_sample, stream, oracle):
+    """The first n_sample rays of the workload cast into a fresh tally of the
+    timed context, against the FP64 oracle on the same rays (Eq. 7 relative
+    difference over cells with oracle tally >= 1e-30; segment counts)."""
+    sub = W.take_rays(prob, slice(0, n_sample))
+    want, st = oracle.cast(prob, rays=sub.rays)
+    vrc.vrc_reset_tally(ctx, stream)
+    vrc.vrc_cast_rays(ctx, sub.rays, stream=stream)
+    rc, stats = vrc.vrc_sync(ctx, stream)
+    got, _ = vrc.vrc_read_tally(ctx, stream=stream)
+    sel = want >= 1e-30
+    rel = np.abs(got[sel] - want[sel]) / want[sel]
+    return {"rays": n_sample, "max_rel_err": float(rel.max()), "mean_rel_err": float(rel.mean()),
+            "cells": int(sel.sum()), "segments_equal": bool(stats["segments"] == st["segments"]),
+            "status": rc}
+
+
 # --------------------------------------------------------------------------- reference arm
 
 def run_reference(args, rank, world):
@@ -267,20 +332,22 @@ def run_reference(args, rank, world):
 
 # --------------------------------------------------------------------------- batched form
 
+PINLATTICE = ("pinlattice: 17x17 cylinders (pitch 1.26 cm, radius 0.45 cm) voxelised on a 544x544x64 "
+              "mesh of 0.039375x0.039375x5 cm cells, 4 materials (core, void gap, cladding, moderator; "
+              "20,000-point tables), 2^24 rays (70% starting in the cylinders), 1/E energies, seed 2")
 BATCHED = ("batched1024: 1,024 independent problems, cubic meshes of 1 cm cells with side "
            "log-uniform in 16-128, 2-8 materials each from the 1,000-point table generator, "
            "uniform-random layout, ray counts log-uniform in 1e3-1e6 (1.4e8 rays), one group, "
            "seed 3; one persistent graph-captured launch per step")
 
 
-def run_batched(args, rank, world, local):
+def measure_batched(args, torch, vrc, local, steps, warmup, form, parity_problems=0):
     """The batched form: every step is one launch of the batch plan (all
     problems), timed with CUDA events; the plan's options come from the
-    project's autotuner (sweep outside the timed region, cached per GPU)."""
-    import torch
-    from paper_1706_07476_gb300 import autotune, vrc
-    torch.cuda.set_device(local)
-    form = vrc.VRC_FORM_FP32 if args.forms.split(",")[-1].strip() == "fp32" else vrc.VRC_FORM_PLAIN
+    project's autotuner (sweep outside the timed region, cached per GPU).
+    With parity_problems > 0, that many problems (evenly spaced) are checked
+    cell by cell against the FP64 oracle after one more launch."""
+    from paper_1706_07476_gb300 import autotune
     probs = W.batched_problems(seed=3)
     ctxs = [vrc.context_for(p, vrc.vrc_default_options(form=form, device=local)) for p in probs]
     rays = [{k: torch.from_numpy(p.rays[k]).cuda() for k in W.RAY_FIELDS} for p in probs]
@@ -288,7 +355,7 @@ def run_batched(args, rank, world, local):
                                                   use_cache=not args.retune)
     batch = vrc.vrc_batch_create(ctxs, rays, vrc.vrc_default_batch_options(**best))
     stream = torch.cuda.Stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         vrc.vrc_batch_launch(batch, stream=stream)
     stream.synchronize()
     for c in ctxs:
@@ -300,39 +367,78 @@ def run_batched(args, rank, world, local):
     l0 = vrc.vrc_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         vrc.vrc_batch_launch(batch, stream=stream)
     e1.record(stream)
     e1.synchronize()
     launches = vrc.vrc_launch_count() - l0
     sampler.__exit__(None, None, None)
     elapsed = e0.elapsed_time(e1) / 1e3
-    seg = 0
+    seg = live = 0
     for c in ctxs:
         rc, st = vrc.vrc_sync(c)
         assert rc == vrc.VRC_OK and st["overflow"] == 0, (rc, st)
         seg += st["segments"]
+        live += st["live"]
     n_rays = sum(p.n_rays for p in probs)
-    value = seg / elapsed
     peaks, src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    alg = (seg / args.steps * BYTES_PER_SEGMENT + n_rays * BYTES_PER_RAY) / (elapsed / args.steps) / 1e9
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if form else "f64",
-        "data": "synthetic",
-        "config": {"workload": BATCHED, "rays_per_step": n_rays,
-                   "segments_per_step": seg / args.steps, "form": "fp32" if form else "plain",
-                   "autotuned_options": best, "tuned_ms": tuned_ms,
-                   "l2": "inputs larger than L2 (4.5 GB rays, 2.6 GB tallies); no flush"},
-        "roofline": {"bound": "hbm", "achieved": alg, "peak": hbm, "unit": "GB/s",
-                     "frac": alg / hbm,
+    lf = roofline_figures(seg / steps, live / steps, n_rays, elapsed / steps, hbm)
+    out = {
+        "value": seg / elapsed, "ms_per_step": 1e3 * elapsed / steps, "steps": steps,
+        "segments_per_step": seg / steps, "live_segments_per_step": live / steps,
+        "rays_per_step": n_rays, "form": "fp32" if form else "plain",
+        "autotuned_options": best, "tuned_ms": tuned_ms,
+        "roofline": {"bound": "hbm", "achieved": lf["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                     "frac": lf["frac"], "live_frac": lf["live_frac"],
                      "traffic": profiled_field("k_cast_batched", "batched", "traffic_bytes_per_step",
                                                BATCHED_SOURCES),
                      "peak_source": f"{src} hbm_gbs", "kernel": "whole step (sort + k_cast_batched)"},
         "clocks": sampler.summary(), "gpu_launches": launches,
         "autotune_sweep": [{"options": o, "ms": ms} for o, ms in table],
+    }
+    if parity_problems:
+        import oracle
+        for c in ctxs:
+            vrc.vrc_reset_tally(c)
+        vrc.vrc_batch_launch(batch, stream=stream)
+        stream.synchronize()
+        worst, seg_ok = 0.0, True
+        idx = np.linspace(0, len(probs) - 1, parity_problems).astype(int)
+        for i in idx:
+            want, st = oracle.cast(probs[i])
+            got, rc = vrc.vrc_read_tally(ctxs[i])
+            _, gst = vrc.vrc_sync(ctxs[i])
+            sel = want >= 1e-30
+            worst = max(worst, float((np.abs(got[sel] - want[sel]) / want[sel]).max()))
+            seg_ok = seg_ok and gst["segments"] == st["segments"]
+        out["parity_sample"] = {"problems": len(idx), "max_rel_err": worst, "segments_equal": seg_ok}
+    batch.close()
+    for c in ctxs:
+        c.close()
+    del rays
+    torch.cuda.empty_cache()
+    return out, probs
+
+
+def run_batched(args, rank, world, local):
+    """--workload batched: the batched form's own JSON line."""
+    import torch
+    from paper_1706_07476_gb300 import vrc
+    torch.cuda.set_device(local)
+    form = vrc.VRC_FORM_FP32 if args.forms.split(",")[-1].strip() == "fp32" else vrc.VRC_FORM_PLAIN
+    m, probs = measure_batched(args, torch, vrc, local, args.steps, args.warmup, form)
+    line = {
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if form else "f64",
+        "data": "synthetic",
+        "config": {"workload": BATCHED, "rays_per_step": m["rays_per_step"],
+                   "segments_per_step": m["segments_per_step"], "form": m["form"],
+                   "autotuned_options": m["autotuned_options"], "tuned_ms": m["tuned_ms"],
+                   "l2": "inputs larger than L2 (4.5 GB rays, 2.6 GB tallies); no flush"},
+        "roofline": m["roofline"], "clocks": m["clocks"], "gpu_launches": m["gpu_launches"],
+        "autotune_sweep": m["autotune_sweep"],
     }
     if not args.no_cpu_baseline:
         import oracle
@@ -343,11 +449,31 @@ def run_batched(args, rank, world, local):
         line["cpu_baseline"] = {"value": segs / dt, "unit": UNIT, "cores": oracle.hardware_threads(),
                                 "kind": "oracle",
                                 "sample": f"64 of the 1,024 problems, evenly spaced ({segs} segments, {dt:.1f} s)"}
-    batch.close()
-    for c in ctxs:
-        c.close()
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_pinlattice(args, torch, vrc, local, stream, steps, warmup, oracle=None):
+    """The pin lattice (544 x 544 x 64 cells of 0.039 x 0.039 x 5 cm, 2^24
+    rays, FP32 form, one group): device-resident casts timed like the
+    headline, and a parity sample of 2^20 rays against the FP64 oracle."""
+    prob = W.pin_lattice(seed=2)
+    ctx = vrc.context_for(prob, vrc.vrc_default_options(form=vrc.VRC_FORM_FP32, device=local))
+    dev = {k: torch.from_numpy(v).cuda() for k, v in prob.rays.items()}
+    r = time_cast(vrc, torch, ctx, dev, stream, steps, warmup)
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    lf = roofline_figures(r["segments_per_step"], r["live_per_step"], prob.n_rays, r["kernel_ms"] / 1e3, hbm)
+    out = {"workload": PINLATTICE, "form": "fp32", "rays_per_step": prob.n_rays, **r,
+           "roofline": {"bound": "hbm", "achieved": lf["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                        "frac": lf["frac"], "live_frac": lf["live_frac"], "traffic": None,
+                        "peak_source": f"{src} hbm_gbs", "kernel": "k_cast<fp32>"}}
+    if oracle is not None:
+        out["parity_sample"] = parity_sample(vrc, ctx, prob, 1 << 20, stream, oracle)
+    ctx.close()
+    del dev
+    torch.cuda.empty_cache()
+    return out
 
 
 # --------------------------------------------------------------------------- streaming
@@ -734,7 +860,9 @@ def main():
         alg_bytes = seg_per_step * BYTES_PER_SEGMENT + prob.n_rays * BYTES_PER_RAY
         results[form] = dict(value=total / elapsed, ms_per_step=1e3 * elapsed / args.steps,
                              segments_per_step=seg_per_step, kernel_ms=1e3 * kernel_s,
-                             alg_gbs=alg_bytes / kernel_s / 1e9, launches=n_launch)
+                             alg_gbs=alg_bytes / kernel_s / 1e9, launches=n_launch,
+                             live_segments_per_step=stats["live"] / args.steps,
+                             live_segments_per_s=sum_over_ranks(stats["live"]) / elapsed)
 
     head = forms[-1]
     R = results[head]
@@ -800,6 +928,15 @@ def main():
             "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)",
             "algorithmic_bytes": f"{BYTES_PER_SEGMENT} B/segment + {BYTES_PER_RAY} B/ray",
             "kernel": f"k_cast<{head}>", "kernel_ms": R["kernel_ms"]}
+    # the same roofline with the tally's 16 B charged only to the segments
+    # that add a score (a segment past the point where exp(-tau) is exactly 0
+    # reads its material id and nothing else)
+    lf = roofline_figures(R["segments_per_step"], R["live_segments_per_step"], prob.n_rays,
+                          R["kernel_ms"] / 1e3, hbm)
+    roof["live"] = {"achieved": lf["live_achieved_gbs"], "frac": lf["live_frac"],
+                    "live_segments_per_step": R["live_segments_per_step"],
+                    "live_fraction_of_segments": lf["live_fraction_of_segments"],
+                    "algorithmic_bytes": "16 B per live segment + 1 B per segment + 32 B per ray"}
     # the kernel's binding limit is instruction issue: warp instructions per
     # segment from the committed profile, against 4 schedulers x SMs x clock
     wips = profiled_field(f"k_cast_{head}", args.workload, "warp_instructions_per_segment")
@@ -876,6 +1013,17 @@ def main():
                 line["parity_sample"] = par
     for c in ctxs.values():
         c.close()
+    del dev_rays, pinned
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_configs and args.workload == "slab256":
+        # the other workloads, a few steps each, each with its parity sample
+        import oracle
+        cs, cw = max(1, args.config_steps), max(3, min(args.warmup, 3))
+        configs = {"pinlattice": measure_pinlattice(args, torch, vrc, local, stream, cs, cw, oracle)}
+        m, _ = measure_batched(args, torch, vrc, local, cs, cw, vrc.VRC_FORM_FP32, parity_problems=16)
+        m["workload"] = BATCHED
+        configs["batched1024"] = m
+        line["configs"] = configs
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -81,6 +81,11 @@ typedef struct {
                              so the tally is bit for bit the same up to summation order); the
                              segment counter then counts only the walked segments.  0 (default):
                              every ray is walked to the mesh exit, as the paper casts it */
+  int32_t rays_per_warp;  /* how the cast kernel hands rays to its warps: -1 interleaved (warp w
+                             of the persistent grid takes rays w*32 + lane, then the next 32 rays
+                             one grid further); R > 0, a multiple of 32 up to 65,536: each warp
+                             takes R consecutive (sorted) rays at a time from a device counter,
+                             so warps that finish early take more work; 0 auto (default) */
 } vrc_options;
 
 /* A uniform 3-D Cartesian mesh (Sec. 3: 3-D Cartesian mesh geometry).
@@ -121,6 +126,9 @@ typedef struct {
   int64_t rays;       /* rays processed (including those that scored nothing) */
   int64_t rejected;   /* rays rejected as VRC_ERR_NONFINITE */
   int64_t overflow;   /* rays stopped by the step bound (VRC_ERR_TRAVERSAL) */
+  int64_t live;       /* segments whose score was added (non-zero): once a ray's transmitted
+                         fraction exp(-tau) is exactly 0 in the form's precision, its later
+                         segments are walked and counted in `segments` but add nothing */
 } vrc_stats;
 
 /* Fills *opt with the defaults.  Never fails. */
@@ -200,13 +208,18 @@ int vrc_cast_rays(vrc_ctx *c, const vrc_rays *r, void *cuda_stream);
  *  - out: caller-owned device array of 8*n floats receiving the sorted rays
  *    as x, y, z, u, v, w, E, wt blocks of n each.
  *  - the key uses the context's mesh box, groups and sort_len_buckets.
- *  - scratch: one fixed device array of about 5 MiB inside libvrc, held by
- *    every GPU that loads the library until exit and shared by every call;
- *    each call writes all of it that it reads, so nothing needs clearing.
- *    Calls that overlap on the GPU (other streams, other threads, other
- *    contexts on the same device) race on it: serialise them.
- *  - the first call on each device looks up the scratch's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - scratch: one fixed device array of about 5 MiB inside libvrc, shared by
+ *    every call; each call writes all of it that it reads, so nothing needs
+ *    clearing.  Calls that overlap on the GPU (other streams, other threads,
+ *    other contexts on the same device) race on it: serialise them.
+ *  - set-up: the first call on each device looks up the scratch's device
+ *    address (cudaGetSymbolAddress) and makes the sort kernels resident.
+ *    Under CUDA's lazy module loading (the default) that is when the driver
+ *    places the array and the kernels' code on the device, which can
+ *    allocate device memory; the device then holds them until the process
+ *    exits.  Make that first call before the caller's pool takes the
+ *    device's free memory, and before any stream capture; every later call
+ *    on that device allocates nothing.
  *  - asynchronous on cuda_stream (NULL = the context's stream).
  * Errors: VRC_ERR_ARG (NULL pointers, host rays, too many rays or keys),
  * VRC_ERR_CUDA. */
@@ -491,10 +504,11 @@ int64_t vrc_launch_count(void);
 /* Number of CUDA devices visible (0 when none or on failure). */
 int vrc_device_count(void);
 
-/* Library version as major*10000 + minor*100 + patch (0.2.0: vrc_options
- * gained stop_at_zero; rectilinear meshes, per-history moments, the
- * next-event estimator and streaming buffers were added). */
-#define VRC_VERSION 200
+/* Library version as major*10000 + minor*100 + patch (0.3.0: vrc_options
+ * gained rays_per_warp and vrc_stats gained live; 0.2.0: vrc_options gained
+ * stop_at_zero; rectilinear meshes, per-history moments, the next-event
+ * estimator and streaming buffers were added). */
+#define VRC_VERSION 300
 int vrc_version(void);
 
 #ifdef __cplusplus

@@ -1,9 +1,9 @@
 """Launch-shape autotuner for the cast and the batched form.
 
 Sweeps the options that set the launch shape (threads per block, rays per
-work item, sort granularity), times each candidate with CUDA events on the
-launching stream, and caches the best choice per GPU name and configuration
-class in a JSON file (``$VRC_AUTOTUNE_CACHE``, default
+warp, rays per work item, sort granularity), times each candidate with CUDA
+events on the launching stream, and caches the best choice per GPU name and
+configuration class in a JSON file (``$VRC_AUTOTUNE_CACHE``, default
 ``~/.cache/vrc_autotune.json``).  The sweep is a coordinate descent: one
 option at a time, holding the best values found so far.
 
@@ -19,18 +19,25 @@ import time
 
 from paper_1706_07476_gb300 import vrc
 
-CACHE = os.environ.get("VRC_AUTOTUNE_CACHE",
-                       os.path.join(os.path.expanduser("~"), ".cache", "vrc_autotune.json"))
+
+
+def cache_path() -> str:
+    return os.environ.get("VRC_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "vrc_autotune.json"))
 
 BATCH_SPACE = {
     "sort_len_buckets": [0, 8, 16, 32],
     "chunk": [1024, 2048, 4096, 8192],
     "block": [128, 256],
 }
+# rays_per_warp: -1 interleaved assignment; R > 0, each warp takes R
+# consecutive sorted rays at a time from a device counter
 CAST_SPACE = {
     "sort_len_buckets": [8, 32, 64, 128],
     "block": [128, 256],
+    "rays_per_warp": [-1, 32, 128, 512, 2048],
 }
+CAST_DEFAULT = {"sort_len_buckets": 64, "block": 256, "rays_per_warp": -1}
 
 
 def _gpu_name(torch) -> str:
@@ -39,7 +46,7 @@ def _gpu_name(torch) -> str:
 
 def _load_cache():
     try:
-        with open(CACHE) as f:
+        with open(cache_path()) as f:
             return json.load(f)
     except (OSError, ValueError):
         return {}
@@ -48,11 +55,12 @@ def _load_cache():
 def _store(key, value):
     data = _load_cache()
     data[key] = value
-    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
-    tmp = CACHE + f".tmp{os.getpid()}"
+    path = cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}"
     with open(tmp, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)
-    os.replace(tmp, CACHE)
+    os.replace(tmp, path)
 
 
 def _pow2_bucket(x: float) -> int:
@@ -105,22 +113,27 @@ def _descend(space, default, measure):
     return best, best_ms, table
 
 
-def tune_batched(torch, problems, ctxs, rays_list, form: int, reps: int = 2, use_cache=True):
-    """Best vrc_batch_options fields for this batch (dict), ms, and the sweep table."""
+def tune_batched(torch, problems, ctxs, rays_list, form: int, reps: int = 2, use_cache=True,
+                 timer=None):
+    """Best vrc_batch_options fields for this batch (dict), ms, and the sweep
+    table.  timer(fn) -> ms as in tune_cast."""
     key = f"{_gpu_name(torch)}|{batched_class(problems, form)}"
     if use_cache:
         hit = _load_cache().get(key)
         if hit:
             return hit["options"], hit["ms"], []
-    stream = torch.cuda.Stream()
+    stream = torch.cuda.Stream() if timer is None else None
+    if timer is None:
+        timer = lambda fn: _time_events(torch, fn, stream, reps)  # noqa: E731
 
     def measure(opts):
         o = vrc.vrc_default_batch_options(**opts)
         batch = vrc.vrc_batch_create(ctxs, rays_list, o)
         try:
-            return _time_events(torch, lambda: vrc.vrc_batch_launch(batch, stream=stream), stream, reps)
+            return timer(lambda: vrc.vrc_batch_launch(batch, stream=stream))
         finally:
-            stream.synchronize()
+            if stream is not None:
+                stream.synchronize()
             batch.close()
 
     best, ms, table = _descend(BATCH_SPACE, {"sort_len_buckets": 16, "chunk": 2048, "block": 256},
@@ -129,21 +142,27 @@ def tune_batched(torch, problems, ctxs, rays_list, form: int, reps: int = 2, use
     return best, ms, table
 
 
-def tune_cast(torch, problem, ctx, dev_rays, form: int, reps: int = 2, use_cache=True):
-    """Best vrc_options fields (sort buckets, block) for one problem's casts."""
+def tune_cast(torch, problem, ctx, dev_rays, form: int, reps: int = 2, use_cache=True, timer=None):
+    """Best vrc_options fields (sort buckets, block, rays per warp) for one
+    problem's casts; leaves them set on ctx.  timer(fn) -> ms times one call
+    (default: the best of `reps` CUDA-event timings after a warm-up)."""
     key = f"{_gpu_name(torch)}|{cast_class(problem, form)}"
     if use_cache:
         hit = _load_cache().get(key)
         if hit:
+            vrc.vrc_set_options(ctx, vrc.vrc_default_options(form=form, sort=1, **hit["options"]))
             return hit["options"], hit["ms"], []
-    stream = torch.cuda.Stream()
+    if timer is None:
+        stream = torch.cuda.Stream()
+        timer = lambda fn: _time_events(torch, fn, stream, reps)  # noqa: E731
+    else:
+        stream = None
 
     def measure(opts):
-        o = vrc.vrc_default_options(form=form, sort=1, **opts)
-        vrc.vrc_set_options(ctx, o)
-        return _time_events(torch, lambda: vrc.vrc_cast_rays(ctx, dev_rays, stream=stream), stream, reps)
+        vrc.vrc_set_options(ctx, vrc.vrc_default_options(form=form, sort=1, **opts))
+        return timer(lambda: vrc.vrc_cast_rays(ctx, dev_rays, stream=stream))
 
-    best, ms, table = _descend(CAST_SPACE, {"sort_len_buckets": 64, "block": 256}, measure)
+    best, ms, table = _descend(CAST_SPACE, CAST_DEFAULT, measure)
     vrc.vrc_set_options(ctx, vrc.vrc_default_options(form=form, sort=1, **best))
     _store(key, {"options": best, "ms": ms, "when": time.time()})
     return best, ms, table

@@ -42,6 +42,8 @@ int check_options(const vrc_options *o) {
   if (o->sort_len_buckets != -1 && (o->sort_len_buckets < 1 || o->sort_len_buckets > 256))
     return fail(VRC_ERR_ARG, "options.sort_len_buckets must be -1 or 1..256");
   if (o->stop_at_zero != 0 && o->stop_at_zero != 1) return fail(VRC_ERR_ARG, "options.stop_at_zero must be 0 or 1");
+  if (o->rays_per_warp < -1 || o->rays_per_warp > 65536 || (o->rays_per_warp > 0 && o->rays_per_warp % 32))
+    return fail(VRC_ERR_ARG, "options.rays_per_warp must be -1, 0 or a multiple of 32 up to 65536");
   return VRC_OK;
 }
 
@@ -144,6 +146,8 @@ CastArgs make_args(const vrc_ctx *c, const RayPtrs &rays) {
   a.rays = rays;
   a.tally = c->d_tally;
   a.stop_zero = c->opt.stop_at_zero;
+  a.rays_per_warp = c->opt.rays_per_warp > 0 ? c->opt.rays_per_warp : 0;  // auto: interleaved
+  a.queue = c->d_queue;
   a.counters = c->d_counters;
   a.status = c->d_status;
   return a;
@@ -271,6 +275,8 @@ int cast_device(vrc_ctx *c, RayPtrs rp, cudaStream_t s) {
     VRC_CUDA(c->get_event(&span.stop), "creating a timing event");
     VRC_CUDA(cudaEventRecord(span.start, s), "recording a timing event");
   }
+  if (a.rays_per_warp > 0)
+    VRC_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s), "zeroing the ray counter");
   VRC_CUDA(launch_cast(form, a, grid, block, s), "launching the cast kernel");
   if (c->timing) {
     VRC_CUDA(cudaEventRecord(span.stop, s), "recording a timing event");
@@ -378,6 +384,7 @@ void vrc_default_options(vrc_options *opt) {
   opt->blocks_per_sm = 0;
   opt->device = -1;
   opt->stop_at_zero = 0;
+  opt->rays_per_warp = 0;
 }
 
 int vrc_create_mesh(const vrc_mesh_desc *d, const vrc_options *opt, vrc_ctx **out) {
@@ -454,7 +461,8 @@ int vrc_create_mesh(const vrc_mesh_desc *d, const vrc_options *opt, vrc_ctx **ou
   if ((e = cudaMalloc((void **)&c->d_mat, (size_t)ncells)) != cudaSuccess ||
       (e = cudaMalloc((void **)&c->d_tally, tally_bytes)) != cudaSuccess ||
       (e = cudaMalloc((void **)&c->d_counters, sizeof(unsigned long long) * kNumCounters)) != cudaSuccess ||
-      (e = cudaMalloc((void **)&c->d_status, sizeof(unsigned))) != cudaSuccess)
+      (e = cudaMalloc((void **)&c->d_status, sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMalloc((void **)&c->d_queue, sizeof(unsigned long long))) != cudaSuccess)
     return bail(cuda_fail(e, "allocating the mesh and tally"));
   if (d->group_edges &&
       (e = cudaMalloc((void **)&c->d_edges, sizeof(double) * (d->n_groups + 1))) != cudaSuccess)
@@ -605,6 +613,7 @@ int vrc_sync(vrc_ctx *c, void *cuda_stream, vrc_stats *stats) {
     stats->rays = (int64_t)cnt[kCntRays];
     stats->rejected = (int64_t)cnt[kCntRejected];
     stats->overflow = (int64_t)cnt[kCntOverflow];
+    stats->live = (int64_t)cnt[kCntLive];
   }
   return status_code(st);
 }

@@ -136,6 +136,8 @@ int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, i
     if (bps <= 0) return fail(VRC_ERR_ARG, "cast kernel does not fit on an SM with %d materials", c->n_materials);
   }
   const int grid = (int)std::min<int64_t>((rp.n + block - 1) / block, (int64_t)c->num_sms * bps);
+  if (a.rays_per_warp > 0)
+    VRC_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s), "zeroing the ray counter");
   VRC_CUDA(launch_cast_hist(form, a, grid, block, s), "launching the per-history cast");
   VRC_CUDA(launch_hist_drain(a.htab, static_cast<double2 *>(c->mom.p), c->num_sms, s),
            "launching the per-history fold");

@@ -66,18 +66,32 @@ __global__ void __launch_bounds__(256, FORM == kFormPlain ? 2 : (std::is_same<Ma
   const int stride = lanes * blockDim.x;
 
   RayCounts cnt;
-  if constexpr (FORM == kFormPlain) {
-    // warp-uniform trip count: the batched walk is warp-collective
-    const WarpQueue Q = warp_queue(smem + L.queue);
-    const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
+  // one round: the 32 rays base + lane of this warp (warp-uniform base)
+  auto round = [&](int64_t base) {
+    if constexpr (FORM == kFormPlain) {  // the batched walk is warp-collective
+      cast_one_plain_warp<SURR, Maker, RECT>(a, base + lane, base + lane < a.rays.n, hash_s, edges,
+                                             sig_s, inv_s, stride, warp_queue(smem + L.queue), cnt);
+    } else if (base + lane < a.rays.n) {
+      cast_one<FORM, SURR, Maker, RECT>(a, base + lane, hash_s, edges, sig_s, inv_s, stride, cnt);
+    }
+  };
+  if (a.rays_per_warp > 0) {
+    // dynamic: the warp takes rays_per_warp consecutive rays at a time from
+    // the launch's counter (the counter only grows, so the loop ends)
+    const unsigned long long n = (unsigned long long)a.rays.n;
+    for (;;) {
+      unsigned long long first = 0;
+      if (lane == 0) first = atomicAdd(a.queue, (unsigned long long)a.rays_per_warp);
+      first = __shfl_sync(0xffffffffu, first, 0);
+      if (first >= n) break;
+      const int64_t end = (int64_t)min(first + (unsigned long long)a.rays_per_warp, n);
+      for (int64_t base = (int64_t)first; base < end; base += 32) round(base);
+    }
+  } else {
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < a.rays.n;
          base += (int64_t)gridDim.x * blockDim.x)
-      cast_one_plain_warp<SURR, Maker, RECT>(a, base + lane, base + lane < a.rays.n, hash_s, edges,
-                                             sig_s, inv_s, stride, Q, cnt);
-  } else {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.rays.n;
-         r += (int64_t)gridDim.x * blockDim.x)
-      cast_one<FORM, SURR, Maker, RECT>(a, r, hash_s, edges, sig_s, inv_s, stride, cnt);
+      round(base);
   }
   flush_counts(cnt, a.counters, a.status);
 }

@@ -486,13 +486,14 @@ struct UniformWalk {
 // score to every crossed cell through `sink` (the ray's group slice of the
 // tally, or its history's slots).  The walk ends when the ray leaves the
 // mesh or after max_steps steps (then *overflow is set).  Returns the number
-// of positive-length segments scored.
+// of positive-length segments walked; nlive counts the scores added to the sink.
 template <int FORM, typename Sink>
 __device__ __forceinline__ uint32_t cast_ray(const MeshDev &M, float px, float py, float pz,
                                              float u, float v, float w, float wt, float dn,
                                              const Sink &sink, const float *sg,
                                              const typename Attenuation<FORM>::inv_t *inv,
-                                             int stride, bool stop_zero, bool *overflow) {
+                                             int stride, bool stop_zero, bool *overflow,
+                                             uint32_t &nlive) {
   UniformWalk W;
   if (!W.init(M, px, py, pz, u, v, w)) return 0;
   Attenuation<FORM> att(wt);
@@ -515,7 +516,10 @@ __device__ __forceinline__ uint32_t cast_ray(const MeshDev &M, float px, float p
       } else {
         sc = att.score(sg[W.mat * stride], inv[W.mat * stride], l);
       }
-      if (sc != 0) sink.add(W.cell, Attenuation<FORM>::to_double(sc));
+      if (sc != 0) {
+        sink.add(W.cell, Attenuation<FORM>::to_double(sc));
+        ++nlive;
+      }
     }
     nseg += l > 0.f;
 
@@ -660,7 +664,8 @@ __device__ __forceinline__ uint32_t cast_ray_rect(const MeshDev &M, float px, fl
                                                   float u, float v, float w, float wt, float dn,
                                                   const Sink &sink, const float *sg,
                                                   const typename Attenuation<FORM>::inv_t *inv,
-                                                  int stride, bool stop_zero, bool *overflow) {
+                                                  int stride, bool stop_zero, bool *overflow,
+                                                  uint32_t &nlive) {
   RectWalk W;
   if (!W.init(M, px, py, pz, u, v, w)) return 0;
   Attenuation<FORM> att(wt);
@@ -681,7 +686,10 @@ __device__ __forceinline__ uint32_t cast_ray_rect(const MeshDev &M, float px, fl
       } else {
         sc = att.score(sg[W.mat * stride], inv[W.mat * stride], l);
       }
-      if (sc != 0) sink.add(W.cell, Attenuation<FORM>::to_double(sc));
+      if (sc != 0) {
+        sink.add(W.cell, Attenuation<FORM>::to_double(sc));
+        ++nlive;
+      }
     }
     nseg += l > 0.f;
 
@@ -748,7 +756,7 @@ __device__ __forceinline__ uint32_t cast_ray_plain_warp(const MeshDev &M, bool a
                                                         float wt, float dn, const Sink &sink,
                                                         const float *sg, const double *inv,
                                                         int stride, bool stop_zero, bool *overflow,
-                                                        const WarpQueue &Q) {
+                                                        const WarpQueue &Q, uint32_t &nlive) {
   const unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   Walk W;
@@ -804,7 +812,10 @@ __device__ __forceinline__ uint32_t cast_ray_plain_warp(const MeshDev &M, bool a
     for (int j = 0; j < nq; ++j) {
       const int slot = lane * kPlainBatch + j;
       const double sc = att.apply(Q.io[slot]);
-      if (sc != 0.0) sink.add(Q.cell[slot], sc);
+      if (sc != 0.0) {
+        sink.add(Q.cell[slot], sc);
+        ++nlive;
+      }
     }
     if (!__any_sync(kAll, active)) break;
   }
@@ -825,7 +836,7 @@ __device__ __forceinline__ void load_ray(const RayPtrs &R, int64_t r, float (&f)
 
 // Per-thread counters of one cast, flushed with one atomic per warp.
 struct RayCounts {
-  uint32_t seg = 0, rays = 0, rej = 0, ovf = 0;
+  uint32_t seg = 0, rays = 0, rej = 0, ovf = 0, live = 0;
 };
 
 // A validated ray: position, direction (and its norm), weight, group.
@@ -891,10 +902,11 @@ __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int
   bool ovf = false;
   if constexpr (RECT)
     c.seg += cast_ray_rect<FORM>(a.mesh, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn,
-                                 Maker::make(a, r, q.g), sig_s, inv_s, stride, a.stop_zero != 0, &ovf);
+                                 Maker::make(a, r, q.g), sig_s, inv_s, stride, a.stop_zero != 0, &ovf,
+                                 c.live);
   else
     c.seg += cast_ray<FORM>(a.mesh, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn, Maker::make(a, r, q.g),
-                            sig_s, inv_s, stride, a.stop_zero != 0, &ovf);
+                            sig_s, inv_s, stride, a.stop_zero != 0, &ovf, c.live);
   c.ovf += ovf;
 }
 
@@ -915,7 +927,7 @@ __device__ __forceinline__ void cast_one_plain_warp(const CastArgs &a, int64_t r
   // a lane without a ray builds its (unused) sink from ray 0 of group 0
   c.seg += cast_ray_plain_warp<Walk>(a.mesh, ok, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn,
                                      Maker::make(a, ok ? r : 0, ok ? q.g : 0), sig_s, inv_s, stride,
-                                     a.stop_zero != 0, &ovf, Q);
+                                     a.stop_zero != 0, &ovf, Q, c.live);
   c.ovf += ovf;
 }
 
@@ -927,10 +939,12 @@ __device__ __forceinline__ void flush_counts(RayCounts c, unsigned long long *co
     c.rays += __shfl_down_sync(0xffffffffu, c.rays, o);
     c.rej += __shfl_down_sync(0xffffffffu, c.rej, o);
     c.ovf += __shfl_down_sync(0xffffffffu, c.ovf, o);
+    c.live += __shfl_down_sync(0xffffffffu, c.live, o);
   }
   if ((threadIdx.x & 31) == 0) {
     if (c.seg) atomicAdd(counters + kCntSegments, (unsigned long long)c.seg);
     if (c.rays) atomicAdd(counters + kCntRays, (unsigned long long)c.rays);
+    if (c.live) atomicAdd(counters + kCntLive, (unsigned long long)c.live);
     if (c.rej) {
       atomicAdd(counters + kCntRejected, (unsigned long long)c.rej);
       atomicOr(status, kStatusNonfinite);

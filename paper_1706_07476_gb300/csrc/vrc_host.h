@@ -115,6 +115,7 @@ struct vrc_ctx {
   double *d_tally = nullptr;
   unsigned long long *d_counters = nullptr;
   unsigned int *d_status = nullptr;
+  unsigned long long *d_queue = nullptr;  // ray counter of a cast with rays_per_warp > 0
 
   int32_t n_union = 0, m_pad = 0, n_hash = 0;
   float l2min = 0.f, inv_bw = 0.f;
@@ -181,6 +182,7 @@ struct vrc_ctx {
     cudaFree(d_tally);
     cudaFree(d_counters);
     cudaFree(d_status);
+    cudaFree(d_queue);
     xsE.release();
     xsInvdE.release();
     xsS.release();

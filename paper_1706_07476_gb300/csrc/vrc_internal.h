@@ -17,7 +17,9 @@ constexpr unsigned kStatusTableFull = 4u;  // a per-history table insert found n
 constexpr unsigned kStatusTimeout = 8u;    // a bounded wait on the tensor cores gave up
 
 // Device counters (unsigned long long each).
-enum Counter { kCntSegments = 0, kCntRays = 1, kCntRejected = 2, kCntOverflow = 3, kNumCounters = 4 };
+// kCntLive: segments whose score was added to the tally (non-zero; once a
+// ray's transmitted fraction is exactly 0 its segments are walked, not scored).
+enum Counter { kCntSegments = 0, kCntRays = 1, kCntRejected = 2, kCntOverflow = 3, kCntLive = 4, kNumCounters = 5 };
 
 // A value held as an unevaluated sum hi + lo of two float32 ("double-float").
 struct df {
@@ -81,6 +83,11 @@ struct CastArgs {
   const uint32_t *hist; // [n] history id of each ray (per-history cast only)
   HistTable htab;       // per-history cast only
   int32_t stop_zero;    // end a walk once its transmitted fraction is exactly 0
+  // Ray assignment: 0, each thread takes rays r, r + (grid threads), ...;
+  // R > 0 (a multiple of 32), each warp takes R consecutive rays at a time
+  // from the counter *queue (zeroed before the launch).
+  int32_t rays_per_warp;
+  unsigned long long *queue;
   unsigned long long *counters;
   unsigned int *status;
 };

@@ -335,4 +335,15 @@ cudaError_t launch_batched_sort(const BSortProblem *probs_dev, const int32_t *ch
 
 int scan_tile_elems() { return kScanTile; }
 
+cudaError_t load_sort_kernels() {
+  cudaFuncAttributes fa;
+  const void *fns[] = {(const void *)k_sort_count, (const void *)k_scan_tiles, (const void *)k_scan_sums,
+                       (const void *)k_scan_apply, (const void *)k_sort_scatter};
+  for (const void *f : fns) {
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace vrc

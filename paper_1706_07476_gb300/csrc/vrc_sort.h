@@ -78,6 +78,11 @@ cudaError_t launch_batched_sort(const BSortProblem *probs_dev, const int32_t *ch
 cudaError_t prepare_batched_sort(const BSortPlan &plan);
 int scan_tile_elems();
 
+// Makes the single-problem sort kernels resident on the current device
+// (cudaFuncGetAttributes on each): under lazy module loading, this is when
+// their code is placed on the device.
+cudaError_t load_sort_kernels();
+
 // Sort-key arguments, group edges (device), device and stream of a context.
 int ctx_sort_args(const vrc_ctx *c, SortKeyArgs *P, const double **edges, int *device,
                   cudaStream_t *stream);

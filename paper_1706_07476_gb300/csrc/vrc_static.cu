@@ -34,15 +34,21 @@ constexpr size_t kTableBytes = align_up(sizeof(uint32_t) * (size_t)(kMaxKeys * k
 constexpr size_t kTilesBytes = align_up(sizeof(uint32_t) * (size_t)((kMaxKeys * kMaxChunks + 8191) / 8192));
 constexpr size_t kScratchBytes = kKeysBytes + 2 * kTableBytes + kTilesBytes;  // about 5 MiB
 
-// The scratch itself: every GPU that loads libvrc holds this array until the
-// process exits.  Host code must not use its name as an address.
+// The scratch itself.  A device holds it from the moment this file's module
+// is placed on that device (the first vrc_sort_rays_static call there, see
+// scratch_address) until the process exits.  Host code must not use its
+// name as an address.
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
 std::mutex g_mu;
 unsigned char *g_scratch_dev[kMaxDevices] = {};
 
-// Device address of g_sort_scratch on `dev` (which must be current),
-// looked up once per device.
+// Set-up, once per device (`dev` must be current): the device address of
+// g_sort_scratch, and the sort kernels made resident.  With CUDA's lazy
+// module loading (the default since CUDA 12.2) a module reaches a device the
+// first time one of its kernels or symbols is used there, and placing it can
+// allocate device memory; doing both here, in the first call, means that
+// later calls find everything in place and allocate nothing.
 int scratch_address(int dev, unsigned char **out) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_scratch_dev[dev]) {
@@ -50,6 +56,9 @@ int scratch_address(int dev, unsigned char **out) {
     cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
     if (e != cudaSuccess || p == nullptr)
       return vrc::set_last_error(VRC_ERR_CUDA, "cudaGetSymbolAddress of the static sort scratch failed");
+    e = vrc::load_sort_kernels();
+    if (e != cudaSuccess)
+      return vrc::set_last_error(VRC_ERR_CUDA, "loading the sort kernels failed");
     g_scratch_dev[dev] = static_cast<unsigned char *>(p);
   }
   *out = g_scratch_dev[dev];

@@ -42,7 +42,7 @@ class VrcError(RuntimeError):
 class vrc_options(C.Structure):
     _fields_ = [("form", C.c_int32), ("sort", C.c_int32), ("sort_len_buckets", C.c_int32),
                 ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("device", C.c_int32),
-                ("stop_at_zero", C.c_int32)]
+                ("stop_at_zero", C.c_int32), ("rays_per_warp", C.c_int32)]
 
 
 class vrc_mesh_desc(C.Structure):
@@ -66,7 +66,7 @@ class vrc_rays(C.Structure):
 
 class vrc_stats(C.Structure):
     _fields_ = [("segments", C.c_int64), ("rays", C.c_int64), ("rejected", C.c_int64),
-                ("overflow", C.c_int64)]
+                ("overflow", C.c_int64), ("live", C.c_int64)]
 
 
 def _load():
@@ -558,7 +558,8 @@ def vrc_sync(ctx: Context, stream=None):
     st = vrc_stats()
     rc = _lib.vrc_sync(ctx.handle, _stream_handle(stream), C.byref(st))
     _check(rc, ok=(VRC_OK, VRC_ERR_NONFINITE, VRC_ERR_TRAVERSAL))
-    return rc, dict(segments=st.segments, rays=st.rays, rejected=st.rejected, overflow=st.overflow)
+    return rc, dict(segments=st.segments, rays=st.rays, rejected=st.rejected, overflow=st.overflow,
+                    live=st.live)
 
 
 def vrc_read_tally(ctx: Context, out: np.ndarray | None = None, flags: int = 0, stream=None):

@@ -57,7 +57,7 @@ def test_slab256_full_size(vrc, slab_full, form):
     print(f"slab256 form={form}: rc={rc} {stats} oracle={st} {rep}")
     assert rc == vrc.VRC_OK
     assert stats["rays"] == prob.n_rays and stats["overflow"] == 0
-    assert abs(stats["segments"] - st["segments"]) <= 2, (stats, st)
+    assert stats["segments"] == st["segments"], (stats, st)
     assert rep["max_rel"] <= REL_TOL, rep
     assert rep["max_abs_below"] <= 1e-28, rep
 
@@ -70,6 +70,6 @@ def test_pin_lattice_full_size(vrc, lattice_full, form):
     rep = H.rel_err_report(want, got)
     print(f"lattice form={form}: rc={rc} {stats} oracle={st} {rep}")
     assert rc == vrc.VRC_OK
-    assert abs(stats["segments"] - st["segments"]) <= 2, (stats, st)
+    assert stats["segments"] == st["segments"], (stats, st)
     assert rep["max_rel"] <= REL_TOL, rep
     assert rep["max_abs_below"] <= 1e-28, rep

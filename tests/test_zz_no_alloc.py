@@ -8,8 +8,10 @@ device array.  This test calls that entry point through the C ABI on two
 batches in a row and checks each result against the allocating path:
 the output is a permutation of the input in group order, and casting it with
 sorting off gives vrc_cast_rays' sorted tally to the tolerance the sort
-tests use.  It sits in its own file, collected last, and passes both alone
-in a fresh process and after the other tests.
+tests use.  It also checks the promise itself: once the first call on the
+device has done its set-up, a second call leaves the device's free memory
+(as the driver reports it) unchanged.  It sits in its own file, collected
+last, and passes both alone in a fresh process and after the other tests.
 """
 from __future__ import annotations
 
@@ -42,13 +44,22 @@ def test_static_sort_matches_allocating_path_twice_in_a_row(vrc):
     prob = W.slab_room(seed=1, n=40, n_rays=2 * n, n_points=1500, n_resonances=30)
     sorter = vrc.context_for(prob)  # mesh box and groups of the sort key
     try:
-        for call, sl in enumerate((slice(0, n), slice(n, 2 * n))):
-            part = W.take_rays(prob, sl)
-            dev = {k: torch.from_numpy(part.rays[k]).cuda() for k in FIELDS}
-            out = torch.full((8 * n,), float("nan"), dtype=torch.float32, device="cuda")
-            torch.cuda.synchronize()
-            vrc.vrc_sort_rays_static(sorter, dev, out, stream=stream)
-            stream.synchronize()
+        # every input and output of both calls exists before the first call,
+        # so that between the two free-memory readings only the second call runs
+        parts = [W.take_rays(prob, sl) for sl in (slice(0, n), slice(n, 2 * n))]
+        devs = [{k: torch.from_numpy(p.rays[k]).cuda() for k in FIELDS} for p in parts]
+        outs = [torch.full((8 * n,), float("nan"), dtype=torch.float32, device="cuda") for _ in parts]
+        torch.cuda.synchronize()
+        vrc.vrc_sort_rays_static(sorter, devs[0], outs[0], stream=stream)
+        stream.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        vrc.vrc_sort_rays_static(sorter, devs[1], outs[1], stream=stream)
+        stream.synchronize()
+        free_after = torch.cuda.mem_get_info()[0]
+        assert free_after == free_before, (free_before, free_after)
+
+        for call in range(2):
+            part, dev, out = parts[call], devs[call], outs[call]
             got = out.view(8, n).cpu().numpy()
 
             # a permutation of the input rays
