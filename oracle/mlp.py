@@ -9,13 +9,16 @@ evaluation per ray serves every cell it crosses, Eq. 4):
 
     x      = (log10 E - log10 e_lo) / (log10 e_hi - log10 e_lo)
     emb(E) = [sin(pi f_0 x), cos(pi f_0 x), ..., sin(pi f_31 x), cos(pi f_31 x)],
-             f_k = 2^(11 k / 31)  (32 frequencies, 1 to 2048)
+             f_k = 2^(5 k / 31)  (32 frequencies, 1 to 32)
     h1 = silu(W1 emb + b1)   (64 -> 128)
     h2 = silu(W2 h1 + b2)    (128 -> 128)
-    y  = W3 h2 + b3          (128 -> 16), y_m = log Sigma_m(E)
+    y  = W3 h2 + b3 + log(a + b E^(-1/2))   (128 -> 16), y_m = log Sigma_m(E)
 
-silu(z) = z / (1 + exp(-z)).  Parameters are one flat float vector in the
-order W1 [128][64], b1 [128], W2 [128][128], b2 [128], W3 [16][128], b3 [16].
+silu(z) = z / (1 + exp(-z)).  The last term is a fixed prior per material,
+the 1/v shape of a total cross section (a constant plus a term in
+1/sqrt(E)), with a_m > 0 and b_m >= 0; the network learns the rest.
+Parameters are one flat float vector in the order W1 [128][64], b1 [128],
+W2 [128][128], b2 [128], W3 [16][128], b3 [16], C [16][2] (C[m] = a_m, b_m).
 The training loss is the mean of (y_m - log Sigma_m)^2 over the unmasked
 (row, material) pairs.
 """
@@ -24,12 +27,12 @@ from __future__ import annotations
 import numpy as np
 
 N_FREQ = 32
-FREQ_MAX_LOG2 = 11  # highest frequency 2^11; a fit study over 2^10 .. 2^15 found 2^11 best
+FREQ_MAX_LOG2 = 5  # highest frequency 2^5 = 32 periods over the energy range
 EMB = 2 * N_FREQ
 HID = 128
 OUT = 16
 SHAPES = (("W1", (HID, EMB)), ("b1", (HID,)), ("W2", (HID, HID)), ("b2", (HID,)),
-          ("W3", (OUT, HID)), ("b3", (OUT,)))
+          ("W3", (OUT, HID)), ("b3", (OUT,)), ("C", (OUT, 2)))
 N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
 
 
@@ -75,6 +78,13 @@ def silu_grad(z):
     return s * (1.0 + z * (1.0 - s))
 
 
+def prior(params, E):
+    """a_m + b_m E^(-1/2) per row and material, and E^(-1/2)."""
+    P = unpack(params)
+    r = 1.0 / np.sqrt(np.asarray(E, np.float64))
+    return P["C"][None, :, 0] + P["C"][None, :, 1] * r[:, None], r
+
+
 def forward(params, E, e_lo: float, e_hi: float):
     """Returns y [M][16] and the intermediate values the gradient needs."""
     P = unpack(params)
@@ -83,8 +93,9 @@ def forward(params, E, e_lo: float, e_hi: float):
     h1 = silu(z1)
     z2 = h1 @ P["W2"].T + P["b2"]
     h2 = silu(z2)
-    y = h2 @ P["W3"].T + P["b3"]
-    return y, dict(x0=x0, z1=z1, h1=h1, z2=z2, h2=h2)
+    q, r = prior(params, E)
+    y = h2 @ P["W3"].T + P["b3"] + np.log(q)
+    return y, dict(x0=x0, z1=z1, h1=h1, z2=z2, h2=h2, q=q, r=r)
 
 
 def loss_and_grad(params, E, target, mask, e_lo: float, e_hi: float):
@@ -99,6 +110,7 @@ def loss_and_grad(params, E, target, mask, e_lo: float, e_hi: float):
     g = {}
     g["W3"] = dy.T @ c["h2"]
     g["b3"] = dy.sum(0)
+    g["C"] = np.stack([(dy / c["q"]).sum(0), (dy * c["r"][:, None] / c["q"]).sum(0)], axis=1)
     dz2 = (dy @ P["W3"]) * silu_grad(c["z2"])
     g["W2"] = dz2.T @ c["h1"]
     g["b2"] = dz2.sum(0)
@@ -109,13 +121,16 @@ def loss_and_grad(params, E, target, mask, e_lo: float, e_hi: float):
 
 
 def init_params(seed: int) -> np.ndarray:
-    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases."""
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases, and
+    the prior a = 1, b = 0 (log q = 0)."""
     rng = np.random.default_rng(seed)
     P = {}
     for name, shape in SHAPES:
         if name.startswith("W"):
             bound = 1.0 / np.sqrt(shape[1])
             P[name] = rng.uniform(-bound, bound, shape)
+        elif name == "C":
+            P[name] = np.stack([np.ones(OUT), np.zeros(OUT)], axis=1)
         else:
             P[name] = np.zeros(shape)
     return pack(P)
