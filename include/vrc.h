@@ -376,17 +376,21 @@ void vrc_stream_destroy(vrc_stream *s);
  * (Sec. 3: hashed search, lin-lin interpolation) by a small network
  * evaluated on the tensor cores:
  *   x = (log10 E - log10 e_lo)/(log10 e_hi - log10 e_lo);
- *   features sin(pi f_k x), cos(pi f_k x), f_k = 2^(11k/31), k = 0..31;
+ *   features sin(pi f_k x), cos(pi f_k x), f_k = 2^(5k/31), k = 0..31;
  *   h1 = silu(W1 x + b1) (64->128); h2 = silu(W2 h1 + b2) (128->128);
- *   y = W3 h2 + b3 (128->16), y_m = log Σt of material m.
+ *   y = W3 h2 + b3 + log(a + b E^(-1/2)) (128->16), y_m = log Σt of material m.
+ * The last term is a fixed per-material prior, the 1/v shape of a total
+ * cross section (a_m > 0, b_m >= 0), fitted to the table before training;
+ * the network learns the rest.
  * Parameters: VRC_MLP_PARAMS float32 values, W1 [128][64], b1 [128],
- * W2 [128][128], b2 [128], W3 [16][128], b3 [16].  Weights are rounded to
- * bfloat16; the two 128-wide layers run on the tensor cores (bfloat16
- * activations, float32 accumulation), the output layer in float32 from
- * float32 h2.  The exact table stays
- * the fallback: after training, every hash bin whose validated relative error
- * exceeds the bound is flagged and rays in flagged bins use the table. */
-#define VRC_MLP_PARAMS 26896
+ * W2 [128][128], b2 [128], W3 [16][128], b3 [16], C [16][2] (a_m, b_m).
+ * W1 and W2 are rounded to bfloat16 and run on the tensor cores with float32
+ * accumulation; their inputs (the features and h1) enter as bfloat16 pairs
+ * hi + lo (about 16 significant bits); the output layer runs in float32
+ * (W3 and h2 float32).  The exact table stays the fallback: after training,
+ * every hash bin whose validated relative error exceeds the bound is flagged
+ * and rays in flagged bins use the table. */
+#define VRC_MLP_PARAMS 26928
 #define VRC_XS_TABLE 0
 #define VRC_XS_SURROGATE 1
 
@@ -397,48 +401,57 @@ int vrc_mlp_forward(const float *params, const float *E, int64_t n, double e_lo,
                     float *log_sigma, void *cuda_stream);
 
 /* Loss and gradient: loss = (1/count) Σ over unmasked (row, output) pairs of
- * (y - target)^2 and its gradient with respect to params.  DEVICE arrays:
- * target [n][16], mask [n][16] (uint8, non-zero = used; NULL = all used),
- * grad [VRC_MLP_PARAMS] and loss [1] (both overwritten).  count = number of
- * used pairs (> 0). */
+ * (y - target)^2 and its gradient with respect to params (the prior's
+ * coefficients included).  DEVICE arrays: target [n][16], mask [n][16]
+ * (uint8, non-zero = used; NULL = all used), grad [VRC_MLP_PARAMS] and
+ * loss [1] (both overwritten).  count = number of used pairs (> 0). */
 int vrc_mlp_loss_grad(const float *params, const float *E, const float *target,
                       const uint8_t *mask, int64_t n, int64_t count, double e_lo, double e_hi,
                       float *grad, float *loss, void *cuda_stream);
 
 typedef struct {
-  int32_t steps;   /* Adam steps (default 8000); 0 keeps the trained parameters and only
+  int32_t steps;   /* Adam steps (default 12000); 0 keeps the trained parameters and only
                       re-validates them at tol (VRC_ERR_STATE if none exist) */
   int32_t batch;   /* rows per step (default 4096) */
   float lr;        /* peak learning rate, cosine decay (default 5e-3) */
   float tol;       /* accepted relative error of Σt per hash bin (default 1e-3) */
   uint64_t seed;   /* initial weights and row sampling (default 4) */
+  float smooth;    /* training uses only the table intervals where log Σt of every
+                      material stays within this of a straight line in log E over 7
+                      union-grid points (default 5e-6); resonance structure stays with
+                      the table */
 } vrc_surrogate_options;
 
 typedef struct {
-  float final_loss;            /* mean squared error of log Σt over the last step */
+  float final_loss;            /* mean squared error of the normalised targets, last step */
   int32_t bins, bins_accepted; /* hash bins, and bins where the surrogate is used */
   float coverage;              /* bins_accepted / bins */
   float max_rel_err_accepted;  /* largest validated relative Σt error in accepted bins */
   float median_rel_err;        /* median validated relative Σt error over all points */
   int64_t train_points, validation_points;
+  float smooth_fraction;       /* fraction of union-grid intervals trained on */
 } vrc_surrogate_report;
 
 void vrc_default_surrogate_options(vrc_surrogate_options *opt);
 
 /* Trains the context's surrogate on its own tables with libvrc's kernels
- * (forward, backward, Adam), then validates it at 8 energies per table
- * interval that are not training points, and flags every hash bin (with its
- * two neighbours) where any material's relative Σt error exceeds tol.  At
- * most 16 materials; void materials are not modelled (Σt = 0 exactly).
- * Synchronous.  Does not change the lookup mode.  report may be NULL.
+ * (forward, backward, Adam): fits each material's prior, trains the network
+ * on the smooth intervals (see vrc_surrogate_options.smooth), then validates
+ * it at 8 energies per union-grid interval that are not training points, and
+ * flags every hash bin (with its two neighbours) where any material's
+ * relative Σt error exceeds tol or that holds no validation point.  At most
+ * 16 materials; void materials are not modelled (Σt = 0 exactly); if a
+ * non-void table has a zero Σt, no bin is accepted.  Synchronous.  Does not
+ * change the lookup mode.  report may be NULL.
  * Errors: VRC_ERR_ARG, VRC_ERR_STATE (no tables), VRC_ERR_OOM, VRC_ERR_CUDA. */
 int vrc_train_surrogate(vrc_ctx *c, const vrc_surrogate_options *opt, vrc_surrogate_report *report);
 
 /* Selects VRC_XS_TABLE (default) or VRC_XS_SURROGATE for later casts
  * (VRC_ERR_STATE if no surrogate has been trained).  With the surrogate, a
- * cast first evaluates the network for every ray (one tensor-core forward
- * pass, Σt of all materials into context scratch of 64 B per ray); rays in
- * flagged bins or outside the table's energy range use the table. */
+ * cast always sorts its rays, those whose energy lies in an accepted bin
+ * first; the network runs on exactly those rays (one tensor-core forward
+ * pass, Σt of all materials into context scratch of 64 B per ray) and every
+ * other ray uses the table.  With no bin accepted the network does no work. */
 int vrc_set_xs_mode(vrc_ctx *c, int32_t mode);
 
 /* Copies the trained parameters (VRC_MLP_PARAMS float32) to a HOST array. */

@@ -175,7 +175,7 @@ int sync_streams(vrc_ctx *c, void *stream) {
 
 
 int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in, uint32_t *carry_out,
-              bool spatial) {
+              bool spatial, const uint32_t **n_accepted) {
   SortKeyArgs P;
   std::memset(&P, 0, sizeof P);
   for (int k = 0; k < 3; ++k) {
@@ -191,6 +191,20 @@ int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in,
   const int max_cells = c->n[0] + c->n[1] + c->n[2] + 1;
   P.len_width = std::max(1, (max_cells + nl - 1) / nl);
   P.n_keys = c->n_groups * nl + 1;
+  if (n_accepted) {  // accepted-bin rays first: twice the keys
+    while (nl > 1 && 2 * (int64_t)c->n_groups * nl + 1 > 16384) nl >>= 1;
+    if (2 * (int64_t)c->n_groups * nl + 1 > 16384)
+      return fail(VRC_ERR_ARG, "too many energy groups for the surrogate's sort");
+    P.n_len = nl;
+    P.len_width = std::max(1, (max_cells + nl - 1) / nl);
+    P.n_keys = 2 * c->n_groups * nl + 1;
+    P.acc_flags = static_cast<const uint8_t *>(c->mlpFlags.p);
+    P.acc_n_hash = c->n_hash;
+    P.acc_l2min = c->l2min;
+    P.acc_inv_bw = c->inv_bw;
+    P.acc_e_lo = c->mlp_lo;
+    P.acc_e_hi = c->mlp_hi;
+  }
   if (spatial) {  // (group, block) keys on at most 8^3 blocks
     int nb = 8;
     while (nb > 1 && (int64_t)c->n_groups * nb * nb * nb + 1 > 16384) nb >>= 1;
@@ -225,34 +239,36 @@ int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in,
   }
   rp.x = rp.y = rp.z = rp.u = rp.v = rp.w = rp.E = rp.wt = nullptr;
   rp.aos = out.aos;
+  // the exclusive prefix sum of the (key, chunk) counts at the first key of
+  // the not-accepted half is the number of accepted rays
+  if (n_accepted)
+    *n_accepted = static_cast<const uint32_t *>(c->sortOffsets.p) + (int64_t)c->n_groups * P.n_len * plan.n_chunks;
   return VRC_OK;
 }
 
 // Sort (optional), surrogate (optional) and cast of a device batch on stream s.
 int cast_device(vrc_ctx *c, RayPtrs rp, cudaStream_t s) {
-  const bool do_sort = c->opt.sort == 1 || (c->opt.sort == -1 && rp.n >= kAutoSortMin);
+  // with the learned surrogate the rays are always sorted: those in accepted
+  // energy bins first, so the network runs on exactly that leading range
+  const bool surr = c->xs_mode == VRC_XS_SURROGATE && c->mlp_ready;
+  const bool do_sort = surr || c->opt.sort == 1 || (c->opt.sort == -1 && rp.n >= kAutoSortMin);
+  const uint32_t *n_acc = nullptr;
   if (do_sort) {
-    int rc = sort_rays(c, rp, s);
+    int rc = sort_rays(c, rp, s, nullptr, nullptr, false, surr ? &n_acc : nullptr);
     if (rc) return rc;
   }
   const float *sig_ray = nullptr;
-  if (c->xs_mode == VRC_XS_SURROGATE && c->mlp_ready) {
+  if (surr) {
     VRC_CUDA(c->sigBuf.ensure(sizeof(float) * 16 * (size_t)rp.n), "allocating surrogate scratch");
     mlp::ApplyArgs aa;
     std::memset(&aa, 0, sizeof aa);
     aa.params = static_cast<const float *>(c->mlpParams.p);
-    aa.E = rp.E;
     aa.aos = rp.aos;
     aa.n = rp.n;
+    aa.n_limit = n_acc;
     aa.out = static_cast<float *>(c->sigBuf.p);
     aa.mode = 1;
     aa.mat_mask = c->mlp_mask;
-    aa.flags = static_cast<const uint8_t *>(c->mlpFlags.p);
-    aa.n_hash = c->n_hash;
-    aa.l2min = c->l2min;
-    aa.inv_bw = c->inv_bw;
-    aa.e_first = c->mlp_lo;
-    aa.e_last = c->mlp_hi;
     aa.emb = mlp::make_embed(c->mlp_lo, c->mlp_hi);
     aa.status = c->d_status;
     VRC_CUDA(mlp::launch_apply(aa, c->num_sms, s), "launching the surrogate");
@@ -260,6 +276,7 @@ int cast_device(vrc_ctx *c, RayPtrs rp, cudaStream_t s) {
   }
   CastArgs a = make_args(c, rp);
   a.sig_ray = sig_ray;
+  a.n_surr = n_acc;
   const int form = c->opt.form;
   const int block = c->opt.block > 0 ? c->opt.block : 256;
   int bps = c->opt.blocks_per_sm;

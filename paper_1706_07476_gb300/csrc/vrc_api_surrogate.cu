@@ -90,11 +90,12 @@ int vrc_mlp_loss_grad(const float *params, const float *E, const float *target, 
 
 void vrc_default_surrogate_options(vrc_surrogate_options *opt) {
   if (!opt) return;
-  opt->steps = 8000;
+  opt->steps = 12000;
   opt->batch = 4096;
   opt->lr = 5e-3f;
   opt->tol = 1e-3f;
   opt->seed = 4;
+  opt->smooth = 5e-6f;
 }
 
 int vrc_train_surrogate(vrc_ctx *c, const vrc_surrogate_options *opt, vrc_surrogate_report *report) {
@@ -102,7 +103,8 @@ int vrc_train_surrogate(vrc_ctx *c, const vrc_surrogate_options *opt, vrc_surrog
   vrc_surrogate_options o;
   vrc_default_surrogate_options(&o);
   if (opt) o = *opt;
-  if (o.steps < 0 || o.batch < 64 || o.batch > (1 << 22) || !(o.lr > 0.f) || !(o.tol > 0.f))
+  if (o.steps < 0 || o.batch < 64 || o.batch > (1 << 22) || !(o.lr > 0.f) || !(o.tol > 0.f) ||
+      !(o.smooth > 0.f))
     return fail(VRC_ERR_ARG, "bad surrogate options");
   if (c->n_materials > mlp::kOut)
     return fail(VRC_ERR_ARG, "the surrogate models at most %d materials", mlp::kOut);
@@ -112,42 +114,121 @@ int vrc_train_surrogate(vrc_ctx *c, const vrc_surrogate_options *opt, vrc_surrog
     int rc = build_xs(c);
     if (rc) { c->xs_dirty = true; return rc; }
   }
+  const bool revalidate = o.steps == 0;
+  if (revalidate && !c->mlp_ready) return fail(VRC_ERR_STATE, "no trained surrogate to re-validate");
   uint32_t mask = 0;
   for (int m = 0; m < c->n_materials; ++m)
     if (c->loaded[m] && !c->tabE[m].empty()) mask |= 1u << m;
   if (mask == 0 || c->n_union < 2) return fail(VRC_ERR_STATE, "no cross-section tables to learn");
+  // a table with a zero sigma cannot be modelled in log sigma; rays would
+  // then need the table for that material, so no bin is accepted at all
+  bool unmodelled = false;
+  for (int m = 0; m < c->n_materials; ++m)
+    if ((mask >> m) & 1u)
+      for (double v : c->tabS[m])
+        if (!(v > 0.0)) { mask &= ~(1u << m); unmodelled = true; break; }
 
-  // energies: the union grid, refined; training at fractions 0, 1/4, 1/2,
-  // 3/4 of every interval (plus the last point), validation at (k + 1/2)/8
   std::vector<double> U((size_t)c->n_union);
   VRC_CUDA(cudaMemcpy(U.data(), c->xsE.p, sizeof(double) * U.size(), cudaMemcpyDeviceToHost), "reading the grid");
   const int nm = c->n_materials;
+  const size_t nu = U.size();
+
+  // Smooth union-grid points: log sigma of every modelled material deviates
+  // from the straight line (in log E) through its two neighbours by less
+  // than o.smooth, at the point and at the 3 points on either side.  Only
+  // intervals between two smooth points are trained on: a resonance's sharp
+  // structure stays with the table, and the network's capacity goes to the
+  // parts of the tables it can fit to the bound.
+  std::vector<std::vector<double>> LS(nm);  // log sigma at the union points
+  for (int m = 0; m < nm; ++m)
+    if ((mask >> m) & 1u) {
+      LS[m].resize(nu);
+      for (size_t i = 0; i < nu; ++i) LS[m][i] = std::log(table_sigma(c->tabE[m], c->tabS[m], U[i]));
+    }
+  std::vector<double> dev(nu, 0.0);
+  for (size_t i = 1; i + 1 < nu; ++i) {
+    const double x0 = std::log(U[i - 1]), x1 = std::log(U[i]), x2 = std::log(U[i + 1]);
+    for (int m = 0; m < nm; ++m)
+      if ((mask >> m) & 1u) {
+        const double lin = (LS[m][i - 1] * (x2 - x1) + LS[m][i + 1] * (x1 - x0)) / (x2 - x0);
+        dev[i] = std::max(dev[i], std::fabs(LS[m][i] - lin));
+      }
+  }
+  std::vector<uint8_t> smooth(nu, 0);
+  for (size_t i = 0; i < nu; ++i) {
+    double w = 0.0;
+    for (size_t j = (i >= 3 ? i - 3 : 0); j <= std::min(nu - 1, i + 3); ++j) w = std::max(w, dev[j]);
+    smooth[i] = w < (double)o.smooth;
+  }
+
+  // training energies: fractions 0, 1/4, 1/2, 3/4 of every smooth interval;
+  // validation at (k + 1/2)/8 of every interval
   std::vector<float> trE, trT, vaE;
   std::vector<double> vaE64;
-  for (size_t i = 0; i + 1 < U.size(); ++i) {
-    for (int q = 0; q < 4; ++q) trE.push_back((float)(U[i] + (U[i + 1] - U[i]) * q / 4.0));
+  int64_t smooth_intervals = 0;
+  for (size_t i = 0; i + 1 < nu; ++i) {
+    if (smooth[i] && smooth[i + 1]) {
+      ++smooth_intervals;
+      for (int q = 0; q < 4; ++q) trE.push_back((float)(U[i] + (U[i + 1] - U[i]) * q / 4.0));
+    }
     for (int q = 0; q < 8; ++q) {
       const double e = U[i] + (U[i + 1] - U[i]) * (q + 0.5) / 8.0;
       vaE.push_back((float)e);
       vaE64.push_back((double)(float)e);
     }
   }
-  trE.push_back((float)U.back());
   const int64_t n_tr = (int64_t)trE.size(), n_va = (int64_t)vaE.size();
-  trT.assign((size_t)n_tr * mlp::kOut, 0.f);
-  for (int64_t i = 0; i < n_tr; ++i)
-    for (int m = 0; m < nm; ++m)
-      if ((mask >> m) & 1u) {
-        const double sg = table_sigma(c->tabE[m], c->tabS[m], (double)trE[i]);
-        trT[(size_t)i * mlp::kOut + m] = (float)std::log(std::max(sg, 1e-300));
-      }
-  // a material whose table has a zero sigma is not modelled
-  for (int m = 0; m < nm; ++m)
-    if ((mask >> m) & 1u)
-      for (double v : c->tabS[m])
-        if (!(v > 0.0)) { mask &= ~(1u << m); break; }
 
-  // initial weights: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)), zero biases
+  // the 1/v prior per material: sigma ~ a + b E^(-1/2), least squares in
+  // relative error over the smooth points (all points if none), a > 0, b >= 0
+  double Cab[mlp::kOut][2];
+  for (int m = 0; m < mlp::kOut; ++m) { Cab[m][0] = 1.0; Cab[m][1] = 0.0; }
+  for (int m = 0; m < nm; ++m) {
+    if (!((mask >> m) & 1u)) continue;
+    double s00 = 0, s01 = 0, s11 = 0, r0 = 0, r1 = 0, smin = INFINITY;
+    for (int pass = 0; pass < 2 && s00 == 0.0; ++pass)
+      for (size_t i = 0; i < nu; ++i) {
+        if (pass == 0 && !smooth[i]) continue;
+        const double S = std::exp(LS[m][i]), r = 1.0 / std::sqrt(U[i]), w2 = 1.0 / (S * S);
+        s00 += w2; s01 += w2 * r; s11 += w2 * r * r; r0 += w2 * S; r1 += w2 * S * r;
+        smin = std::min(smin, S);
+      }
+    const double det = s00 * s11 - s01 * s01;
+    double a = r0 / s00, b = 0.0;
+    if (det > 0.0) {
+      a = (r0 * s11 - r1 * s01) / det;
+      b = (s00 * r1 - s01 * r0) / det;
+    }
+    if (b < 0.0) { b = 0.0; a = r0 / s00; }
+    Cab[m][0] = std::max(a, 1e-3 * smin);
+    Cab[m][1] = b;
+  }
+  auto prior = [&](int m, double e) { return Cab[m][0] + Cab[m][1] / std::sqrt(e); };
+
+  // targets: log sigma minus the prior, normalised per material (mean 0,
+  // spread 1 over the training set); the normalisation is folded into W3
+  // and b3 after training
+  double mu[mlp::kOut] = {}, sd[mlp::kOut];
+  for (int m = 0; m < mlp::kOut; ++m) sd[m] = 1.0;
+  trT.assign((size_t)n_tr * mlp::kOut, 0.f);
+  if (n_tr > 0) {
+    std::vector<double> t((size_t)n_tr);
+    for (int m = 0; m < nm; ++m) {
+      if (!((mask >> m) & 1u)) continue;
+      double s1 = 0, s2 = 0;
+      for (int64_t i = 0; i < n_tr; ++i) {
+        t[i] = std::log(table_sigma(c->tabE[m], c->tabS[m], (double)trE[i]) / prior(m, (double)trE[i]));
+        s1 += t[i];
+        s2 += t[i] * t[i];
+      }
+      mu[m] = s1 / n_tr;
+      sd[m] = std::max(std::sqrt(std::max(s2 / n_tr - mu[m] * mu[m], 0.0)), 1e-3);
+      for (int64_t i = 0; i < n_tr; ++i) trT[(size_t)i * mlp::kOut + m] = (float)((t[i] - mu[m]) / sd[m]);
+    }
+  }
+
+  // initial weights: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)), zero biases;
+  // the prior is held at a = 1, b = 0 (log 1 = 0) while training
   std::vector<float> P(mlp::kParams, 0.f);
   auto fill = [&](int off, int rows, int cols, uint64_t salt) {
     const float bound = 1.f / std::sqrt((float)cols);
@@ -159,58 +240,69 @@ int vrc_train_surrogate(vrc_ctx *c, const vrc_surrogate_options *opt, vrc_surrog
   fill(mlp::kOffW1, mlp::kHid, mlp::kEmb, 1);
   fill(mlp::kOffW2, mlp::kHid, mlp::kHid, 2);
   fill(mlp::kOffW3, mlp::kOut, mlp::kHid, 3);
+  for (int m = 0; m < mlp::kOut; ++m) P[mlp::kOffC + 2 * m] = 1.f;
 
   TmpDev tmp;
-  float *d_trE, *d_trT, *d_grad, *d_m1, *d_m2, *d_loss, *d_vaE, *d_vaY;
-  VRC_CUDA(tmp.alloc((void **)&d_trE, sizeof(float) * n_tr), "allocating training data");
-  VRC_CUDA(tmp.alloc((void **)&d_trT, sizeof(float) * trT.size()), "allocating training data");
+  float *d_trE = nullptr, *d_trT = nullptr, *d_grad, *d_m1, *d_m2, *d_loss, *d_vaE, *d_vaY;
+  VRC_CUDA(tmp.alloc((void **)&d_trE, sizeof(float) * std::max<int64_t>(n_tr, 1)), "allocating training data");
+  VRC_CUDA(tmp.alloc((void **)&d_trT, sizeof(float) * std::max<size_t>(trT.size(), 1)), "allocating training data");
   VRC_CUDA(tmp.alloc((void **)&d_grad, sizeof(float) * mlp::kParams), "allocating training state");
   VRC_CUDA(tmp.alloc((void **)&d_m1, sizeof(float) * mlp::kParams), "allocating training state");
   VRC_CUDA(tmp.alloc((void **)&d_m2, sizeof(float) * mlp::kParams), "allocating training state");
   VRC_CUDA(tmp.alloc((void **)&d_loss, sizeof(float) * (o.steps + 1)), "allocating training state");
   VRC_CUDA(tmp.alloc((void **)&d_vaE, sizeof(float) * n_va), "allocating validation data");
   VRC_CUDA(tmp.alloc((void **)&d_vaY, sizeof(float) * n_va * mlp::kOut), "allocating validation data");
-  if (!(o.steps == 0 && c->mlp_ready))
-    VRC_CUDA(c->mlpParams.ensure(sizeof(float) * mlp::kParams), "allocating the surrogate");
+  VRC_CUDA(c->mlpParams.ensure(sizeof(float) * mlp::kParams), "allocating the surrogate");
   VRC_CUDA(c->mlpFlags.ensure((size_t)c->n_hash), "allocating the surrogate flags");
   float *d_P = static_cast<float *>(c->mlpParams.p);
   cudaStream_t s = c->stream;
-  VRC_CUDA(cudaMemcpy(d_trE, trE.data(), sizeof(float) * n_tr, cudaMemcpyHostToDevice), "uploading training data");
-  VRC_CUDA(cudaMemcpy(d_trT, trT.data(), sizeof(float) * trT.size(), cudaMemcpyHostToDevice), "uploading training data");
-  VRC_CUDA(cudaMemcpy(d_vaE, vaE.data(), sizeof(float) * n_va, cudaMemcpyHostToDevice), "uploading validation data");
-  const bool revalidate = o.steps == 0;
-  if (revalidate && !c->mlp_ready) return fail(VRC_ERR_STATE, "no trained surrogate to re-validate");
-  if (!revalidate)
-    VRC_CUDA(cudaMemcpy(d_P, P.data(), sizeof(float) * mlp::kParams, cudaMemcpyHostToDevice), "uploading weights");
-  VRC_CUDA(cudaMemsetAsync(d_m1, 0, sizeof(float) * mlp::kParams, s), "zeroing Adam state");
-  VRC_CUDA(cudaMemsetAsync(d_m2, 0, sizeof(float) * mlp::kParams, s), "zeroing Adam state");
-  VRC_CUDA(cudaMemsetAsync(d_loss, 0, sizeof(float) * (o.steps + 1), s), "zeroing losses");
-
-  const int n_out = __builtin_popcount(mask);
-  mlp::TrainArgs ta;
-  std::memset(&ta, 0, sizeof ta);
-  ta.params = d_P;
-  ta.E = d_trE;
-  ta.target = d_trT;
-  ta.mat_mask = mask;
-  ta.m = o.batch;
-  ta.set_n = n_tr;
-  ta.inv_count = 1.f / (float)((int64_t)o.batch * n_out);
-  ta.grad = d_grad;
-  ta.emb = mlp::make_embed(U.front(), U.back());
-  const int warm = std::min(200, std::max(1, o.steps / 20));
-  for (int step = 1; step <= o.steps; ++step) {
-    VRC_CUDA(cudaMemsetAsync(d_grad, 0, sizeof(float) * mlp::kParams, s), "zeroing the gradient");
-    ta.seed = host_mix64(o.seed ^ ((uint64_t)step << 32));
-    ta.loss = d_loss + step;
-    VRC_CUDA(mlp::launch_train(ta, s), "launching a training step");
-    const double prog = (double)(step - 1) / std::max(1, o.steps - 1);
-    double lr = o.lr * (0.02 + 0.98 * 0.5 * (1.0 + std::cos(M_PI * prog)));
-    if (step <= warm) lr *= (double)step / warm;
-    VRC_CUDA(mlp::launch_adam(d_P, d_grad, d_m1, d_m2, mlp::kParams, (float)lr, 0.9f, 0.999f, 1e-8f, step, s),
-             "launching Adam");
+  if (n_tr > 0) {
+    VRC_CUDA(cudaMemcpy(d_trE, trE.data(), sizeof(float) * n_tr, cudaMemcpyHostToDevice), "uploading training data");
+    VRC_CUDA(cudaMemcpy(d_trT, trT.data(), sizeof(float) * trT.size(), cudaMemcpyHostToDevice), "uploading training data");
   }
-  // validation
+  VRC_CUDA(cudaMemcpy(d_vaE, vaE.data(), sizeof(float) * n_va, cudaMemcpyHostToDevice), "uploading validation data");
+  VRC_CUDA(cudaMemsetAsync(d_loss, 0, sizeof(float) * (o.steps + 1), s), "zeroing losses");
+  const int n_out = __builtin_popcount(mask);
+  if (!revalidate) {
+    VRC_CUDA(cudaMemcpy(d_P, P.data(), sizeof(float) * mlp::kParams, cudaMemcpyHostToDevice), "uploading weights");
+    VRC_CUDA(cudaMemsetAsync(d_m1, 0, sizeof(float) * mlp::kParams, s), "zeroing Adam state");
+    VRC_CUDA(cudaMemsetAsync(d_m2, 0, sizeof(float) * mlp::kParams, s), "zeroing Adam state");
+    mlp::TrainArgs ta;
+    std::memset(&ta, 0, sizeof ta);
+    ta.params = d_P;
+    ta.E = d_trE;
+    ta.target = d_trT;
+    ta.mat_mask = mask;
+    ta.m = o.batch;
+    ta.set_n = n_tr;
+    ta.inv_count = 1.f / (float)((int64_t)o.batch * std::max(n_out, 1));
+    ta.grad = d_grad;
+    ta.emb = mlp::make_embed(U.front(), U.back());
+    const int warm = std::min(200, std::max(1, o.steps / 20));
+    for (int step = 1; step <= o.steps && n_tr > 0 && n_out > 0; ++step) {
+      VRC_CUDA(cudaMemsetAsync(d_grad, 0, sizeof(float) * mlp::kParams, s), "zeroing the gradient");
+      ta.seed = host_mix64(o.seed ^ ((uint64_t)step << 32));
+      ta.loss = d_loss + step;
+      VRC_CUDA(mlp::launch_train(ta, s), "launching a training step");
+      const double prog = (double)(step - 1) / std::max(1, o.steps - 1);
+      double lr = o.lr * (0.02 + 0.98 * 0.5 * (1.0 + std::cos(M_PI * prog)));
+      if (step <= warm) lr *= (double)step / warm;
+      VRC_CUDA(mlp::launch_adam(d_P, d_grad, d_m1, d_m2, mlp::kTrained, (float)lr, 0.9f, 0.999f, 1e-8f, step, s),
+               "launching Adam");
+    }
+    // fold the target normalisation into W3 and b3, and set the prior
+    VRC_CUDA(cudaMemcpyAsync(P.data(), d_P, sizeof(float) * mlp::kParams, cudaMemcpyDeviceToHost, s),
+             "reading the trained weights");
+    VRC_CUDA(cudaStreamSynchronize(s), "training the surrogate");
+    for (int m = 0; m < mlp::kOut; ++m) {
+      for (int k = 0; k < mlp::kHid; ++k) P[mlp::kOffW3 + m * mlp::kHid + k] *= (float)sd[m];
+      P[mlp::kOffB3 + m] = (float)(sd[m] * P[mlp::kOffB3 + m] + mu[m]);
+      P[mlp::kOffC + 2 * m] = (float)Cab[m][0];
+      P[mlp::kOffC + 2 * m + 1] = (float)Cab[m][1];
+    }
+    VRC_CUDA(cudaMemcpy(d_P, P.data(), sizeof(float) * mlp::kParams, cudaMemcpyHostToDevice), "uploading weights");
+  }
+  // validation: log sigma of the network (prior included) against the tables
   mlp::ApplyArgs aa;
   std::memset(&aa, 0, sizeof aa);
   aa.params = d_P;
@@ -219,15 +311,16 @@ int vrc_train_surrogate(vrc_ctx *c, const vrc_surrogate_options *opt, vrc_surrog
   aa.out = d_vaY;
   aa.mode = 0;
   aa.mat_mask = mask;
-  aa.emb = ta.emb;
+  aa.emb = mlp::make_embed(U.front(), U.back());
   aa.status = c->d_status;
   VRC_CUDA(mlp::launch_apply(aa, c->num_sms, s), "launching the validation pass");
   std::vector<float> Y((size_t)n_va * mlp::kOut), L((size_t)o.steps + 1, 0.f);
-  VRC_CUDA(cudaStreamSynchronize(s), "training the surrogate");
+  VRC_CUDA(cudaStreamSynchronize(s), "validating the surrogate");
   VRC_CUDA(cudaMemcpy(Y.data(), d_vaY, sizeof(float) * Y.size(), cudaMemcpyDeviceToHost), "reading validation");
   VRC_CUDA(cudaMemcpy(L.data(), d_loss, sizeof(float) * L.size(), cudaMemcpyDeviceToHost), "reading losses");
 
   std::vector<float> bin_err((size_t)c->n_hash, 0.f), all_err;
+  std::vector<int32_t> bin_pts((size_t)c->n_hash, 0);
   all_err.reserve((size_t)n_va);
   const double l2a = std::log2(U.front());
   for (int64_t i = 0; i < n_va; ++i) {
@@ -236,20 +329,24 @@ int vrc_train_surrogate(vrc_ctx *c, const vrc_surrogate_options *opt, vrc_surrog
       if (!((mask >> m) & 1u)) continue;
       const double sg = table_sigma(c->tabE[m], c->tabS[m], vaE64[i]);
       const double got = std::exp((double)Y[(size_t)i * mlp::kOut + m]);
-      worst = std::max(worst, (float)(std::fabs(got - sg) / sg));
+      const float err = (float)(std::fabs(got - sg) / sg);
+      worst = std::isnan(err) ? INFINITY : std::max(worst, err);
     }
     int b = (int)std::floor((std::log2(vaE64[i]) - l2a) * c->inv_bw);
     b = std::min(std::max(b, 0), c->n_hash - 1);
     bin_err[b] = std::max(bin_err[b], worst);
+    bin_pts[b] += 1;
     all_err.push_back(worst);
   }
+  // a bin is accepted when it and both neighbours were validated within tol
   std::vector<uint8_t> flags((size_t)c->n_hash, 0);
   int accepted = 0;
   float max_acc = 0.f;
+  auto bad_bin = [&](int b) { return bin_pts[b] == 0 || !(bin_err[b] <= o.tol); };
   for (int b = 0; b < c->n_hash; ++b) {
-    bool bad = bin_err[b] > o.tol || !std::isfinite(bin_err[b]);
-    if (b > 0) bad = bad || bin_err[b - 1] > o.tol;
-    if (b + 1 < c->n_hash) bad = bad || bin_err[b + 1] > o.tol;
+    bool bad = unmodelled || bad_bin(b);
+    if (b > 0) bad = bad || bad_bin(b - 1);
+    if (b + 1 < c->n_hash) bad = bad || bad_bin(b + 1);
     flags[b] = bad ? 1 : 0;
     if (!bad) { ++accepted; max_acc = std::max(max_acc, bin_err[b]); }
   }
@@ -268,6 +365,7 @@ int vrc_train_surrogate(vrc_ctx *c, const vrc_surrogate_options *opt, vrc_surrog
     report->median_rel_err = all_err.empty() ? 0.f : all_err[all_err.size() / 2];
     report->train_points = n_tr;
     report->validation_points = n_va;
+    report->smooth_fraction = nu > 1 ? (float)smooth_intervals / (float)(nu - 1) : 0.f;
   }
   return VRC_OK;
 }

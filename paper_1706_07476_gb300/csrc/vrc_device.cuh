@@ -191,7 +191,7 @@ struct Attenuation;
 // (vrc_math64.h: within 0.51 and 1.8 ulp of the exact values), indexed from the
 // float32 product Sigma l.  A void cell (Sigma = 0) has x = 0, factor exactly
 // 1 and path term l.  The float32 inputs are widened and W is tested for zero
-// with integer operations, which leaves the FP64 pipe to the 17 float64
+// with integer operations, which leaves the FP64 pipe to the 15 float64
 // arithmetic operations of a segment.  A segment's (e^-x, path term) needs
 // no ray state (terms); the score and the carry W *= e^-x do (apply), so the
 // warp-batched walk can compute the first for any lane's segment.  score()
@@ -396,9 +396,9 @@ struct UniformWalk {
     int ncell;
   };
 
-  // Sets up the walk; false if the ray misses the mesh.
+  // Sets up the walk; false if the ray misses the mesh (dn is not used).
   __device__ __forceinline__ bool init(const MeshDev &M, float px, float py, float pz, float u,
-                                       float v, float w) {
+                                       float v, float w, float = 0.f) {
     const float p[3] = {px, py, pz};
     const float d[3] = {u, v, w};
     const df inf = {INFINITY, 0.f};
@@ -482,26 +482,27 @@ struct UniformWalk {
   }
 };
 
-// Walks one ray through a uniform mesh (UniformWalk) and adds its Eq. 4
-// score to every crossed cell through `sink` (the ray's group slice of the
-// tally, or its history's slots).  The walk ends when the ray leaves the
-// mesh or after max_steps steps (then *overflow is set).  Returns the number
-// of positive-length segments walked; nlive counts the scores added to the sink.
-template <int FORM, typename Sink>
-__device__ __forceinline__ uint32_t cast_ray(const MeshDev &M, float px, float py, float pz,
-                                             float u, float v, float w, float wt, float dn,
-                                             const Sink &sink, const float *sg,
-                                             const typename Attenuation<FORM>::inv_t *inv,
-                                             int stride, bool stop_zero, bool *overflow,
-                                             uint32_t &nlive) {
-  UniformWalk W;
-  if (!W.init(M, px, py, pz, u, v, w)) return 0;
+// Walks one ray through the mesh (Walk: UniformWalk or RectWalk) and adds
+// its Eq. 4 score to every crossed cell through `sink` (the ray's group
+// slice of the tally, or its history's slots).  The walk ends when the ray
+// leaves the mesh or after max_steps steps (then *overflow is set).  Returns
+// the number of positive-length segments walked; nlive counts the scores
+// added to the sink.
+template <int FORM, typename Walk, typename Sink>
+__device__ __forceinline__ uint32_t cast_ray_walk(const MeshDev &M, float px, float py, float pz,
+                                                  float u, float v, float w, float wt, float dn,
+                                                  const Sink &sink, const float *sg,
+                                                  const typename Attenuation<FORM>::inv_t *inv,
+                                                  int stride, bool stop_zero, bool *overflow,
+                                                  uint32_t &nlive) {
+  Walk W;
+  if (!W.init(M, px, py, pz, u, v, w, dn)) return 0;
   Attenuation<FORM> att(wt);
   uint32_t nseg = 0;
   const int max_steps = M.n[0] + M.n[1] + M.n[2] + 3;
   for (int step = 0;; ++step) {
     if (stop_zero && att.dead()) break;  // every later score is +0 (opt-in)
-    const UniformWalk::Next t = W.next();
+    const typename Walk::Next t = W.next();
     // FP32 form: once every score is +0 the walk skips the loads of the next
     // cell's material and of sigma (the plain form measured faster keeping them)
     const bool live = FORM == kFormFp32 ? !att.dead() : true;
@@ -573,9 +574,9 @@ struct RectWalk {
     int ncell;
   };
 
-  // Sets up the walk; false if the ray misses the mesh.
+  // Sets up the walk; false if the ray misses the mesh (dn is not used).
   __device__ __forceinline__ bool init(const MeshDev &M, float px, float py, float pz, float u,
-                                       float v, float w) {
+                                       float v, float w, float = 0.f) {
     p[0] = px; p[1] = py; p[2] = pz;
     const float d[3] = {u, v, w};
     const df inf = {INFINITY, 0.f};
@@ -658,48 +659,6 @@ struct RectWalk {
   }
 };
 
-// cast_ray on a rectilinear mesh (RectWalk).
-template <int FORM, typename Sink>
-__device__ __forceinline__ uint32_t cast_ray_rect(const MeshDev &M, float px, float py, float pz,
-                                                  float u, float v, float w, float wt, float dn,
-                                                  const Sink &sink, const float *sg,
-                                                  const typename Attenuation<FORM>::inv_t *inv,
-                                                  int stride, bool stop_zero, bool *overflow,
-                                                  uint32_t &nlive) {
-  RectWalk W;
-  if (!W.init(M, px, py, pz, u, v, w)) return 0;
-  Attenuation<FORM> att(wt);
-  uint32_t nseg = 0;
-  const int max_steps = M.n[0] + M.n[1] + M.n[2] + 3;
-  for (int step = 0;; ++step) {
-    if (stop_zero && att.dead()) break;  // every later score is +0 (opt-in)
-    const RectWalk::Next t = W.next();
-    const bool live = FORM == kFormFp32 ? !att.dead() : true;
-    const unsigned nmat = (t.leaving || !live) ? 0u : __ldg(M.mat + t.ncell);
-
-    const float l = W.length(t, dn);
-    if (live) {
-      typename Attenuation<FORM>::score_t sc;
-      if constexpr (FORM == kFormFp32) {
-        const float2 si = *reinterpret_cast<const float2 *>(sg + W.mat * stride);
-        sc = att.score(si.x, si.y, l);
-      } else {
-        sc = att.score(sg[W.mat * stride], inv[W.mat * stride], l);
-      }
-      if (sc != 0) {
-        sink.add(W.cell, Attenuation<FORM>::to_double(sc));
-        ++nlive;
-      }
-    }
-    nseg += l > 0.f;
-
-    if (t.leaving) break;
-    if (step >= max_steps) { *overflow = true; break; }
-    W.advance(M, t, nmat);
-  }
-  return nseg;
-}
-
 // ---------------------------------------------------------------------------
 // Plain form, with the float64 work shared by the warp.
 // A float64 operation occupies GB300's FP64 pipe for a whole warp however
@@ -760,7 +719,7 @@ __device__ __forceinline__ uint32_t cast_ray_plain_warp(const MeshDev &M, bool a
   const unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   Walk W;
-  if (active) active = W.init(M, px, py, pz, u, v, w);
+  if (active) active = W.init(M, px, py, pz, u, v, w, dn);
   Attenuation<kFormPlain> att(wt);  // W at the entry of the next segment to apply
   float tau = 0.f;                   // float32 optical depth walked so far
   const float tau_dead = 760.f + (wt > 1.f ? __logf(wt) : 0.f);
@@ -867,13 +826,12 @@ __device__ __forceinline__ bool ray_setup(const CastArgs &a, int64_t r, const in
   const int g = group_of(edges, a.n_groups, (double)E);
   if (g < 0) return false;
   bool from_table = true;
-  if (SURR) {  // surrogate sigma, unless this ray's energy bin is flagged
-    const float4 *q = reinterpret_cast<const float4 *>(a.sig_ray + r * 16);
-    const float4 v0 = __ldg(q);
-    if (!isnan(v0.x)) {
+  if (SURR) {  // surrogate sigma for the leading rays (those in accepted energy bins)
+    if (r < (int64_t)__ldg(a.n_surr)) {
+      const float4 *q = reinterpret_cast<const float4 *>(a.sig_ray + r * 16);
       from_table = false;
       for (int m4 = 0; m4 < (a.xs.n_mat + 3) / 4; ++m4) {
-        const float4 v = m4 == 0 ? v0 : __ldg(q + m4);
+        const float4 v = __ldg(q + m4);
         const float s4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -900,13 +858,10 @@ __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int
   RayIn q;
   if (!ray_setup<FORM, SURR>(a, r, hash_s, edges, sig_s, inv_s, stride, c, q)) return;
   bool ovf = false;
-  if constexpr (RECT)
-    c.seg += cast_ray_rect<FORM>(a.mesh, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn,
-                                 Maker::make(a, r, q.g), sig_s, inv_s, stride, a.stop_zero != 0, &ovf,
-                                 c.live);
-  else
-    c.seg += cast_ray<FORM>(a.mesh, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn, Maker::make(a, r, q.g),
-                            sig_s, inv_s, stride, a.stop_zero != 0, &ovf, c.live);
+  typedef typename std::conditional<RECT, RectWalk, UniformWalk>::type Walk;
+  c.seg += cast_ray_walk<FORM, Walk>(a.mesh, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn,
+                                     Maker::make(a, r, q.g), sig_s, inv_s, stride, a.stop_zero != 0,
+                                     &ovf, c.live);
   c.ovf += ovf;
 }
 

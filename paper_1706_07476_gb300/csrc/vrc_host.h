@@ -232,8 +232,11 @@ constexpr int64_t kAutoSortMin = 65536;
 // position of ray i.
 // With spatial set, the key is (group, spatial block of the start point)
 // instead, for point events (the direction is not used).
+// With n_accepted set, rays in the learned surrogate's accepted energy bins
+// are put first and *n_accepted receives the device address of their count.
 int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in = nullptr,
-              uint32_t *carry_out = nullptr, bool spatial = false);
+              uint32_t *carry_out = nullptr, bool spatial = false,
+              const uint32_t **n_accepted = nullptr);
 // Sort (optional), surrogate (optional) and cast of a device batch on stream s.
 int cast_device(vrc_ctx *c, RayPtrs rp, cudaStream_t s);
 // Device view of a ray batch: device arrays as given, host arrays copied

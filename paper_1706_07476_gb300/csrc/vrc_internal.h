@@ -78,7 +78,8 @@ struct CastArgs {
   const double *edges;  // [n_groups+1] or nullptr (single group, every energy)
   int32_t n_groups;
   RayPtrs rays;
-  const float *sig_ray; // [n][16] per-ray sigma from the surrogate (NaN in [0] = use the table), or nullptr
+  const float *sig_ray; // [n][16] per-ray sigma from the surrogate for rays r < *n_surr, or nullptr
+  const uint32_t *n_surr; // device count of leading rays with surrogate sigma (with sig_ray)
   double *tally;        // [n_groups][ncells]
   const uint32_t *hist; // [n] history id of each ray (per-history cast only)
   HistTable htab;       // per-history cast only

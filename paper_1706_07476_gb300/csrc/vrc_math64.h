@@ -26,8 +26,10 @@
 // 1], Sterbenz) and rounded once otherwise, where |e^y - 1| >= 0.49; for
 // n = 0 the second line is q itself, which keeps full relative accuracy as
 // y -> 0.  A 256-entry table (4 KiB) rather than 64 entries saves one
-// series term: 17 float64 operations per segment instead of 18, 3.6 % of the
-// plain cast's time on GB300.
+// series term.  n as a float64 and the exact product 2^m T_hi are built from
+// integer fields, not with float64 arithmetic: 15 float64 operations per
+// segment in the plain cast (13 here, the product Sigma l and the path term's
+// division by Sigma).
 //
 // Range: n >= -261632 keeps m >= -1022, so 2^m is a normal number built from
 // its exponent bits (y >= -708.3 always qualifies).  Below it e^y < 2^-1021,
@@ -62,6 +64,16 @@ VRC_M64_FN double bits_to_double(uint64_t b) {
 #endif
 }
 
+VRC_M64_FN uint64_t double_bits(double d) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(d);
+#else
+  uint64_t b;
+  memcpy(&b, &d, sizeof b);
+  return b;
+#endif
+}
+
 VRC_M64_FN uint32_t float_bits(float f) {
 #ifdef __CUDA_ARCH__
   return __float_as_uint(f);
@@ -92,12 +104,10 @@ VRC_M64_FN float fmaf_rn(float a, float b, float c) {
 constexpr float kInvCf = 369.32993046757463f;
 constexpr double kC1 = 0x1.62e42fefa39efp-9;
 constexpr double kC2 = 0x1.abc9e3b39803fp-64;
-// 1.5 * 2^23 and 1.5 * 2^52: adding one rounds to an integer held in the low
-// mantissa bits (float32 for |n| < 2^22, float64 for |n| < 2^51).
+// 1.5 * 2^23: adding it rounds a float32 to an integer held in the low
+// mantissa bits (for |n| < 2^22).
 constexpr float kRoundF = 12582912.0f;
-constexpr double kRound = 6755399441055744.0;
 constexpr uint32_t kRoundFBits = 0x4b400000u;
-constexpr uint64_t kRoundBits = 0x4338000000000000ull;
 // Smallest n with m = floor(n/256) >= -1022.
 constexpr int32_t kNMin = -261632;
 
@@ -376,13 +386,26 @@ VRC_M64_FN void table_entry(uint32_t j, double *hi, double *lo) {
 #endif
 }
 
+// The float64 equal to an integer-valued float32 f (|f| < 2^24), built from
+// f's sign, exponent (rebiased by 1023 - 127) and mantissa with integer
+// operations; 0 maps to +0.
+VRC_M64_FN double int_float_to_double(float f) {
+  const uint32_t b = float_bits(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  if (e == 0u) return 0.0;
+  return bits_to_double(((uint64_t)((b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xfffffu)) << 32) |
+                        ((uint64_t)(b << 29)));
+}
+
 // Writes e^y to *ey and e^y - 1 to *em1, for y <= 0 (not NaN); yf is y
-// rounded to float32 (or any float32 within 2^-23 |y| of it).
+// rounded to float32 (or any float32 within 2^-23 |y| of it).  The integer n
+// (as a float64) and 2^m T_hi are formed with integer operations, which
+// leaves 13 float64 operations here.
 VRC_M64_FN void exp_expm1(double y, float yf, double *ey, double *em1) {
   yf = yf > -1000.f ? yf : -1000.f;
   const float tf = fmaf_rn(yf, kInvCf, kRoundF);
   const int32_t n = (int32_t)(float_bits(tf) - kRoundFBits);  // nearest(256 yf / ln2)
-  const double nd = bits_to_double(kRoundBits + (uint64_t)(int64_t)n) - kRound;
+  const double nd = int_float_to_double(tf - kRoundF);         // n, exactly (|n| < 2^19)
   double r = fmad(-nd, kC1, y);  // exact
   r = fmad(-nd, kC2, r);
   double p = 8.333333333333333e-03;       // 1/5!
@@ -396,7 +419,9 @@ VRC_M64_FN void exp_expm1(double y, float yf, double *ey, double *em1) {
   const uint32_t m = (uint32_t)(n >> 8);  // floor(n / 256), two's complement
   const double s = bits_to_double((uint64_t)(m + 1023u) << 52);  // 2^m
   const double c = fmad(thi, q, tlo);
-  const double a = s * thi;  // exact
+  // a = 2^m T_hi (exact): T_hi in [1, 2), so m goes into its exponent field
+  // (m >= -1022 in range keeps a normal; out of range a is not used)
+  const double a = bits_to_double(double_bits(thi) + ((uint64_t)(int64_t)(int32_t)m << 52));
   const bool in_range = n >= kNMin;
   *ey = in_range ? fmad(s, c, a) : 0.0;
   *em1 = in_range ? fmad(s, c, a - 1.0) : -1.0;

@@ -2,8 +2,10 @@
 // one kernel) and Adam.  The training step's matrix products are warp-level
 // mma.sync.m16n8k16 with bfloat16 operands and float32 accumulation; operand
 // tiles come from shared memory through ldmatrix (.trans where the stored
-// layout is the transpose of the operand).  The per-ray forward pass used by
-// the cast runs on tcgen05 (vrc_mlp_tc.cu).
+// layout is the transpose of the operand).  The forward products take each
+// activation as a bfloat16 pair hi + lo (two products into one
+// accumulator), as the per-ray forward pass on tcgen05 does (vrc_mlp_tc.cu);
+// the backward products use the hi parts (gradient noise of 2^-9 relative).
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -107,23 +109,34 @@ __device__ __forceinline__ void add_col_sums(const float (&d)[4], float *dst, in
 // ---------------------------------------------------------------------------
 constexpr int LDH = kHid + 1;  // float32 h2 rows, padded so row-wise reads spread over banks
 constexpr size_t kTrainSmem =
-    sizeof(bf16) * (size_t)(kHid * LD64 + kHid * LD128 + BM * LD64 + 2 * BM * LD128) +
-    sizeof(float) * (size_t)(BM * LDH + kOut * kHid + BM * kOut + 2 * BM * kHid + 2 * kHid + kOut + BM);
+    sizeof(bf16) * (size_t)(kHid * LD64 + kHid * LD128 + 2 * BM * LD64 + 3 * BM * LD128 + 2 * BM * kHid) +
+    sizeof(float) * (size_t)(BM * LDH + kOut * kHid + 2 * BM * kOut + 2 * kHid + 3 * kOut + BM);
+
+// Two floats as bfloat16 pairs hi = bf16(v), lo = bf16(v - hi).
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  hi = *reinterpret_cast<const uint32_t *>(&h);
+  lo = pack2(a - hf.x, b - hf.y);
+}
 
 __global__ void __launch_bounds__(kTrainThreads) k_mlp_train(TrainArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   bf16 *W1s = reinterpret_cast<bf16 *>(smem);  // [128][72]
   bf16 *W2s = W1s + kHid * LD64;               // [128][136]
-  bf16 *X0 = W2s + kHid * LD128;               // [64][72]
-  bf16 *H1 = X0 + BM * LD64;                   // [64][136]
-  bf16 *DZ2 = H1 + BM * LD128;                 // [64][136]
-  float *H2 = reinterpret_cast<float *>(DZ2 + BM * LD128);  // [64][129] float32 h2; later dz1 (bf16)
-  float *W3f = H2 + BM * LDH;                  // [16][128] bf16-valued W3 held in float32
+  bf16 *X0 = W2s + kHid * LD128;               // [64][72] features, hi
+  bf16 *X0l = X0 + BM * LD64;                  // [64][72] features, lo
+  bf16 *H1 = X0l + BM * LD64;                  // [64][136] h1, hi
+  bf16 *H1l = H1 + BM * LD128;                 // [64][136] h1, lo
+  bf16 *DZ2 = H1l + BM * LD128;                // [64][136]
+  bf16 *D1 = DZ2 + BM * LD128;                 // [64][128] silu'(z1)
+  bf16 *D2 = D1 + BM * kHid;                   // [64][128] silu'(z2)
+  float *H2 = reinterpret_cast<float *>(D2 + BM * kHid);  // [64][129] float32 h2; later dz1 (bf16)
+  float *W3f = H2 + BM * LDH;                  // [16][128] W3, float32
   float *DY = W3f + kOut * kHid;               // [64][16]
-  float *D1 = DY + BM * kOut;                  // [64][128] silu'(z1)
-  float *D2 = D1 + BM * kHid;                  // [64][128] silu'(z2)
-  float *bs = D2 + BM * kHid;                  // b1, b2, b3
-  float *Es = bs + 2 * kHid + kOut;            // [64]
+  float *Q = DY + BM * kOut;                   // [64][16] prior a + b E^(-1/2)
+  float *bs = Q + BM * kOut;                   // b1, b2, b3, C [16][2]
+  float *Es = bs + 2 * kHid + 3 * kOut;        // [64]
   __shared__ int64_t src[BM];
   __shared__ float red[kTrainThreads / 32];
 
@@ -133,9 +146,10 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train(TrainArgs a) {
 
   for (int i = tid; i < kHid * kEmb; i += kTrainThreads) W1s[(i / kEmb) * LD64 + i % kEmb] = __float2bfloat16_rn(P[kOffW1 + i]);
   for (int i = tid; i < kHid * kHid; i += kTrainThreads) W2s[(i / kHid) * LD128 + i % kHid] = __float2bfloat16_rn(P[kOffW2 + i]);
-  for (int i = tid; i < kOut * kHid; i += kTrainThreads) W3f[i] = __bfloat162float(__float2bfloat16_rn(P[kOffW3 + i]));
+  for (int i = tid; i < kOut * kHid; i += kTrainThreads) W3f[i] = P[kOffW3 + i];
   for (int i = tid; i < kHid; i += kTrainThreads) { bs[i] = P[kOffB1 + i]; bs[kHid + i] = P[kOffB2 + i]; }
   if (tid < kOut) bs[2 * kHid + tid] = P[kOffB3 + tid];
+  if (tid < 2 * kOut) bs[2 * kHid + kOut + tid] = P[kOffC + tid];
   if (tid < BM) {
     const int64_t R = (int64_t)blockIdx.x * BM + tid;
     int64_t s = -1;
@@ -148,7 +162,10 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train(TrainArgs a) {
     const int r = i / kFreq, f = i % kFreq;
     float sn, cs;
     embed_pair(a.emb, Es[r], f, &sn, &cs);
-    *reinterpret_cast<uint32_t *>(X0 + r * LD64 + 2 * f) = pack2(sn, cs);
+    uint32_t hi, lo;
+    split2(sn, cs, hi, lo);
+    *reinterpret_cast<uint32_t *>(X0 + r * LD64 + 2 * f) = hi;
+    *reinterpret_cast<uint32_t *>(X0l + r * LD64 + 2 * f) = lo;
   }
   __syncthreads();
 
@@ -157,14 +174,17 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train(TrainArgs a) {
   {
     float acc[16][4] = {};
     for (int k0 = 0; k0 < kEmb; k0 += 16) {
-      uint32_t af[4];
+      uint32_t af[4], al[4];
       ldm_x4(af, a_rows(X0, LD64, rw, k0, lane));
+      ldm_x4(al, a_rows(X0l, LD64, rw, k0, lane));
 #pragma unroll
       for (int np = 0; np < 8; ++np) {
         uint32_t bf[4];
         ldm_x4(bf, b_rows(W1s, LD64, np * 16, k0, lane));
         mma_bf16(acc[2 * np], af, bf[0], bf[1]);
         mma_bf16(acc[2 * np + 1], af, bf[2], bf[3]);
+        mma_bf16(acc[2 * np], al, bf[0], bf[1]);
+        mma_bf16(acc[2 * np + 1], al, bf[2], bf[3]);
       }
     }
 #pragma unroll
@@ -174,9 +194,11 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train(TrainArgs a) {
       for (int h = 0; h < 2; ++h) {
         const int row = rw + g + 8 * h;
         const float z0 = acc[nt][2 * h] + bs[c], z1 = acc[nt][2 * h + 1] + bs[c + 1];
-        *reinterpret_cast<uint32_t *>(H1 + row * LD128 + c) = pack2(silu(z0), silu(z1));
-        D1[row * kHid + c] = silu_grad(z0);
-        D1[row * kHid + c + 1] = silu_grad(z1);
+        uint32_t hi, lo;
+        split2(silu(z0), silu(z1), hi, lo);
+        *reinterpret_cast<uint32_t *>(H1 + row * LD128 + c) = hi;
+        *reinterpret_cast<uint32_t *>(H1l + row * LD128 + c) = lo;
+        *reinterpret_cast<uint32_t *>(D1 + row * kHid + c) = pack2(silu_grad(z0), silu_grad(z1));
       }
     }
   }
@@ -185,14 +207,17 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train(TrainArgs a) {
   {
     float acc[16][4] = {};
     for (int k0 = 0; k0 < kHid; k0 += 16) {
-      uint32_t af[4];
+      uint32_t af[4], al[4];
       ldm_x4(af, a_rows(H1, LD128, rw, k0, lane));
+      ldm_x4(al, a_rows(H1l, LD128, rw, k0, lane));
 #pragma unroll
       for (int np = 0; np < 8; ++np) {
         uint32_t bf[4];
         ldm_x4(bf, b_rows(W2s, LD128, np * 16, k0, lane));
         mma_bf16(acc[2 * np], af, bf[0], bf[1]);
         mma_bf16(acc[2 * np + 1], af, bf[2], bf[3]);
+        mma_bf16(acc[2 * np], al, bf[0], bf[1]);
+        mma_bf16(acc[2 * np + 1], al, bf[2], bf[3]);
       }
     }
 #pragma unroll
@@ -204,8 +229,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train(TrainArgs a) {
         const float z0 = acc[nt][2 * h] + bs[kHid + c], z1 = acc[nt][2 * h + 1] + bs[kHid + c + 1];
         H2[row * LDH + c] = silu(z0);
         H2[row * LDH + c + 1] = silu(z1);
-        D2[row * kHid + c] = silu_grad(z0);
-        D2[row * kHid + c + 1] = silu_grad(z1);
+        *reinterpret_cast<uint32_t *>(D2 + row * kHid + c) = pack2(silu_grad(z0), silu_grad(z1));
       }
     }
   }
@@ -216,9 +240,15 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train(TrainArgs a) {
   {
     const int r = tid >> 1, m0 = (tid & 1) * 8;
     const int64_t s = src[r];
+    const float rs = rsqrtf(Es[r]);
+    const float *C = bs + 2 * kHid + kOut;
     float y[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) y[j] = bs[2 * kHid + m0 + j];
+    for (int j = 0; j < 8; ++j) {  // b3 and the prior log(a + b E^(-1/2))
+      const float q = fmaf(C[2 * (m0 + j) + 1], rs, C[2 * (m0 + j)]);
+      Q[r * kOut + m0 + j] = q;
+      y[j] = bs[2 * kHid + m0 + j] + logf(q);
+    }
     const float *h = H2 + r * LDH;
     for (int k = 0; k < kHid; ++k) {
       const float hk = h[k];
@@ -252,7 +282,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train(TrainArgs a) {
         gw[m] = fmaf(dy, hk, gw[m]);
         dot = fmaf(dy, W3f[m * kHid + k], dot);
       }
-      const float dz = dot * D2[r * kHid + k];
+      const float dz = dot * __bfloat162float(D2[r * kHid + k]);
       DZ2[r * LD128 + k] = __float2bfloat16_rn(dz);
       db += dz;
     }
@@ -260,9 +290,17 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train(TrainArgs a) {
     for (int m = 0; m < kOut; ++m) atomicAdd(a.grad + kOffW3 + m * kHid + k, gw[m]);
     atomicAdd(a.grad + kOffB2 + k, db);
     if (tid < kOut) {
-      float sb = 0.f;
-      for (int r = 0; r < BM; ++r) sb += DY[r * kOut + tid];
+      // b3, and the prior: dy/da = 1/q, dy/db = E^(-1/2)/q
+      float sb = 0.f, sa = 0.f, sc = 0.f;
+      for (int r = 0; r < BM; ++r) {
+        const float dy = DY[r * kOut + tid], iq = 1.f / Q[r * kOut + tid];
+        sb += dy;
+        sa = fmaf(dy, iq, sa);
+        sc = fmaf(dy * iq, rsqrtf(Es[r]), sc);
+      }
       atomicAdd(a.grad + kOffB3 + tid, sb);
+      atomicAdd(a.grad + kOffC + 2 * tid, sa);
+      atomicAdd(a.grad + kOffC + 2 * tid + 1, sc);
     }
   }
   __syncthreads();
@@ -314,8 +352,8 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_train(TrainArgs a) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int row = rw + g + 8 * h;
-        dz[2 * h] = acc[nt][2 * h] * D1[row * kHid + c];
-        dz[2 * h + 1] = acc[nt][2 * h + 1] * D1[row * kHid + c + 1];
+        dz[2 * h] = acc[nt][2 * h] * __bfloat162float(D1[row * kHid + c]);
+        dz[2 * h + 1] = acc[nt][2 * h + 1] * __bfloat162float(D1[row * kHid + c + 1]);
         *reinterpret_cast<uint32_t *>(DZ1 + row * LD128 + c) = pack2(dz[2 * h], dz[2 * h + 1]);
       }
       add_col_sums(dz, a.grad + kOffB1, c, lane);

@@ -3,16 +3,22 @@
 //
 // The network maps one energy to log Sigma_t of up to 16 materials:
 //   x = (log10 E - l0) * inv_range,  features sin(pi f_k x), cos(pi f_k x),
-//   f_k = 2^(11k/31), k = 0..31 (64 features, interleaved sin/cos);
+//   f_k = 2^(5k/31), k = 0..31 (64 features, interleaved sin/cos);
 //   h1 = silu(W1 x + b1) (64 -> 128), h2 = silu(W2 h1 + b2) (128 -> 128),
-//   y = W3 h2 + b3 (128 -> 16).
+//   y = W3 h2 + b3 + log(a + b E^(-1/2)) (128 -> 16).
+// The last term is a fixed per-material prior, the 1/v shape of a total
+// cross section (a_m > 0, b_m >= 0, fitted to the table before training and
+// not trained); the network learns the rest.
 // Parameters are float32 masters in one array: W1 [128][64], b1, W2
-// [128][128], b2, W3 [16][128], b3.  Kernels round every weight to bfloat16.
-// The two 128-wide layers run on the tensor cores (bfloat16 operands,
-// float32 accumulation: tcgen05 in the forward pass, mma.sync in training);
-// the 128 -> 16 output layer runs in float32 on the CUDA cores from float32
-// h2 (2,048 FMAs per ray), because rounding h2 to bfloat16 would put about
-// 1e-2 of noise on log sigma, ten times the accepted error of the surrogate.
+// [128][128], b2, W3 [16][128], b3, C [16][2] (a_m, b_m).  W1 and W2 are
+// rounded to bfloat16 and run on the tensor cores (tcgen05 in the forward
+// pass, mma.sync in training) with float32 accumulation; their inputs (the
+// features and h1) enter as a pair of bfloat16 values, hi = bf16(v) and
+// lo = bf16(v - hi), two products into one accumulator, so the activations
+// keep about 16 significant bits (a single bfloat16 rounding, 2^-9, puts
+// about 1e-3 of noise on log sigma, the accepted error of the surrogate).
+// The 128 -> 16 output layer runs in float32 on the CUDA cores, W3 and h2 in
+// float32 (2,048 FMAs per ray).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -22,7 +28,7 @@ namespace vrc {
 namespace mlp {
 
 constexpr int kFreq = 32;
-constexpr double kFreqMaxLog2 = 11.0;  // highest embedding frequency 2^11
+constexpr double kFreqMaxLog2 = 5.0;  // highest embedding frequency 2^5
 constexpr int kEmb = 64;
 constexpr int kHid = 128;
 constexpr int kOut = 16;
@@ -32,7 +38,9 @@ constexpr int kOffW2 = kOffB1 + kHid;
 constexpr int kOffB2 = kOffW2 + kHid * kHid;
 constexpr int kOffW3 = kOffB2 + kHid;
 constexpr int kOffB3 = kOffW3 + kOut * kHid;
-constexpr int kParams = kOffB3 + kOut;  // 26,896
+constexpr int kOffC = kOffB3 + kOut;     // prior coefficients (a_m, b_m)
+constexpr int kParams = kOffC + 2 * kOut;  // 26,928
+constexpr int kTrained = kOffC;          // Adam updates parameters [0, kTrained)
 
 struct Embed {
   float l0, inv_range;   // x = (log10 E - l0) * inv_range
@@ -68,9 +76,11 @@ cudaError_t launch_adam(float *params, const float *grad, float *m1, float *m2, 
                         float beta1, float beta2, float eps, int step, cudaStream_t s);
 
 // Forward pass for n energies.  mode 0: y = log sigma to out[n][16].
-// mode 1: sigma = exp(y) to out[n][16], with out[i][0] = NaN when the ray's
-// hash bin is flagged (flags[bin] != 0) or its energy lies outside
-// [e_first, e_last]; outputs with bit j clear in mat_mask are written as 0.
+// mode 1: sigma = (a + b E^(-1/2)) exp(W3 h2 + b3) to out[n][16]; outputs
+// with bit j clear in mat_mask are written as 0.  With flags set, out[i][0]
+// = NaN when the ray's hash bin is flagged (flags[bin] != 0) or its energy
+// lies outside [e_first, e_last].  With n_limit set, only rows below
+// min(n, *n_limit) are evaluated (a device count, read by the kernel).
 struct ApplyArgs {
   const float *params;
   const float *E;          // energies, or nullptr when aos is set
@@ -84,6 +94,7 @@ struct ApplyArgs {
   float l2min, inv_bw;
   double e_first, e_last;
   Embed emb;
+  const uint32_t *n_limit; // device row count to evaluate, or nullptr (all n rows)
   unsigned int *status;    // kStatusTimeout is set here if a tensor-core wait gives up (may be nullptr)
 };
 

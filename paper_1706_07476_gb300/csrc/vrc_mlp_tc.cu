@@ -1,21 +1,26 @@
 // Per-ray forward pass of the learned cross-section surrogate on the
 // fifth-generation tensor cores (tcgen05, accumulators in tensor memory).
 //
-// One persistent block per SM holds the bfloat16 weights once and runs four
+// One persistent block per SM holds the bfloat16 weights once and runs two
 // independent groups of 128 threads (four warps each), each on its own tiles
 // of 128 rays with its own operand buffer, mbarrier, named barrier and 128
 // tensor-memory columns.  Thread t of a group owns ray t of the tile, which
 // is row t of every matrix and lane t of the tensor memory (warp j of the
-// group reads lane quarter j).  Per tile:
-//   1. each thread writes its ray's 64 embedding features (bfloat16) to A0;
-//   2. one thread issues D = A0 W1^T (M = N = 128, K = 64, four K = 16
-//      steps) into the group's columns and commits to the group's mbarrier;
-//   3. each thread loads its row of D, adds b1, applies SiLU, rounds to
-//      bfloat16 and writes the row to A1;
-//   4. D = A1 W2^T (K = 128, eight steps) into the same columns;
+// group reads lane quarter j).  Every activation enters the tensor cores as
+// a pair of bfloat16 matrices, hi = bf16(v) and lo = bf16(v - hi), whose two
+// products go into one accumulator (about 16 significant bits per value).
+// Per tile:
+//   1. each thread writes its ray's 64 embedding features to A0hi, A0lo;
+//   2. one thread issues D = A0hi W1^T + A0lo W1^T (M = N = 128, K = 64, four
+//      K = 16 steps each) into the group's columns and commits to the
+//      group's mbarrier;
+//   3. each thread loads its row of D, adds b1, applies SiLU and writes the
+//      row's hi and lo parts to A1hi, A1lo;
+//   4. D = A1hi W2^T + A1lo W2^T (K = 128, eight steps each) into the same
+//      columns;
 //   5. each thread loads its row, h2 = SiLU(D + b2) in float32, and forms the
-//      128 -> 16 output layer on the CUDA cores (2,048 FMAs), then writes
-//      log sigma or sigma.
+//      float32 128 -> 16 output layer on the CUDA cores (2,048 FMAs), adds the
+//      1/v prior and writes log sigma or sigma.
 // Operands live in shared memory in the canonical K-major layout without
 // swizzle: 8-row x 16-byte core matrices, consecutive along K 128 bytes
 // apart (leading byte offset) and along rows K*16 bytes apart (stride byte
@@ -35,23 +40,25 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 constexpr int kTile = 128;            // rays per tile: the MMA's M and the tensor-memory lanes
-constexpr int kGroups = 4;            // independent groups of 128 threads per block
+constexpr int kGroups = 2;            // independent groups of 128 threads per block
 constexpr int kTcThreads = 128 * kGroups;
-constexpr uint32_t kTmemCols = 512;   // allocated once per block; group g uses columns 128 g ..
+constexpr uint32_t kTmemCols = 256;   // allocated once per block; group g uses columns 128 g ..
 constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before a wait gives up
 
 // shared memory (bytes from the block's base)
 constexpr uint32_t kSW1 = 0;          // W1 [128][64] bfloat16, 16 KiB
 constexpr uint32_t kSW2 = 16384;      // W2 [128][128], 32 KiB
-constexpr uint32_t kSW3 = 49152;      // W3 transposed, [128][16] float32 (bfloat16 values), 8 KiB
-constexpr uint32_t kSB = 57344;       // b1, b2, b3 float32 (272 values)
-constexpr uint32_t kSBar = 58432;     // per group an mbarrier (8 B); then the tensor-memory address
-// Per group one 32 KiB operand buffer: A1 [128][128], whose first 16 KiB also
-// hold A0 [128][64] (A0 is read only by the layer-1 MMA, which has completed
-// before A1 is written; A1 is read only by the layer-2 MMA, which has
-// completed before the next tile's A0 is written).
+constexpr uint32_t kSW3 = 49152;      // W3 transposed, [128][16] float32, 8 KiB
+constexpr uint32_t kSB = 57344;       // b1, b2, b3, then the prior C [16][2] (float32, 304 values)
+constexpr uint32_t kSBar = 58624;     // per group an mbarrier (8 B); then the tensor-memory address
+// Per group one 64 KiB operand buffer: A1hi [128][128] at 0 and A1lo at
+// 32 KiB; A0hi [128][64] at 0 and A0lo at 16 KiB share A1hi's bytes (A0 is
+// read only by the layer-1 MMAs, which have completed before A1 is written;
+// A1 is read only by the layer-2 MMAs, which have completed before the next
+// tile's A0 is written).
 constexpr uint32_t kSGroup = 59392;
-constexpr uint32_t kGroupBytes = 32768;
+constexpr uint32_t kGroupBytes = 65536;
+constexpr uint32_t kA0Lo = 16384, kA1Lo = 32768;
 constexpr uint32_t kSmemTc = kSGroup + kGroups * kGroupBytes;  // 190,464
 
 // Byte offset of element (r, k) of a K-column matrix in the core-matrix layout.
@@ -61,6 +68,15 @@ __device__ __forceinline__ uint32_t cm_off(int r, int k, int K) {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Two floats as bfloat16 pairs hi = bf16(v), lo = bf16(v - hi) (first value
+// in the low half of each word).
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  hi = *reinterpret_cast<const uint32_t *>(&h);
+  lo = pack2(a - hf.x, b - hf.y);
 }
 
 // Shared-memory matrix descriptor: start address, leading and stride byte
@@ -153,6 +169,11 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int g = tid >> 7, gt = tid & 127;  // group, thread (= row) within the group
+  // rows to evaluate: all n, or the device count (e.g. the accepted rays of a cast)
+  const int64_t n = a.n_limit ? min(a.n, (int64_t)*a.n_limit) : a.n;
+  const int64_t tiles = (n + kTile - 1) / kTile;
+  if ((int64_t)blockIdx.x * kGroups >= tiles) return;  // the whole block has no tile
+
   float *W3f = reinterpret_cast<float *>(smem + kSW3);
   float *bs = reinterpret_cast<float *>(smem + kSB);
   const uint32_t bar = smem_u32(smem + kSBar + 8 * g);
@@ -163,10 +184,11 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
 
   stage_weights(smem, kSW1, P + kOffW1, kEmb);
   stage_weights(smem, kSW2, P + kOffW2, kHid);
-  for (int i = tid; i < kOut * kHid; i += kTcThreads)  // W3[m][k] -> W3f[k][m]
-    W3f[(i % kHid) * kOut + i / kHid] = __bfloat162float(__float2bfloat16_rn(P[kOffW3 + i]));
+  for (int i = tid; i < kOut * kHid; i += kTcThreads)  // W3[m][k] -> W3f[k][m], float32
+    W3f[(i % kHid) * kOut + i / kHid] = P[kOffW3 + i];
   for (int i = tid; i < kHid; i += kTcThreads) { bs[i] = P[kOffB1 + i]; bs[kHid + i] = P[kOffB2 + i]; }
   if (tid < kOut) bs[2 * kHid + tid] = P[kOffB3 + tid];
+  if (tid < 2 * kOut) bs[2 * kHid + kOut + tid] = P[kOffC + tid];
   if (gt == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -181,36 +203,42 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
   const uint32_t tmem_row = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lane quarter
   const uint32_t sA0 = smem_u32(A0), sA1 = smem_u32(A1);
   const uint32_t sW1 = smem_u32(smem + kSW1), sW2 = smem_u32(smem + kSW2);
+  const float *C = bs + 2 * kHid + kOut;  // prior (a_m, b_m)
 
-  const int64_t tiles = (a.n + kTile - 1) / kTile;
   for (int64_t tile = (int64_t)blockIdx.x * kGroups + g; tile < tiles; tile += (int64_t)gridDim.x * kGroups) {
     const int64_t row = tile * kTile + gt;
-    const float E = row < a.n ? (a.aos ? __ldg(a.aos + 2 * row + 1).z : a.E[row]) : 1.0f;
+    const float E = row < n ? (a.aos ? __ldg(a.aos + 2 * row + 1).z : a.E[row]) : 1.0f;
 
-    // 1. embedding row: features 2f, 2f + 1 = sin, cos of pi f_f x
+    // 1. embedding row: features 2f, 2f + 1 = sin, cos of pi f_f x, as hi and lo
     const float x = embed_x(a.emb, E);
 #pragma unroll
     for (int kc = 0; kc < kEmb / 8; ++kc) {
-      uint32_t w[4];
+      uint32_t wh[4], wl[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         float sn, cs;
         embed_pair_x(a.emb, x, kc * 4 + q, &sn, &cs);
-        w[q] = pack2(sn, cs);
+        split2(sn, cs, wh[q], wl[q]);
       }
-      *reinterpret_cast<uint4 *>(A0 + cm_off(gt, kc * 8, kEmb)) = make_uint4(w[0], w[1], w[2], w[3]);
+      const uint32_t o = cm_off(gt, kc * 8, kEmb);
+      *reinterpret_cast<uint4 *>(A0 + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+      *reinterpret_cast<uint4 *>(A0 + kA0Lo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
     }
     fence_async_smem();
     fence_before();
     group_sync(g);
 
-    // 2. D = A0 W1^T
+    // 2. D = A0hi W1^T + A0lo W1^T
     if (gt == 0) {
       fence_after();
 #pragma unroll
       for (int kk = 0; kk < kEmb / 16; ++kk)
         mma_bf16_tc(tmem, smem_desc(sA0 + kk * 256, 128, kEmb * 16), smem_desc(sW1 + kk * 256, 128, kEmb * 16),
                     kk > 0);
+#pragma unroll
+      for (int kk = 0; kk < kEmb / 16; ++kk)
+        mma_bf16_tc(tmem, smem_desc(sA0 + kA0Lo + kk * 256, 128, kEmb * 16),
+                    smem_desc(sW1 + kk * 256, 128, kEmb * 16), 1);
       mma_commit(bar);
     }
     if (group_sync_or(g, !wait_phase(bar, 0))) {
@@ -219,33 +247,39 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
     }
     fence_after();
 
-    // 3. h1 = SiLU(D + b1) as bfloat16 into A1
+    // 3. h1 = SiLU(D + b1) as hi and lo bfloat16 into A1hi, A1lo
 #pragma unroll
     for (int c = 0; c < kHid / 32; ++c) {
       uint32_t r[32];
       tmem_ld32(r, tmem_row + c * 32);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        uint32_t w[4];
+        uint32_t wh[4], wl[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int j = q * 8 + 2 * e, k = c * 32 + j;
-          w[e] = pack2(silu(__uint_as_float(r[j]) + bs[k]), silu(__uint_as_float(r[j + 1]) + bs[k + 1]));
+          split2(silu(__uint_as_float(r[j]) + bs[k]), silu(__uint_as_float(r[j + 1]) + bs[k + 1]), wh[e], wl[e]);
         }
-        *reinterpret_cast<uint4 *>(A1 + cm_off(gt, c * 32 + q * 8, kHid)) = make_uint4(w[0], w[1], w[2], w[3]);
+        const uint32_t o = cm_off(gt, c * 32 + q * 8, kHid);
+        *reinterpret_cast<uint4 *>(A1 + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+        *reinterpret_cast<uint4 *>(A1 + kA1Lo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
       }
     }
     fence_async_smem();
     fence_before();
     group_sync(g);
 
-    // 4. D = A1 W2^T
+    // 4. D = A1hi W2^T + A1lo W2^T
     if (gt == 0) {
       fence_after();
 #pragma unroll
       for (int kk = 0; kk < kHid / 16; ++kk)
         mma_bf16_tc(tmem, smem_desc(sA1 + kk * 256, 128, kHid * 16), smem_desc(sW2 + kk * 256, 128, kHid * 16),
                     kk > 0);
+#pragma unroll
+      for (int kk = 0; kk < kHid / 16; ++kk)
+        mma_bf16_tc(tmem, smem_desc(sA1 + kA1Lo + kk * 256, 128, kHid * 16),
+                    smem_desc(sW2 + kk * 256, 128, kHid * 16), 1);
       mma_commit(bar);
     }
     if (group_sync_or(g, !wait_phase(bar, 1))) {
@@ -254,7 +288,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
     }
     fence_after();
 
-    // 5. h2 = SiLU(D + b2) in float32, y = W3 h2 + b3 on the CUDA cores
+    // 5. h2 = SiLU(D + b2) in float32, W3 h2 + b3 on the CUDA cores
     float p[kOut];
 #pragma unroll
     for (int m = 0; m < kOut; ++m) p[m] = bs[2 * kHid + m];
@@ -279,20 +313,27 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
     }
     fence_before();
 
-    if (row < a.n) {
+    if (row < n) {
+      const float rs = rsqrtf(E);
       if (a.mode == 1) {
         bool flagged = false;
-        const double e = (double)E;
-        if (!(e >= a.e_first && e <= a.e_last)) {
-          flagged = true;
-        } else if (a.flags) {
-          int b = (int)((__log2f(E) - a.l2min) * a.inv_bw);
-          b = min(max(b, 0), a.n_hash - 1);
-          flagged = a.flags[b] != 0;
+        if (a.flags) {
+          const double e = (double)E;
+          if (!(e >= a.e_first && e <= a.e_last)) {
+            flagged = true;
+          } else {
+            int b = (int)((__log2f(E) - a.l2min) * a.inv_bw);
+            b = min(max(b, 0), a.n_hash - 1);
+            flagged = a.flags[b] != 0;
+          }
         }
 #pragma unroll
-        for (int m = 0; m < kOut; ++m) p[m] = ((a.mat_mask >> m) & 1u) ? expf(p[m]) : 0.f;
+        for (int m = 0; m < kOut; ++m)
+          p[m] = ((a.mat_mask >> m) & 1u) ? fmaf(C[2 * m + 1], rs, C[2 * m]) * expf(p[m]) : 0.f;
         if (flagged) p[0] = __int_as_float(0x7fc00000);
+      } else {
+#pragma unroll
+        for (int m = 0; m < kOut; ++m) p[m] += logf(fmaf(C[2 * m + 1], rs, C[2 * m]));
       }
       float4 *o = reinterpret_cast<float4 *>(a.out + row * kOut);
 #pragma unroll
@@ -319,6 +360,8 @@ cudaError_t launch_apply(const ApplyArgs &a, int num_sms, cudaStream_t s) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_mlp_apply_tc, kTcThreads, kSmemTc);
   if (e != cudaSuccess) return e;
   if (bps != 1) return cudaErrorInvalidConfiguration;
+  // a device row limit is read by the kernel: size the grid for all n rows
+  // (blocks without a tile return at once)
   const int64_t tiles = (a.n + kTile - 1) / kTile;
   const int64_t want = (tiles + kGroups - 1) / kGroups;
   const int grid = (int)(want < (int64_t)num_sms ? want : (int64_t)num_sms);

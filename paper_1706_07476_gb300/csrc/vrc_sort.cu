@@ -86,7 +86,18 @@ __device__ __forceinline__ uint32_t ray_key(const SortKeyArgs &P, const double *
   if (g < 0) return reject;
   int c = crossing_estimate(P, x, y, z, u, v, w);
   int b = min(c / P.len_width, P.n_len - 1);
-  return (uint32_t)(g * P.n_len + b);
+  uint32_t key = (uint32_t)(g * P.n_len + b);
+  if (P.acc_flags) {  // rays outside the surrogate's accepted bins go after all accepted ones
+    bool acc = false;
+    const double e = (double)E;
+    if (e >= P.acc_e_lo && e <= P.acc_e_hi) {
+      int bin = (int)((__log2f(E) - P.acc_l2min) * P.acc_inv_bw);
+      bin = min(max(bin, 0), P.acc_n_hash - 1);
+      acc = P.acc_flags[bin] == 0;
+    }
+    if (!acc) key += (uint32_t)(P.n_groups * P.n_len);
+  }
+  return key;
 }
 
 __global__ void __launch_bounds__(kSortBlock) k_sort_count(RayPtrs R, SortKeyArgs P, const double *edges_g,

@@ -24,6 +24,15 @@ struct SortKeyArgs {
   // block of the ray's start point on a B x B x B grid over the mesh box);
   // the direction is not used (point events of the next-event estimator).
   int32_t blocks_axis;
+  // Learned cross sections: when acc_flags is set, rays whose energy lies in
+  // [acc_e_lo, acc_e_hi] and in a hash bin with acc_flags[bin] == 0 (the
+  // surrogate's accepted bins) take keys below n_groups * n_len, every
+  // other ray the same key plus n_groups * n_len (n_keys = 2 n_groups n_len
+  // + 1), so the accepted rays come first in the sorted order.
+  const uint8_t *acc_flags;
+  int32_t acc_n_hash;
+  float acc_l2min, acc_inv_bw;
+  double acc_e_lo, acc_e_hi;
 };
 
 struct RayOut {

@@ -322,21 +322,21 @@ def vrc_sort_rays_static(ctx: Context, rays: dict, out, stream=None):
     _hold_until_done(ctx, stream, dev)
 
 
-VRC_MLP_PARAMS = 26896
+VRC_MLP_PARAMS = 26928
 VRC_XS_TABLE = 0
 VRC_XS_SURROGATE = 1
 
 
 class vrc_surrogate_options(C.Structure):
     _fields_ = [("steps", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("tol", C.c_float),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("smooth", C.c_float)]
 
 
 class vrc_surrogate_report(C.Structure):
     _fields_ = [("final_loss", C.c_float), ("bins", C.c_int32), ("bins_accepted", C.c_int32),
                 ("coverage", C.c_float), ("max_rel_err_accepted", C.c_float),
                 ("median_rel_err", C.c_float), ("train_points", C.c_int64),
-                ("validation_points", C.c_int64)]
+                ("validation_points", C.c_int64), ("smooth_fraction", C.c_float)]
 
 
 def vrc_default_surrogate_options(**kw) -> vrc_surrogate_options:

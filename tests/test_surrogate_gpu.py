@@ -2,16 +2,17 @@
 (oracle/mlp.py), its training on the method's own tables, the flagged-bin
 fallback, and the tally it gives against the FP64 oracle.
 
-Tolerances.  The GPU rounds weights, features and the first hidden layer's
-activations (and, backward, the hidden-layer gradients) to bfloat16
-(relative 2^-9 = 2e-3 each) and accumulates in float32; the output layer is
-float32.  The reference uses the same
-bf16-rounded weights in float64 otherwise.  Forward: relative Frobenius error
-of the outputs <= 2e-2.  Gradients: per tensor, relative Frobenius error
-<= 5e-2 and cosine similarity >= 0.998.  Tallies with the surrogate: the
-validated relative error of sigma_t in accepted bins is <= 1e-3, which moves
-a score by about 1e-3 (1 + tau); the stated bound is 1e-2 max relative per
-cell against the oracle.
+Tolerances.  The GPU rounds W1 and W2 to bfloat16 (the reference uses the
+same rounded weights in float64); the features and h1 enter the tensor cores
+as bfloat16 pairs hi + lo (about 2^-17 relative), the sines, cosines and
+SiLU come from hardware approximations (about 1e-6), sums are float32.
+Forward: relative Frobenius error of the outputs <= 1e-4.  Gradients: the
+backward products take the bfloat16 hi parts only, and the SiLU
+derivatives are stored as bfloat16 (2^-9 relative each); per tensor,
+relative Frobenius error <= 1e-2 and cosine similarity >= 0.9999.
+Tallies with the surrogate: the validated relative error of sigma_t in
+accepted bins is <= 1e-3, which moves a score by about 1e-3 (1 + tau); the
+stated bound is 1e-2 max relative per cell against the oracle, 1e-3 mean.
 """
 from __future__ import annotations
 
@@ -41,13 +42,15 @@ def _params(seed):
     P = M.unpack(M.init_params(seed))
     for b in ("b1", "b2", "b3"):
         P[b] = 0.1 * rng.normal(size=P[b].shape)
+    P["C"][:, 0] = rng.uniform(0.1, 3.0, M.OUT)
+    P["C"][:, 1] = rng.uniform(0.0, 2.0, M.OUT)
     return M.pack(P).astype(np.float32)
 
 
 def _ref_params(p32):
-    """The weights the GPU sees (bf16), biases as given."""
+    """The weights the GPU sees (W1, W2 in bf16), the rest as given."""
     P = M.unpack(p32.astype(np.float64))
-    for w in ("W1", "W2", "W3"):
+    for w in ("W1", "W2"):
         P[w] = M.bf16_round(P[w])
     return M.pack(P)
 
@@ -63,7 +66,8 @@ def test_mlp_forward_matches_fp64_reference(vrc):
     torch.cuda.synchronize()
     got = out.cpu().numpy().astype(np.float64)
     want, _ = M.forward(_ref_params(p), E.astype(np.float64), E_LO, E_HI)
-    assert _rel(got, want) <= 2e-2, _rel(got, want)
+    print(f"forward rel Frobenius {_rel(got, want):.3e}, max abs {np.abs(got - want).max():.3e}")
+    assert _rel(got, want) <= 1e-4, _rel(got, want)
 
 
 def test_mlp_gradient_matches_fp64_reference(vrc):
@@ -72,7 +76,8 @@ def test_mlp_gradient_matches_fp64_reference(vrc):
     p = _params(2)
     n = 200  # several 64-row blocks and a ragged last one
     E = W.log_uniform(rng, n)
-    T = (rng.normal(size=(n, 16)) * 2.0).astype(np.float32)
+    T = (np.log(M.prior(_ref_params(p), E.astype(np.float64))[0])
+         + rng.normal(size=(n, 16)) * 2.0).astype(np.float32)
     mask = (rng.random((n, 16)) < 0.85).astype(np.uint8)
     count = int(mask.sum())
     grad = torch.empty(M.N_PARAMS, dtype=torch.float32, device="cuda")
@@ -84,11 +89,13 @@ def test_mlp_gradient_matches_fp64_reference(vrc):
     g = grad.cpu().numpy().astype(np.float64)
     want_loss, want = M.loss_and_grad(_ref_params(p), E.astype(np.float64), T.astype(np.float64),
                                       mask.astype(bool), E_LO, E_HI)
-    assert float(loss.item()) == pytest.approx(want_loss, rel=1e-2)
+    assert float(loss.item()) == pytest.approx(want_loss, rel=1e-4)
     G, Wt = M.unpack(g), M.unpack(want)
     for name, _ in M.SHAPES:
-        assert _rel(G[name], Wt[name]) <= 5e-2, (name, _rel(G[name], Wt[name]))
-        assert _cos(G[name], Wt[name]) >= 0.998, (name, _cos(G[name], Wt[name]))
+        print(f"grad {name}: rel Frobenius {_rel(G[name], Wt[name]):.3e}, cos {_cos(G[name], Wt[name]):.7f}")
+    for name, _ in M.SHAPES:
+        assert _rel(G[name], Wt[name]) <= 1e-2, (name, _rel(G[name], Wt[name]))
+        assert _cos(G[name], Wt[name]) >= 0.9999, (name, _cos(G[name], Wt[name]))
 
 
 def _surrogate_problem(n_mat=4, n=24, n_rays=1 << 15, n_points=2000, n_res=20, seed=4):
@@ -101,47 +108,55 @@ def test_training_reduces_loss_and_validates(vrc):
     ctx = vrc.context_for(prob)
     try:
         short = vrc.vrc_train_surrogate(ctx, vrc.vrc_default_surrogate_options(steps=20))
-        rep = vrc.vrc_train_surrogate(ctx, vrc.vrc_default_surrogate_options(steps=3000))
+        rep = vrc.vrc_train_surrogate(ctx, vrc.vrc_default_surrogate_options(steps=6000))
         print("surrogate report", rep)
         assert rep["final_loss"] < 0.25 * short["final_loss"]
-        assert rep["bins"] > 0 and 0 <= rep["bins_accepted"] <= rep["bins"]
-        if rep["bins_accepted"]:
-            assert rep["max_rel_err_accepted"] <= 1e-3
-        # re-validation at a loose bound keeps the parameters and accepts bins
+        assert 0 < rep["smooth_fraction"] < 1 and rep["train_points"] > 0
+        # the bound is met somewhere, and wherever a bin is accepted
+        assert rep["bins"] > 0 and 0 < rep["bins_accepted"] <= rep["bins"], rep
+        assert rep["max_rel_err_accepted"] <= 1e-3
+        # re-validation at a loose bound keeps the parameters and accepts more bins
         params = vrc.vrc_get_surrogate_params(ctx)
         loose = vrc.vrc_train_surrogate(ctx, vrc.vrc_default_surrogate_options(steps=0, tol=0.5))
         assert np.array_equal(params, vrc.vrc_get_surrogate_params(ctx))
-        assert loose["bins_accepted"] > 0 and loose["max_rel_err_accepted"] <= 0.5
+        assert loose["bins_accepted"] > rep["bins_accepted"] and loose["max_rel_err_accepted"] <= 0.5
         assert loose["median_rel_err"] == pytest.approx(rep["median_rel_err"], rel=1e-6)
-        # the learned function on fresh energies against the table
+        # the trained parameters through the ABI's forward pass against the
+        # FP64 reference of the same network, at fresh energies
         import torch
         rng = np.random.default_rng(7)
         E = W.log_uniform(rng, 20000)
+        lo, hi = prob.tables[0][0][0], prob.tables[0][0][-1]
         out = torch.empty((len(E), 16), dtype=torch.float32, device="cuda")
-        vrc.vrc_mlp_forward(torch.from_numpy(params).cuda(), torch.from_numpy(E).cuda(),
-                            prob.tables[0][0][0], prob.tables[0][0][-1], out)
+        vrc.vrc_mlp_forward(torch.from_numpy(params).cuda(), torch.from_numpy(E).cuda(), lo, hi, out)
         torch.cuda.synchronize()
-        y = out.cpu().numpy()
+        y = out.cpu().numpy()[:, :len(prob.tables)].astype(np.float64)
+        want, _ = M.forward(_ref_params(params), E.astype(np.float64), lo, hi)
+        assert np.abs(y - want[:, :len(prob.tables)]).max() <= 1e-4
+        # and against the tables at fresh energies: within the bound about as
+        # often as the energy falls in an accepted bin (the network is not
+        # trained on resonance structure, which stays with the table)
         sig = np.stack([np.interp(E.astype(np.float64), t[0], t[1]) for t in prob.tables], 1)
-        rel = np.abs(np.exp(y[:, :len(prob.tables)].astype(np.float64)) - sig) / sig
-        assert np.median(rel) < 0.2, np.median(rel)
+        rel = (np.abs(np.exp(y) - sig) / sig).max(1)
+        print(f"fresh energies within 1e-3: {np.mean(rel <= 1e-3):.3f} (coverage {rep['coverage']:.3f})")
+        assert np.mean(rel <= 1e-3) >= 0.8 * rep["coverage"]
     finally:
         ctx.close()
 
 
 @pytest.mark.parametrize("form", [0, 1], ids=["plain", "fp32"])
 def test_surrogate_cast_vs_oracle(vrc, form):
-    """With the network used wherever its validated error is below tol, the
-    tally stays within the stated bound 10 tol of the oracle (max over cells,
-    mean below tol); the table mode on the same context keeps 1e-4."""
+    """Trained to the 1e-3 bound with bins accepted, the surrogate's cast
+    stays within the stated bound of the oracle (1e-2 max relative per cell,
+    1e-3 mean); the table mode on the same context keeps 1e-4."""
     import torch
-    tol = 0.1
+    tol = 1e-3
     prob = _surrogate_problem(n_mat=16, n=32, n_rays=1 << 16, n_points=3000, n_res=20)
     want, st = oracle.cast(prob)
     ctx = vrc.context_for(prob, vrc.vrc_default_options(form=form))
     try:
-        rep = vrc.vrc_train_surrogate(ctx, vrc.vrc_default_surrogate_options(steps=3000, tol=tol))
-        assert rep["bins_accepted"] > 0, rep
+        rep = vrc.vrc_train_surrogate(ctx, vrc.vrc_default_surrogate_options(tol=tol))
+        assert rep["bins_accepted"] > 0 and rep["max_rel_err_accepted"] <= tol, rep
         vrc.vrc_set_xs_mode(ctx, vrc.VRC_XS_SURROGATE)
         rays = {k: torch.from_numpy(v).cuda() for k, v in prob.rays.items()}
         vrc.vrc_cast_rays(ctx, rays)
@@ -150,13 +165,51 @@ def test_surrogate_cast_vs_oracle(vrc, form):
         assert rc == vrc.VRC_OK and stats["segments"] == st["segments"]
         r = H.rel_err_report(want, got)
         print(f"surrogate form={form} coverage={rep['coverage']:.3f} tally {r}")
-        assert r["max_rel"] <= 10 * tol and r["mean_rel"] <= tol, r
+        assert r["max_rel"] <= 1e-2 and r["mean_rel"] <= 1e-3, r
         assert r["max_rel"] > 1e-6  # the network's sigma was used
         vrc.vrc_set_xs_mode(ctx, vrc.VRC_XS_TABLE)
         vrc.vrc_reset_tally(ctx)
         vrc.vrc_cast_rays(ctx, rays)
         got_t, _ = vrc.vrc_read_tally(ctx)
         assert H.rel_err_report(want, got_t)["max_rel"] <= 1e-4
+    finally:
+        ctx.close()
+
+
+def test_no_accepted_bin_costs_nothing(vrc):
+    """With no bin accepted (a bound no network meets), the surrogate mode
+    casts every ray from the table: the same tally as the table mode, and
+    no slower (the network runs on no ray)."""
+    import torch
+    prob = W.surrogate_mesh(seed=4, n_rays=1 << 22)
+    ctx = vrc.context_for(prob, vrc.vrc_default_options(form=1))
+    rays = {k: torch.from_numpy(v).cuda() for k, v in prob.rays.items()}
+    s = torch.cuda.Stream()
+    try:
+        rep = vrc.vrc_train_surrogate(ctx, vrc.vrc_default_surrogate_options(steps=200, tol=1e-12))
+        assert rep["bins_accepted"] == 0
+
+        def run(mode):
+            vrc.vrc_set_xs_mode(ctx, mode)
+            vrc.vrc_cast_rays(ctx, rays, stream=s)  # warm-up
+            times = []
+            for _ in range(5):
+                vrc.vrc_reset_tally(ctx, s)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                vrc.vrc_cast_rays(ctx, rays, stream=s)
+                b.record(s)
+                b.synchronize()
+                times.append(a.elapsed_time(b))
+            tally, _ = vrc.vrc_read_tally(ctx, stream=s)
+            return float(np.median(times)), tally
+
+        t_table, tally_table = run(vrc.VRC_XS_TABLE)
+        t_surr, tally_surr = run(vrc.VRC_XS_SURROGATE)
+        print(f"no accepted bin: table {t_table:.3f} ms, surrogate mode {t_surr:.3f} ms "
+              f"({t_table / t_surr:.3f}x)")
+        np.testing.assert_allclose(tally_surr, tally_table, rtol=1e-12, atol=1e-300)
+        assert t_surr <= 1.05 * t_table
     finally:
         ctx.close()
 
@@ -175,11 +228,11 @@ def test_xs_mode_requires_training(vrc):
 def test_surrogate_gain_full_size(vrc):
     """The surrogate workload at full size (32^3, 16 materials of 20,000
     points with 200 resonances each, 2^24 rays): what the trained network
-    gains or loses against the table lookup, in segments/s and in bytes of
-    lookup data, with each tally's error against the FP64 oracle.  Three
-    runs: the table; the surrogate at the 1e-3 bound (rays in flagged bins
-    fall back to the table); the surrogate accepted everywhere (the speed it
-    would give, and the error it would cost)."""
+    gains or loses against the table lookup, in segments/s, with each
+    tally's error against the FP64 oracle.  Three runs: the table; the
+    surrogate at the 1e-3 bound (rays in flagged bins use the table); the
+    network accepted everywhere (the speed it would give, and the error it
+    would cost)."""
     import torch
     prob = W.surrogate_mesh(seed=4)
     want, st = oracle.cast(prob)
@@ -202,22 +255,22 @@ def test_surrogate_gain_full_size(vrc):
 
     try:
         rep = vrc.vrc_train_surrogate(ctx)
+        assert rep["coverage"] > 0, ("no bin accepted at 1e-3: the surrogate gains nothing here", rep)
         vrc.vrc_set_xs_mode(ctx, vrc.VRC_XS_TABLE)
         table = timed()
         vrc.vrc_set_xs_mode(ctx, vrc.VRC_XS_SURROGATE)
         checked = timed()
         every = vrc.vrc_train_surrogate(ctx, vrc.vrc_default_surrogate_options(steps=0, tol=1e30))
         forced = timed()
-        table_bytes = 4 * 16 * len(prob.tables[0][0])
         print(f"surrogate full: coverage at 1e-3 {rep['coverage']:.4f} (median validated error "
-              f"{rep['median_rel_err']:.3e}); segments/s table {table[0]:.3e}, surrogate+fallback "
-              f"{checked[0]:.3e} ({checked[0] / table[0]:.3f}x), network everywhere {forced[0]:.3e} "
-              f"({forced[0] / table[0]:.3f}x, coverage {every['coverage']:.3f}); lookup data "
-              f"{table_bytes} B table vs {4 * vrc.VRC_MLP_PARAMS} B weights; tally max rel err "
-              f"table {table[1]['max_rel']:.2e}, surrogate+fallback {checked[1]['max_rel']:.2e}, "
+              f"{rep['median_rel_err']:.3e}, smooth fraction {rep['smooth_fraction']:.3f}); segments/s "
+              f"table {table[0]:.3e}, surrogate+fallback {checked[0]:.3e} ({checked[0] / table[0]:.3f}x), "
+              f"network everywhere {forced[0]:.3e} ({forced[0] / table[0]:.3f}x, coverage "
+              f"{every['coverage']:.3f}); tally max rel err table {table[1]['max_rel']:.2e}, "
+              f"surrogate+fallback {checked[1]['max_rel']:.2e} (mean {checked[1]['mean_rel']:.2e}), "
               f"everywhere {forced[1]['max_rel']:.2e} (mean {forced[1]['mean_rel']:.2e})")
         assert table[1]["max_rel"] <= 1e-4
-        assert checked[1]["max_rel"] <= 1e-2  # the stated bound of the checked surrogate
+        assert checked[1]["max_rel"] <= 1e-2 and checked[1]["mean_rel"] <= 1e-3, checked[1]
         assert every["coverage"] == 1.0
     finally:
         ctx.close()
