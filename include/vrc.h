@@ -316,22 +316,28 @@ int vrc_moments_fold(vrc_ctx *c, void *cuda_stream);
  * Scores go to S1/S2 only: the tally is untouched.  The tabulated cross
  * sections are used (not the surrogate); the rays are sorted as in
  * vrc_cast_rays (options.sort), their history ids with them.
- * Needs (group count x cells) < 2^32 - 1.  Device scratch: a table of
- * 16-byte slots sized to twice an upper bound of the call's segments, with a
- * bitmap of one bit per slot, kept for later calls; the sorted copy of the
- * rays and of their ids (36 B per ray); VRC_ERR_OOM when it does not fit (split the call).  The
- * call waits for that bound (one small device-to-host read); the cast and
- * the fold into S1/S2 are then queued on cuda_stream (NULL = the context's
- * stream).  Host arrays may be reused on return; device arrays must stay
- * valid until the stream passes the call. */
+ * Needs (group count x cells) < 2^32 - 1.  How: each ray writes its scores
+ * as (history, bin, score) records into its own stretch of a pair buffer,
+ * sized by an upper bound of its segments; the records are sorted into
+ * buckets of consecutive bins, and per bucket the scores of each (history,
+ * bin) are summed in shared memory and folded into S1/S2.  Device scratch,
+ * kept for later calls: two pair buffers of 16 B per bound segment (about
+ * 3 GB each for 2^20 rays crossing 256^3 cells), 12 B per ray, the bucket
+ * table, and the sorted copy of the rays and of their ids (36 B per ray);
+ * VRC_ERR_OOM when it does not fit or when the call's bound passes 2^32 - 1
+ * segments (split the call).  The call waits for that bound (one small
+ * device-to-host read); the cast and the fold into S1/S2 are then queued on
+ * cuda_stream (NULL = the context's stream).  Host arrays may be reused on
+ * return; device arrays must stay valid until the stream passes the call. */
 int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, int64_t n_histories,
                        void *cuda_stream);
 
 /* Synchronous: total = S1 and sigma = sqrt(B/(B-1) (S2 - S1^2/B)) per
  * (group, cell) into HOST arrays of n = n_groups*nx*ny*nz float64 (sigma may
  * be NULL; sigma is 0 with fewer than 2 samples); *samples receives B (the
- * batch or history count).  Reports a per-history table overflow as
- * VRC_ERR_OOM. */
+ * batch or history count).  Reports a per-history overflow (a ray with
+ * more segments than its bound, or a bucket whose keys overflow the
+ * shared-memory table) as VRC_ERR_OOM. */
 int vrc_moments_read(vrc_ctx *c, double *total, double *sigma, int64_t n, int64_t *samples,
                      void *cuda_stream);
 

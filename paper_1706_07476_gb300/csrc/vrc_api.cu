@@ -157,7 +157,7 @@ int status_code(unsigned st) {
   if (st & kStatusTimeout)
     return fail(VRC_ERR_CUDA, "a bounded wait on the tensor cores gave up; results are incomplete");
   if (st & kStatusTableFull)
-    return fail(VRC_ERR_OOM, "the per-history table overflowed; its scores are incomplete");
+    return fail(VRC_ERR_OOM, "the per-history pairs overflowed their room; their scores are incomplete");
   if (st & kStatusTraversal)
     return fail(VRC_ERR_TRAVERSAL, "a ray needed more grid steps than the mesh allows");
   if (st & kStatusNonfinite)

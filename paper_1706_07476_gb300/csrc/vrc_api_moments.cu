@@ -20,9 +20,8 @@ int vrc_moments_enable(vrc_ctx *c, int32_t mode) {
   c->moment_mode = mode;
   if (mode == VRC_MOMENTS_OFF) {
     c->mom.release();
-    c->histTab.release();
-    c->histBits.release();
-    c->histCap = 0;
+    c->pairBuf.release();
+    c->pairSorted.release();
     c->moments = false;
     return VRC_OK;
   }
@@ -82,39 +81,6 @@ int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, i
              "copying history ids to the device");
     hist = static_cast<const uint32_t *>(c->histIds.p);
   }
-  // table size: twice an upper bound of the call's segments, a power of two
-  BoundGeom G;
-  for (int k = 0; k < 3; ++k) {
-    G.lo[k] = c->org[k];
-    G.h[k] = c->h[k];
-    G.n[k] = c->n[k];
-    G.e[k] = c->rect ? static_cast<const double *>(c->rectD.p) + c->rect_off[k] : nullptr;
-  }
-  VRC_CUDA(c->histBound.ensure(sizeof(unsigned long long)), "allocating the segment bound");
-  unsigned long long *d_bound = static_cast<unsigned long long *>(c->histBound.p);
-  VRC_CUDA(cudaMemsetAsync(d_bound, 0, sizeof(unsigned long long), s), "zeroing the segment bound");
-  VRC_CUDA(launch_segment_bound(G, rp, d_bound, c->num_sms, s), "launching the segment bound");
-  unsigned long long bound = 0;
-  VRC_CUDA(cudaMemcpyAsync(&bound, d_bound, sizeof bound, cudaMemcpyDeviceToHost, s), "reading the segment bound");
-  VRC_CUDA(cudaStreamSynchronize(s), "waiting for the segment bound");  // host arrays are free from here
-  unsigned long long cap = 1024;
-  while (cap < 2 * bound) cap <<= 1;
-  if (cap > c->histCap) {
-    c->histTab.release();
-    c->histBits.release();
-    c->histCap = 0;
-    size_t free_b = 0, total_b = 0;
-    VRC_CUDA(cudaMemGetInfo(&free_b, &total_b), "querying device memory");
-    const unsigned long long bytes = 16ull * cap + cap / 8ull;
-    if (bytes > free_b / 10 * 9)
-      return fail(VRC_ERR_OOM, "this call's histories need a %.1f GB table (%.1f GB free); split the call",
-                  bytes / 1e9, free_b / 1e9);
-    VRC_CUDA(c->histTab.ensure(16ull * cap), "allocating the per-history table");
-    VRC_CUDA(c->histBits.ensure(cap / 8ull), "allocating the per-history table");
-    VRC_CUDA(cudaMemsetAsync(c->histTab.p, 0, 16ull * cap, s), "clearing the per-history table");
-    VRC_CUDA(cudaMemsetAsync(c->histBits.p, 0, cap / 8ull, s), "clearing the per-history table");
-    c->histCap = cap;
-  }
   // sort the rays as vrc_cast_rays does, the history ids with them
   if (c->opt.sort == 1 || (c->opt.sort == -1 && rp.n >= kAutoSortMin)) {
     VRC_CUDA(c->histSorted.ensure(sizeof(uint32_t) * (size_t)rp.n), "allocating the sorted history ids");
@@ -123,11 +89,63 @@ int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, i
     if (rc) return rc;
     hist = sorted;
   }
+  // room of each ray in the pair buffer (an upper bound of its segments),
+  // and each ray's first pair; one small read of the total sizes the buffers
+  BoundGeom G;
+  for (int k = 0; k < 3; ++k) {
+    G.lo[k] = c->org[k];
+    G.h[k] = c->h[k];
+    G.n[k] = c->n[k];
+    G.e[k] = c->rect ? static_cast<const double *>(c->rectD.p) + c->rect_off[k] : nullptr;
+  }
+  const size_t nr = (size_t)rp.n;
+  VRC_CUDA(c->rayCap.ensure(sizeof(uint32_t) * nr), "allocating per-ray pair room");
+  VRC_CUDA(c->rayOff.ensure(sizeof(uint32_t) * nr), "allocating per-ray pair room");
+  VRC_CUDA(c->rayCnt.ensure(sizeof(uint32_t) * nr), "allocating per-ray pair room");
+  const int tile = scan_tile_elems();
+  // buckets of 2^shift consecutive bins, at most 16,384 of them
+  const int64_t n_bins = c->ncells * c->n_groups;
+  int shift = 0;
+  while (((n_bins - 1) >> shift) + 1 > 16384) ++shift;
+  const int n_buckets = (int)(((n_bins - 1) >> shift) + 1);
+  const int64_t tiles = std::max<int64_t>(((int64_t)n_buckets + tile) / tile, ((int64_t)nr + tile - 1) / tile);
+  VRC_CUDA(c->pairBoff.ensure(sizeof(uint32_t) * 2 * (size_t)(n_buckets + 1)), "allocating the pair sort table");
+  VRC_CUDA(c->pairTiles.ensure(sizeof(uint32_t) * (size_t)tiles), "allocating the pair sort table");
+  uint32_t *cap = static_cast<uint32_t *>(c->rayCap.p), *off = static_cast<uint32_t *>(c->rayOff.p);
+  VRC_CUDA(launch_ray_caps(G, rp, cap, c->num_sms, s), "launching the pair room");
+  VRC_CUDA(launch_exclusive_scan(cap, rp.n, off, static_cast<uint32_t *>(c->pairTiles.p), s),
+           "launching the pair room scan");
+  VRC_CUDA(c->histBound.ensure(2 * sizeof(uint32_t)), "allocating the pair count");
+  uint32_t *d_last = static_cast<uint32_t *>(c->histBound.p);
+  VRC_CUDA(cudaMemcpyAsync(d_last, cap + nr - 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s), "reading the pair room");
+  VRC_CUDA(cudaMemcpyAsync(d_last + 1, off + nr - 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s), "reading the pair room");
+  uint32_t last[2] = {0, 0};
+  VRC_CUDA(cudaMemcpyAsync(last, d_last, sizeof last, cudaMemcpyDeviceToHost, s), "reading the pair room");
+  VRC_CUDA(cudaStreamSynchronize(s), "waiting for the pair room");  // host arrays are free from here
+  const unsigned long long total = (unsigned long long)last[0] + last[1];
+  if (total >= 0xffffffffull)
+    return fail(VRC_ERR_OOM, "this call's rays may cross up to %llu cells, more than 2^32 - 1; split the call",
+                total);
+  const size_t pair_bytes = 16ull * std::max<unsigned long long>(total, 1);
+  if (pair_bytes > c->pairBuf.bytes || pair_bytes > c->pairSorted.bytes) {
+    c->pairBuf.release();
+    c->pairSorted.release();
+    size_t free_b = 0, total_b = 0;
+    VRC_CUDA(cudaMemGetInfo(&free_b, &total_b), "querying device memory");
+    if (2 * pair_bytes > free_b / 10 * 9)
+      return fail(VRC_ERR_OOM, "this call's histories need %.1f GB of pair buffers (%.1f GB free); split the call",
+                  2 * pair_bytes / 1e9, free_b / 1e9);
+    VRC_CUDA(c->pairBuf.ensure(pair_bytes), "allocating the pair buffer");
+    VRC_CUDA(c->pairSorted.ensure(pair_bytes), "allocating the pair buffer");
+  }
   CastArgs a = make_args(c, rp);
   a.hist = hist;
-  a.htab.e = static_cast<unsigned long long *>(c->histTab.p);
-  a.htab.mask = cap - 1;
-  a.htab.bits = static_cast<unsigned int *>(c->histBits.p);
+  a.pout.pairs = static_cast<ulonglong2 *>(c->pairBuf.p);
+  a.pout.off = off;
+  a.pout.cap = cap;
+  a.pout.cnt = static_cast<uint32_t *>(c->rayCnt.p);
+  // rays the cast rejects write no count
+  VRC_CUDA(cudaMemsetAsync(a.pout.cnt, 0, sizeof(uint32_t) * nr, s), "zeroing the pair counts");
   const int form = c->opt.form;
   const int block = c->opt.block > 0 ? c->opt.block : 256;
   int bps = c->opt.blocks_per_sm;
@@ -139,7 +157,10 @@ int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, i
   if (a.rays_per_warp > 0)
     VRC_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s), "zeroing the ray counter");
   VRC_CUDA(launch_cast_hist(form, a, grid, block, s), "launching the per-history cast");
-  VRC_CUDA(launch_hist_drain(a.htab, static_cast<double2 *>(c->mom.p), c->num_sms, s),
+  uint32_t *bcount = static_cast<uint32_t *>(c->pairBoff.p), *bbase = bcount + (n_buckets + 1);
+  VRC_CUDA(launch_pair_fold(a.pout, rp.n, shift, n_buckets, bcount, bbase, static_cast<uint32_t *>(c->pairTiles.p),
+                            static_cast<ulonglong2 *>(c->pairSorted.p), static_cast<double2 *>(c->mom.p),
+                            c->d_status, c->num_sms, s),
            "launching the per-history fold");
   c->batches += n_histories;
   return VRC_OK;

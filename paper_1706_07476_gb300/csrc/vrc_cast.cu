@@ -44,10 +44,9 @@ SmemLayout smem_layout(int form, const CastArgs &a, int block) {
 }
 
 // Blocks per SM: 2 for the plain form (its warp queues and float64 state),
-// 3 for per-history casts (the compare-and-swap inserts need registers), 4
-// for the FP32 tally cast.
+// 4 for the FP32 form.
 template <int FORM, bool SURR, typename Maker = TallyMaker, bool RECT = false>
-__global__ void __launch_bounds__(256, FORM == kFormPlain ? 2 : (std::is_same<Maker, HistMaker>::value ? 3 : 4))
+__global__ void __launch_bounds__(256, FORM == kFormPlain ? 2 : 4)
     k_cast(CastArgs a, SmemLayout L) {
   typedef typename Attenuation<FORM>::inv_t inv_t;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -154,16 +153,16 @@ cudaError_t launch_cast(int form, const CastArgs &a, int grid, int block, cudaSt
   return surr ? launch_t<kFormFp32, true>(a, grid, block, s) : launch_t<kFormFp32, false>(a, grid, block, s);
 }
 
-// Per-history cast: the same kernel with the history table as the sink
-// (tabulated cross sections; the ray order is the caller's).
+// Per-history cast: the same kernel with each ray's pair stretch as the
+// sink (tabulated cross sections; the ray order is the caller's).
 cudaError_t cast_hist_occupancy(int form, const CastArgs &a, int block, int *blocks_per_sm) {
-  if (form == kFormPlain) return occupancy_t<kFormPlain, false, HistMaker>(a, block, blocks_per_sm);
-  return occupancy_t<kFormFp32, false, HistMaker>(a, block, blocks_per_sm);
+  if (form == kFormPlain) return occupancy_t<kFormPlain, false, PairMaker>(a, block, blocks_per_sm);
+  return occupancy_t<kFormFp32, false, PairMaker>(a, block, blocks_per_sm);
 }
 
 cudaError_t launch_cast_hist(int form, const CastArgs &a, int grid, int block, cudaStream_t s) {
-  if (form == kFormPlain) return launch_t<kFormPlain, false, HistMaker>(a, grid, block, s);
-  return launch_t<kFormFp32, false, HistMaker>(a, grid, block, s);
+  if (form == kFormPlain) return launch_t<kFormPlain, false, PairMaker>(a, grid, block, s);
+  return launch_t<kFormFp32, false, PairMaker>(a, grid, block, s);
 }
 
 namespace {

@@ -280,90 +280,45 @@ struct TallySink {
   }
 };
 
-// Finalizer of SplitMix64 (Steele, Lea and Flood, "Fast splittable
-// pseudorandom number generators", OOPSLA 2014): a bijective 64-bit mix.
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
-  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-  return z ^ (z >> 31);
-}
-
-// One 128-bit compare-and-swap on a 16-byte slot (lo = first 8 bytes):
-// returns the slot's previous contents in (old_lo, old_hi).
-__device__ __forceinline__ void cas128(unsigned long long *slot, unsigned long long cmp_lo,
-                                       unsigned long long cmp_hi, unsigned long long new_lo,
-                                       unsigned long long new_hi, unsigned long long &old_lo,
-                                       unsigned long long &old_hi) {
-  asm volatile(
-      "{\n\t.reg .b128 d, b, c;\n\t"
-      "mov.b128 b, {%2, %3};\n\t"
-      "mov.b128 c, {%4, %5};\n\t"
-      "atom.global.cas.b128 d, [%6], b, c;\n\t"
-      "mov.b128 {%0, %1}, d;\n\t}"
-      : "=l"(old_lo), "=l"(old_hi)
-      : "l"(cmp_lo), "l"(cmp_hi), "l"(new_lo), "l"(new_hi), "l"(slot)
-      : "memory");
-}
-
-// The per-history table: the score of (history, bin) is summed in one
-// 16-byte slot (key + 1, value bits), found by linear probing from
-// mix64(key).  Every access is a 128-bit compare-and-swap on the whole slot:
-// the first, expecting an empty slot, claims it with the score in one step;
-// a slot that already holds the key is updated by compare-and-swap from the
-// contents that the failed claim returned.  A claim also sets the slot's bit
-// in the table's bitmap, so the fold visits only claimed slots.  Each failed update means another
-// thread's update went in; after kMaxCasRetries of them, or after probing the
-// whole table, kStatusTableFull is set and the score dropped (the host sizes
-// the table at twice an upper bound of the segments, so a full table does not
-// happen in practice).
-constexpr int kMaxCasRetries = 1 << 16;
-
-struct HistSink {
-  HistTable t;
-  unsigned long long base;  // (history << 32) + group * ncells + 1
+// Per-history cast: each score goes out as one (key, value) pair with a plain
+// store into the ray's own stretch of the pair buffer (no atomics, nothing
+// to wait for); the pairs are summed per (history, bin) after the cast.  A
+// ray that would write more pairs than its room (an upper bound of its
+// segments) sets kStatusTableFull and drops the rest.
+struct PairSink {
+  ulonglong2 *out;            // this ray's stretch
+  unsigned long long kbase;   // (group * ncells) << 32 | history id
+  uint32_t cap;
   unsigned int *status;
+  mutable uint32_t n;
   __device__ __forceinline__ void add(int cell, double v) const {
-    const unsigned long long key = base + (unsigned)cell;
-    const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
-    unsigned long long i = mix64(key) & t.mask;
-    for (unsigned long long probe = 0; probe <= t.mask; ++probe) {
-      unsigned long long *slot = t.e + 2 * i;
-      unsigned long long ok, ov;
-      cas128(slot, 0ull, 0ull, key, vb, ok, ov);
-      if (ok == 0ull && ov == 0ull) {  // claimed with the score
-        atomicOr(t.bits + (i >> 5), 1u << (unsigned)(i & 31ull));
-        return;
-      }
-      if (ok == key) {
-        for (int it = 0; it < kMaxCasRetries; ++it) {
-          const unsigned long long nv =
-              (unsigned long long)__double_as_longlong(__longlong_as_double((long long)ov) + v);
-          unsigned long long k2, v2;
-          cas128(slot, key, ov, key, nv, k2, v2);
-          if (v2 == ov) return;
-          ov = v2;  // another update of this slot went in first
-        }
-        break;
-      }
-      i = (i + 1) & t.mask;
-    }
-    atomicOr(status, kStatusTableFull);
+    if (n < cap)
+      out[n] = make_ulonglong2(kbase + ((unsigned long long)(unsigned)cell << 32),
+                               (unsigned long long)__double_as_longlong(v));
+    else
+      atomicOr(status, kStatusTableFull);
+    ++n;
   }
 };
 
-// Sink of ray r in group g for a plain cast and for a per-history cast.
+// Sink of ray r in group g for a plain cast and for a per-history cast, and
+// what a ray leaves behind when its walk ends.
 struct TallyMaker {
   __device__ __forceinline__ static TallySink make(const CastArgs &a, int64_t, int g) {
     uint64_t policy;
     asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
     return {a.tally + (int64_t)g * a.mesh.ncells, policy};
   }
+  __device__ __forceinline__ static void finish(const CastArgs &, int64_t, const TallySink &) {}
 };
-struct HistMaker {
-  __device__ __forceinline__ static HistSink make(const CastArgs &a, int64_t r, int g) {
-    return {a.htab,
-            ((unsigned long long)__ldg(a.hist + r) << 32) + (unsigned long long)g * a.mesh.ncells + 1ull,
-            a.status};
+struct PairMaker {
+  __device__ __forceinline__ static PairSink make(const CastArgs &a, int64_t r, int g) {
+    return {a.pout.pairs + __ldg(a.pout.off + r),
+            (((unsigned long long)g * (unsigned long long)a.mesh.ncells) << 32) | __ldg(a.hist + r),
+            __ldg(a.pout.cap + r), a.status, 0u};
+  }
+  __device__ __forceinline__ static void finish(const CastArgs &a, int64_t r, const PairSink &s) {
+    a.pout.cnt[r] = s.n < s.cap ? s.n : s.cap;
   }
 };
 
@@ -859,9 +814,10 @@ __device__ __forceinline__ void cast_one(const CastArgs &a, int64_t r, const int
   if (!ray_setup<FORM, SURR>(a, r, hash_s, edges, sig_s, inv_s, stride, c, q)) return;
   bool ovf = false;
   typedef typename std::conditional<RECT, RectWalk, UniformWalk>::type Walk;
-  c.seg += cast_ray_walk<FORM, Walk>(a.mesh, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn,
-                                     Maker::make(a, r, q.g), sig_s, inv_s, stride, a.stop_zero != 0,
-                                     &ovf, c.live);
+  const auto sink = Maker::make(a, r, q.g);
+  c.seg += cast_ray_walk<FORM, Walk>(a.mesh, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn, sink, sig_s,
+                                     inv_s, stride, a.stop_zero != 0, &ovf, c.live);
+  Maker::finish(a, r, sink);
   c.ovf += ovf;
 }
 
@@ -880,9 +836,10 @@ __device__ __forceinline__ void cast_one_plain_warp(const CastArgs &a, int64_t r
       has_ray && ray_setup<kFormPlain, SURR>(a, r, hash_s, edges, sig_s, inv_s, stride, c, q);
   bool ovf = false;
   // a lane without a ray builds its (unused) sink from ray 0 of group 0
-  c.seg += cast_ray_plain_warp<Walk>(a.mesh, ok, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn,
-                                     Maker::make(a, ok ? r : 0, ok ? q.g : 0), sig_s, inv_s, stride,
-                                     a.stop_zero != 0, &ovf, Q, c.live);
+  const auto sink = Maker::make(a, ok ? r : 0, ok ? q.g : 0);
+  c.seg += cast_ray_plain_warp<Walk>(a.mesh, ok, q.x, q.y, q.z, q.u, q.v, q.w, q.wt, q.dn, sink, sig_s,
+                                     inv_s, stride, a.stop_zero != 0, &ovf, Q, c.live);
+  if (ok) Maker::finish(a, r, sink);
   c.ovf += ovf;
 }
 

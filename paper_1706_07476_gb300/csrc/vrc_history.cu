@@ -1,12 +1,13 @@
 // Tally moments (the sums behind the tally's standard deviation in Eqs. 5
 // and 8), kept as (S1, S2) pairs per (group, cell): the batch fold, the read
-// (S1 and sigma), and for per-history moments the segment bound that sizes
-// the history table and the drain that turns the table's per-(history,
-// cell) sums x into S1 += x, S2 += x^2.
+// (S1 and sigma), and for per-history moments the room of each ray in the
+// pair buffer and the fold of a per-history cast's (key, score) pairs into
+// S1 += x, S2 += x^2, x the summed score of one history in one bin.
 #include <algorithm>
 #include <math.h>
 
 #include "vrc_internal.h"
+#include "vrc_sort.h"
 
 namespace vrc {
 
@@ -67,8 +68,40 @@ __device__ __forceinline__ unsigned long long ray_bound(const BoundGeom &G, cons
   return cells;
 }
 
-__global__ void k_segment_bound(BoundGeom G, RayPtrs R, unsigned long long *bound) {
-  unsigned long long acc = 0;
+// ray_bound on a uniform mesh in float32 arithmetic: the clipped entry and
+// exit points can each be one cell off per axis in float32, so the margin is
+// two cells per axis more than ray_bound's.
+__device__ __forceinline__ unsigned long long ray_bound_f(const BoundGeom &G, const float f[6]) {
+  if (!(f[3] != 0.f || f[4] != 0.f || f[5] != 0.f)) return 0;
+  float s_in = 0.f, s_out = INFINITY;
+  for (int k = 0; k < 3; ++k) {
+    const float lo = (float)G.lo[k], hi = (float)(G.lo[k] + G.h[k] * G.n[k]);
+    if (f[3 + k] == 0.f) {
+      if (!(f[k] >= lo && f[k] < hi)) return 0;
+    } else {
+      const float inv = 1.f / f[3 + k];
+      float a = (lo - f[k]) * inv, b = (hi - f[k]) * inv;
+      if (inv < 0.f) { const float t = a; a = b; b = t; }
+      s_in = fmaxf(s_in, a);
+      s_out = fminf(s_out, b);
+    }
+  }
+  if (!(s_in < s_out)) return 1 + 3 + 6;  // a near miss: the walk may still clip a corner
+  unsigned long long cells = 1 + 3 + 6;
+  for (int k = 0; k < 3; ++k) {
+    if (f[3 + k] == 0.f) continue;
+    const float ih = (float)(1.0 / G.h[k]), lo = (float)G.lo[k], nm1 = (float)(G.n[k] - 1);
+    const float a = fminf(fmaxf(floorf((fmaf(s_in, f[3 + k], f[k]) - lo) * ih), 0.f), nm1);
+    const float b = fminf(fmaxf(floorf((fmaf(s_out, f[3 + k], f[k]) - lo) * ih), 0.f), nm1);
+    cells += (unsigned long long)fabsf(b - a);
+  }
+  return cells;
+}
+
+// Room of every ray in the pair buffer: an upper bound of its segments
+// (float32 on a uniform mesh, float64 on a rectilinear one), capped at
+// 2^32 - 1.
+__global__ void k_ray_caps(BoundGeom G, RayPtrs R, uint32_t *cap) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R.n;
        r += (int64_t)gridDim.x * blockDim.x) {
     float f[6];
@@ -78,33 +111,146 @@ __global__ void k_segment_bound(BoundGeom G, RayPtrs R, unsigned long long *boun
     } else {
       f[0] = R.x[r]; f[1] = R.y[r]; f[2] = R.z[r]; f[3] = R.u[r]; f[4] = R.v[r]; f[5] = R.w[r];
     }
-    acc += ray_bound(G, f);
+    const bool ok = isfinite(f[0]) && isfinite(f[1]) && isfinite(f[2]) && isfinite(f[3]) && isfinite(f[4]) &&
+                    isfinite(f[5]);
+    const unsigned long long b = !ok ? 0ull : (G.e[0] ? ray_bound(G, f) : ray_bound_f(G, f));
+    cap[r] = b < 0xffffffffull ? (uint32_t)b : 0xffffffffu;
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(bound, acc);
 }
 
-// Every claimed slot (key + 1, x), found from the bitmap: mom[bin] += (x,
-// x^2), slot = 0, bitmap word = 0.  S1 and S2 of a bin share a 16-byte pair,
-// so the two reductions of a slot touch one 32-byte sector: one DRAM
-// read-modify-write where separate S1 and S2 arrays took two.
-__global__ void k_hist_drain(ulonglong2 *e, unsigned int *bits, unsigned long long words,
-                             double2 *__restrict__ mom) {
-  for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < words;
-       j += (unsigned long long)gridDim.x * blockDim.x) {
-    unsigned w = bits[j];
-    if (w == 0u) continue;
-    bits[j] = 0u;
-    while (w) {
-      const int b = __ffs(w) - 1;
-      w &= w - 1u;
-      ulonglong2 *slot = e + 32ull * j + (unsigned)b;
-      const ulonglong2 v = *slot;
-      const unsigned bin = (unsigned)((v.x - 1ull) & 0xffffffffull);
-      const double x = __longlong_as_double((long long)v.y);
-      atomicAdd(&mom[bin].x, x);
-      atomicAdd(&mom[bin].y, x * x);
-      *slot = make_ulonglong2(0ull, 0ull);
+// ---- fold of the per-history pairs ------------------------------------------
+// A counting sort puts the pairs into buckets of 2^shift consecutive bins
+// (block c takes rays c * kPairChunkRays .., one warp per ray, its pairs read
+// by consecutive lanes); then one block per bucket sums the scores of equal
+// keys (history, bin) in a shared-memory hash table and adds (x, x^2) to the
+// bin's moments.  A bucket's bins are a contiguous stretch of the moment
+// array, so those reductions stay in L2.  A bucket with more keys than half
+// the table is folded in several passes, each over the keys whose hash falls
+// in that pass.
+constexpr int kFoldThreads = 256;
+constexpr int kFoldSlots = 4096;  // shared-memory hash table of the fold: 64 KiB, 3 blocks per SM
+constexpr int kFoldBlockThreads = 512;
+constexpr int kFoldPassKeys = kFoldSlots * 7 / 10;  // keys per pass: load factor at most 0.7
+constexpr unsigned long long kEmptyKey = ~0ull;  // bin 2^32 - 1 never occurs
+
+// Each warp takes 32 consecutive rays at a time and spreads their pairs
+// over its lanes: lane l handles pairs base + l of the 32 rays' pairs in a
+// row (the ray of a pair found by a binary search over the warp's prefix
+// sums of the counts), so consecutive lanes read consecutive pairs.
+// Each warp takes 32 consecutive rays at a time (a grid-stride loop over
+// groups of 32) and spreads their pairs over its lanes: lane l handles pairs
+// j + l of the group's pairs in a row (the ray of a pair found by a binary
+// search over the warp's prefix sums of the counts), so consecutive lanes
+// read consecutive pairs; four such rounds are loaded before any is used.
+// Count pass: count[b] += pairs of bucket b.  Scatter pass: each pair goes
+// to cursor[b]++ (cursor[b] starts at the bucket's first slot).  Lanes of a
+// warp with the same bucket (mostly consecutive pairs of one ray) share one
+// global atomic.
+template <bool SCATTER>
+__global__ void __launch_bounds__(kFoldThreads) k_pair_bucket(PairOut P, int64_t n_rays, int shift,
+                                                              uint32_t *count, ulonglong2 *sorted) {
+  const unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < n_rays;
+       r0 += 32 * warps) {
+    const int64_t r = r0 + lane;
+    const uint32_t n = r < n_rays ? P.cnt[r] : 0u;
+    const uint32_t o = r < n_rays ? P.off[r] : 0u;
+    uint32_t incl = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t t = __shfl_up_sync(kAll, incl, d);
+      if (lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kAll, incl, 31), excl = incl - n;
+    for (uint32_t base = 0; base < total; base += 4 * 32) {
+      ulonglong2 q[4];
+      bool valid[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t t = base + 32 * u + lane;
+        int k = 0;  // the last ray whose pairs start at or before t
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const uint32_t e = __shfl_sync(kAll, excl, k + step);
+          if (e <= t) k += step;
+        }
+        const uint32_t ok = __shfl_sync(kAll, o, k), ek = __shfl_sync(kAll, excl, k);
+        valid[u] = t < total;
+        q[u] = valid[u] ? P.pairs[ok + (t - ek)] : make_ulonglong2(0ull, 0ull);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t b = valid[u] ? (uint32_t)(q[u].x >> 32) >> shift : 0xffffffffu;
+        const unsigned peers = __match_any_sync(kAll, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t first = 0;
+        if (valid[u] && lane == leader) first = atomicAdd(count + b, (uint32_t)__popc(peers));
+        if (SCATTER) {
+          first = __shfl_sync(kAll, first, leader);
+          if (valid[u]) sorted[first + __popc(peers & ((1u << lane) - 1u))] = q[u];
+        }
+      }
+    }
+  }
+}
+
+// 32-bit hash of a pair key (history in the low word, bin in the high one).
+__device__ __forceinline__ uint32_t key_hash(unsigned long long k) {
+  uint32_t h = (uint32_t)k * 0x9E3779B1u ^ (uint32_t)(k >> 32) * 0x85EBCA77u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  return h ^ (h >> 13);
+}
+
+__global__ void __launch_bounds__(kFoldBlockThreads, 3) k_pair_fold(const ulonglong2 *__restrict__ sorted,
+                                                                    const uint32_t *__restrict__ base,
+                                                                    int n_buckets, double2 *__restrict__ mom,
+                                                                    unsigned int *status) {
+  extern __shared__ unsigned long long keys[];  // [kFoldSlots], then the sums [kFoldSlots]
+  double *vals = reinterpret_cast<double *>(keys + kFoldSlots);
+  // the table starts empty; every drain leaves the slots it used empty again
+  for (int t = threadIdx.x; t < kFoldSlots; t += blockDim.x) { keys[t] = kEmptyKey; vals[t] = 0.0; }
+  __syncthreads();
+  for (int b = blockIdx.x; b < n_buckets; b += gridDim.x) {
+    const uint32_t begin = base[b], end = base[b + 1];
+    if (begin == end) continue;
+    // a table sized to the bucket, or several passes of the full table, each
+    // over the keys whose hash falls in it
+    const uint32_t count = end - begin;
+    const uint32_t passes = (count + kFoldPassKeys - 1) / kFoldPassKeys;
+    uint32_t slots = 64, lg = 6;
+    while (10 * count > 7 * slots && slots < (uint32_t)kFoldSlots) { slots <<= 1; ++lg; }
+    for (uint32_t p = 0; p < passes; ++p) {
+      bool full = false;
+      for (uint32_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
+        const ulonglong2 q = sorted[i];
+        const uint32_t h = key_hash(q.x);
+        if (passes > 1 && h % passes != p) continue;
+        uint32_t slot = h >> (32 - lg);
+        uint32_t probe = 0;
+        for (; probe < slots; ++probe) {
+          const unsigned long long old = atomicCAS(&keys[slot], kEmptyKey, q.x);
+          if (old == kEmptyKey || old == q.x) break;
+          slot = (slot + 1) & (slots - 1);
+        }
+        if (probe == slots) { full = true; continue; }
+        atomicAdd(&vals[slot], __longlong_as_double((long long)q.y));
+      }
+      if (full) atomicOr(status, kStatusTableFull);
+      __syncthreads();
+      for (uint32_t t = threadIdx.x; t < slots; t += blockDim.x) {
+        const unsigned long long k = keys[t];
+        if (k == kEmptyKey) continue;
+        const double x = vals[t];
+        keys[t] = kEmptyKey;
+        vals[t] = 0.0;
+        double2 *m = mom + (k >> 32);
+        atomicAdd(&m->x, x);
+        atomicAdd(&m->y, x * x);
+      }
+      __syncthreads();
     }
   }
 }
@@ -154,22 +300,36 @@ cudaError_t launch_moment_read(const double2 *mom, double *total, double *sigma,
   return cudaGetLastError();
 }
 
-cudaError_t launch_segment_bound(const BoundGeom &g, const RayPtrs &rays, unsigned long long *bound,
-                                 int num_sms, cudaStream_t s) {
+cudaError_t launch_ray_caps(const BoundGeom &g, const RayPtrs &rays, uint32_t *cap, int num_sms,
+                            cudaStream_t s) {
   if (rays.n <= 0) return cudaSuccess;
   const int block = 256;
   const int grid = (int)std::min<int64_t>((rays.n + block - 1) / block, (int64_t)num_sms * 8);
-  k_segment_bound<<<grid, block, 0, s>>>(g, rays, bound);
+  k_ray_caps<<<grid, block, 0, s>>>(g, rays, cap);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_hist_drain(const HistTable &t, double2 *mom, int num_sms, cudaStream_t s) {
-  const unsigned long long words = (t.mask + 1ull) / 32ull;
-  const int block = 256;
-  const int grid = (int)std::min<unsigned long long>((words + block - 1) / block, (unsigned long long)num_sms * 8);
-  k_hist_drain<<<grid, block, 0, s>>>(reinterpret_cast<ulonglong2 *>(t.e), t.bits, words, mom);
+cudaError_t launch_pair_fold(const PairOut &p, int64_t n_rays, int shift, int n_buckets, uint32_t *count,
+                             uint32_t *base, uint32_t *tiles, ulonglong2 *sorted, double2 *mom,
+                             unsigned int *status, int num_sms, cudaStream_t s) {
+  if (n_rays <= 0) return cudaSuccess;
+  cudaError_t e;
+  const int grid = (int)std::min<int64_t>((n_rays + 255) / 256, (int64_t)num_sms * 8);
+  // count[n_buckets] stays 0, so base[n_buckets] is the number of pairs
+  if ((e = cudaMemsetAsync(count, 0, sizeof(uint32_t) * (size_t)(n_buckets + 1), s)) != cudaSuccess) return e;
+  k_pair_bucket<false><<<grid, kFoldThreads, 0, s>>>(p, n_rays, shift, count, nullptr);
   note_launches(1);
+  if ((e = launch_exclusive_scan(count, (int64_t)n_buckets + 1, base, tiles, s)) != cudaSuccess) return e;
+  // the scatter's cursors start at the bases
+  if ((e = cudaMemcpyAsync(count, base, sizeof(uint32_t) * (size_t)n_buckets, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return e;
+  k_pair_bucket<true><<<grid, kFoldThreads, 0, s>>>(p, n_rays, shift, count, sorted);
+  const int fold_smem = 2 * 8 * kFoldSlots;
+  if ((e = cudaFuncSetAttribute(k_pair_fold, cudaFuncAttributeMaxDynamicSharedMemorySize, fold_smem)) != cudaSuccess) return e;
+  const int fgrid = (int)std::min<int64_t>(n_buckets, (int64_t)num_sms * 3);
+  k_pair_fold<<<fgrid, kFoldBlockThreads, fold_smem, s>>>(sorted, base, n_buckets, mom, status);
+  note_launches(2);
   return cudaGetLastError();
 }
 

@@ -139,12 +139,13 @@ struct vrc_ctx {
   bool moments = false;
   int moment_mode = VRC_MOMENTS_OFF;
   int64_t batches = 0;    // samples folded into the moments (batches or histories)
-  DevBuf histTab;         // per-history table, histCap slots of 16 bytes, all zero between calls
-  unsigned long long histCap = 0;
+  DevBuf pairBuf;         // per-history cast: (key, score) pairs, each ray's stretch
+  DevBuf pairSorted;      // the pairs sorted into bin buckets
+  DevBuf rayCap, rayOff, rayCnt;  // per ray: room, first pair, pairs written (uint32)
+  DevBuf pairBoff, pairTiles;  // bucket counts (then cursors) and bases; scan scratch
   DevBuf histIds;         // device copy of host history ids
   DevBuf histSorted;      // history ids in sorted ray order
-  DevBuf histBits;        // claim bitmap of the table, histCap bits, all zero between calls
-  DevBuf histBound;       // segment bound of the current call
+  DevBuf histBound;       // last room and last offset of the current call (pair count)
 
   bool timing = false;
   std::vector<TimedSpan> pending;
@@ -198,10 +199,15 @@ struct vrc_ctx {
     mlpFlags.release();
     sigBuf.release();
     mom.release();
-    histTab.release();
+    pairBuf.release();
+    pairSorted.release();
+    rayCap.release();
+    rayOff.release();
+    rayCnt.release();
+    pairBoff.release();
+    pairTiles.release();
     histIds.release();
     histSorted.release();
-    histBits.release();
     histBound.release();
     rectDf.release();
     rectD.release();

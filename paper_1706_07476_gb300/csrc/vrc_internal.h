@@ -63,13 +63,15 @@ struct RayPtrs {
   int64_t n;
 };
 
-// Per-history scratch table: 2^k entries of two 64-bit words, (key + 1,
-// float64 value bits), 0 marking an empty slot; key = history << 32 | bin,
-// bin = group * ncells + cell.
-struct HistTable {
-  unsigned long long *e;       // [cap][2]
-  unsigned long long mask;     // cap - 1
-  unsigned int *bits;          // [cap / 32] one bit per slot, set when the slot is claimed
+// Output of a per-history cast: ray r writes its scores, in walk order, to
+// pairs[off[r]] .. pairs[off[r] + cap[r] - 1] as (key, float64 bits), key =
+// bin << 32 | history id, bin = group * ncells + cell, and the number
+// written to cnt[r] (cap[r] is an upper bound of the ray's segments).
+struct PairOut {
+  ulonglong2 *pairs;
+  const uint32_t *off;
+  const uint32_t *cap;
+  uint32_t *cnt;
 };
 
 struct CastArgs {
@@ -82,7 +84,7 @@ struct CastArgs {
   const uint32_t *n_surr; // device count of leading rays with surrogate sigma (with sig_ray)
   double *tally;        // [n_groups][ncells]
   const uint32_t *hist; // [n] history id of each ray (per-history cast only)
-  HistTable htab;       // per-history cast only
+  PairOut pout;         // per-history cast only
   int32_t stop_zero;    // end a walk once its transmitted fraction is exactly 0
   // Ray assignment: 0, each thread takes rays r, r + (grid threads), ...;
   // R > 0 (a multiple of 32), each warp takes R consecutive rays at a time
@@ -133,21 +135,28 @@ cudaError_t launch_per_volume_rect(const double *src, double *dst, int64_t n, in
                                    const double *wz, cudaStream_t s);
 // Tally moments (vrc_history.cu): mom[bin] = (S1, S2), the sums of the
 // samples and of their squares per (group, cell).  Batch moments: the fold
-// mom += (t, t^2), t = 0.  Per-history moments: an upper bound of the
-// segments of a ray batch (added to *bound), the cast that scores into the
-// history table (vrc_cast.cu), and the drain mom[bin] += (x, x^2) that also
-// empties it.
+// mom += (t, t^2), t = 0.  Per-history moments: an upper bound of each
+// ray's segments (cap), the cast that writes each ray's (key, score) pairs
+// (vrc_cast.cu), a counting sort of the pairs into buckets of 2^shift
+// consecutive bins, and per bucket the sum x of every (history, bin) and
+// mom[bin] += (x, x^2).
 cudaError_t launch_fold_moments(double *tally, double2 *mom, int64_t n, cudaStream_t s);
 struct BoundGeom {
   double lo[3], h[3];
   int32_t n[3];
   const double *e[3];  // rectilinear plane positions (device), or nullptr
 };
-cudaError_t launch_segment_bound(const BoundGeom &g, const RayPtrs &rays, unsigned long long *bound,
-                                 int num_sms, cudaStream_t s);
+cudaError_t launch_ray_caps(const BoundGeom &g, const RayPtrs &rays, uint32_t *cap, int num_sms,
+                            cudaStream_t s);
 cudaError_t launch_cast_hist(int form, const CastArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t cast_hist_occupancy(int form, const CastArgs &a, int block, int *blocks_per_sm);
-cudaError_t launch_hist_drain(const HistTable &t, double2 *mom, int num_sms, cudaStream_t s);
+// Bucket sort and fold of the pairs of n_rays rays (PairOut with pairs,
+// off and cnt set) into mom: count and base hold n_buckets + 1 values;
+// tiles is scan scratch; sorted receives the pairs bucket by bucket; status
+// gets kStatusTableFull if a bucket's shared-memory table overflows.
+cudaError_t launch_pair_fold(const PairOut &p, int64_t n_rays, int shift, int n_buckets, uint32_t *count,
+                             uint32_t *base, uint32_t *tiles, ulonglong2 *sorted, double2 *mom,
+                             unsigned int *status, int num_sms, cudaStream_t s);
 // total[i] = S1; sigma[i] = sqrt(B/(B-1) (S2 - S1^2/B)) if sigma is not null.
 cudaError_t launch_moment_read(const double2 *mom, double *total, double *sigma, int64_t n, double B,
                                cudaStream_t s);

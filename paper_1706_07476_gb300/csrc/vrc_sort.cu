@@ -346,6 +346,17 @@ cudaError_t launch_batched_sort(const BSortProblem *probs_dev, const int32_t *ch
 
 int scan_tile_elems() { return kScanTile; }
 
+cudaError_t launch_exclusive_scan(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *tiles,
+                                  cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int n_tiles = (int)((n + kScanTile - 1) / kScanTile);
+  k_scan_tiles<<<n_tiles, kScanBlock, 0, s>>>(in, n, tiles);
+  k_scan_sums<<<1, kScanBlock, 0, s>>>(tiles, n_tiles);
+  k_scan_apply<<<n_tiles, kScanBlock, 0, s>>>(in, n, tiles, out);
+  note_launches(3);
+  return cudaGetLastError();
+}
+
 cudaError_t load_sort_kernels() {
   cudaFuncAttributes fa;
   const void *fns[] = {(const void *)k_sort_count, (const void *)k_scan_tiles, (const void *)k_scan_sums,

@@ -87,6 +87,11 @@ cudaError_t launch_batched_sort(const BSortProblem *probs_dev, const int32_t *ch
 cudaError_t prepare_batched_sort(const BSortPlan &plan);
 int scan_tile_elems();
 
+// out[i] = in[0] + ... + in[i-1] (uint32, n values); tiles is scratch of
+// ceil(n / scan_tile_elems()) values.  Three kernel launches on stream s.
+cudaError_t launch_exclusive_scan(const uint32_t *in, int64_t n, uint32_t *out, uint32_t *tiles,
+                                  cudaStream_t s);
+
 // Makes the single-problem sort kernels resident on the current device
 // (cudaFuncGetAttributes on each): under lazy module loading, this is when
 // their code is placed on the device.
