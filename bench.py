@@ -75,6 +75,8 @@ def parse():
                                            "detectors", "surrogate"],
                     default="slab256")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
+    ap.add_argument("--problems", type=int, default=1024,
+                    help="batched workload: the first N of its 1,024 problems (profiling a subset)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-parity-sample", action="store_true")
     ap.add_argument("--no-micro", action="store_true")
@@ -103,6 +105,18 @@ def workload_text(args, prob):
     if args.workload == "graded":
         return GRADED, f"float64 [{prob.n_groups}][{prob.mesh.nz}][{prob.mesh.ny}][{prob.mesh.nx}]"
     return WORKLOAD, "float64 [16][256^3] (2 GiB)"
+
+
+def headline_config(args, prob, world):
+    """The headline line's config: what the workload is, the same for the
+    GPU arm and the reference arm (measured figures go elsewhere)."""
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    return {"workload": workload_text(args, prob)[0], "rays_per_step": prob.n_rays,
+            "form": forms[-1], "sort": args.sort, "tally": workload_text(args, prob)[1],
+            "l2": ("inputs larger than L2 (512 MiB rays, 2 GiB tally, 16 MiB mesh); no flush"
+                   if args.workload == "slab256" else
+                   "inputs larger than L2 (512 MiB rays); tally 7 MB; no flush"),
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 # --------------------------------------------------------------------------- clocks
@@ -322,10 +336,10 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "rays_per_step": per_step,
-                   "note": "each step is a bounded sample of the workload's rays"},
+        "config": headline_config(args, prob, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{per_step} consecutive rays of the slab256 workload per step"},
+                         "sample": f"{per_step} consecutive rays of the {prob.name} workload per step "
+                                   f"(each step a bounded sample of the step's 2^24 rays)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -350,7 +364,7 @@ def measure_batched(args, torch, vrc, local, steps, warmup, form, parity_problem
     With parity_problems > 0, that many problems (evenly spaced) are checked
     cell by cell against the FP64 oracle after one more launch."""
     from paper_1706_07476_gb300 import autotune
-    probs = W.batched_problems(seed=3)
+    probs = W.batched_problems(seed=3, n_problems=args.problems)
     ctxs = [vrc.context_for(p, vrc.vrc_default_options(form=form, device=local)) for p in probs]
     rays = [{k: torch.from_numpy(p.rays[k]).cuda() for k in W.RAY_FIELDS} for p in probs]
     best, tuned_ms, table = autotune.tune_batched(torch, probs, ctxs, rays, form,
@@ -989,13 +1003,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": R["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if head == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": workload_text(args, prob)[0], "rays_per_step": prob.n_rays,
-                   "segments_per_step": R["segments_per_step"], "form": head,
-                   "sort": args.sort, "tally": workload_text(args, prob)[1],
-                   "l2": ("inputs larger than L2 (512 MiB rays, 2 GiB tally, 16 MiB mesh); no flush"
-                          if args.workload == "slab256" else
-                          "inputs larger than L2 (512 MiB rays); tally 7 MB; no flush"),
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": headline_config(args, prob, world),
+        "segments_per_step": R["segments_per_step"],
         "forms": results,
         "stop_at_zero": stop,
         "roofline": roof,
