@@ -85,7 +85,8 @@ typedef struct {
                              of the persistent grid takes rays w*32 + lane, then the next 32 rays
                              one grid further); R > 0, a multiple of 32 up to 65,536: each warp
                              takes R consecutive (sorted) rays at a time from a device counter,
-                             so warps that finish early take more work; 0 auto (default) */
+                             so warps that finish early take more work; 0 auto (default:
+                             32 in the plain form, interleaved in the FP32 form) */
 } vrc_options;
 
 /* A uniform 3-D Cartesian mesh (Sec. 3: 3-D Cartesian mesh geometry).
