@@ -50,7 +50,7 @@ extern "C" {
 /* PLAIN: the paper's arithmetic (Sec. 3): single-precision cross sections
  * and distances, Eq. 4 evaluated in double precision, float64 tally.
  * Distances are computed with double-float (two float32) arithmetic; each
- * segment's e^-x and e^-x - 1 are within 0.51 and 1.8 ulp of the exact
+ * segment's e^-x and e^-x - 1 are within 0.6 and 2 ulp of the exact
  * values.  A ray stops scoring once its optical depth passes
  * 760 + ln(max(wt, 1)), where wt e^-tau is below the float64 range (any
  * score dropped there is below 1e-322).

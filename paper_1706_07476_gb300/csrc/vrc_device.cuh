@@ -188,11 +188,11 @@ struct Attenuation;
 // Plain form: the ray's weight times its transmitted fraction, W = wt
 // exp(-tau_in), carried in float64.  The cell's factor e^-x, x = Sigma l, and
 // the path term's e^-x - 1 both come from one float64 range reduction
-// (vrc_math64.h: within 0.51 and 1.8 ulp of the exact values), indexed from the
+// (vrc_math64.h: within 0.6 and 2 ulp of the exact values), indexed from the
 // float32 product Sigma l.  A void cell (Sigma = 0) has x = 0, factor exactly
-// 1 and path term l.  The float32 inputs are widened and W is tested for zero
-// with integer operations, which leaves the FP64 pipe to the 15 float64
-// arithmetic operations of a segment.  A segment's (e^-x, path term) needs
+// 1 and path term l.  The float32 inputs are widened, their exact product x
+// is formed and W is tested for zero with integer operations, which leaves
+// the FP64 pipe to the 13 float64 arithmetic operations of a segment.  A segment's (e^-x, path term) needs
 // no ray state (terms); the score and the carry W *= e^-x do (apply), so the
 // warp-batched walk can compute the first for any lane's segment.  score()
 // returns the float64 contribution.
@@ -206,7 +206,7 @@ struct Attenuation<kFormPlain> {
   // (e^-x, path term): path term = -(e^-x - 1)/Sigma, or l in void
   __device__ __forceinline__ static double2 terms(float sig, double inv, float l) {
     const double ld = f2d_bits(l);
-    const double x = f2d_bits(sig) * ld;  // exact: a float product fits a double
+    const double x = m64::exact_product(sig, l);
     double factor, em;
     m64::exp_expm1(-x, -(sig * l), &factor, &em);
     return make_double2(factor, sig > 0.f ? -em * inv : ld);

@@ -1,9 +1,11 @@
 // Error bound of the float64 exp / expm1 pair used by the plain form, built
-// for the host: both results against long-double expl / expm1l, in units of
-// the last place of the float64 nearest the reference.  Exit status 0 when,
+// for the host, and the exact float32 product it takes: both results of the
+// pair against long-double expl / expm1l, in units of the last place of the
+// float64 nearest the reference.  Exit status 0 when,
 // for every y >= -708.3, e^y is within 0.6 ulp and e^y - 1 within 2 ulp,
 // every y below -709.5 gives (0, -1) and the y between give one or the
-// other; prints the worst cases either way.
+// other, and every exact product equals the float64 product; prints the
+// worst cases either way.
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -59,10 +61,10 @@ int main() {
   for (int i = 0; i < 2000000; ++i) check(-760.0 * uniform01());       // whole range
   for (int i = 0; i < 1000000; ++i) check(-8.0 * uniform01());         // typical Sigma l
   for (int i = 0; i < 1000000; ++i) check(-pow(10.0, -300.0 + 302.0 * uniform01()));  // tiny to 100
-  // either side of every reduction boundary (y = (n + 1/2) ln2/256) and of
-  // every n ln2/256, down to the end of the range
-  const double c = 0.6931471805599453 / 256;
-  for (int n = 0; n < 262400; ++n) {
+  // either side of reduction boundaries (y = (n + 1/2) ln2/N) and of
+  // n ln2/N: every n below 2^17, then every 7th down to the end of the range
+  const double c = 0.6931471805599453 / vrc::m64::kTabSize;
+  for (int n = 0; n < 1024 * 2050; n += (n < (1 << 17) ? 1 : 7)) {
     for (int d = -4; d <= 4; ++d) {
       check(-(n + 0.5) * c + d * 2e-16 * (1.0 + n * c));
       check(-n * c + d * 2e-16 * (1.0 + n * c));
@@ -86,11 +88,28 @@ int main() {
     rcp_off += got != want;
     ++n_rcp;
   }
+  // exact product of two float32: bit for bit the float64 product, over
+  // random normal pairs, zero and subnormal factors
+  long prod_off = 0, n_prod = 0;
+  for (int i = 0; i < 4000000; ++i) {
+    const uint64_t u = (uint64_t)(uniform01() * 0x1p53);
+    uint32_t ba = (uint32_t)u & 0x7fffffffu, bb = (uint32_t)(u >> 21) & 0x7fffffffu;
+    if (i % 97 == 0) ba &= 0x007fffffu;  // subnormal or zero
+    if (i % 89 == 0) bb = 0u;
+    if ((ba >> 23) == 0xffu || (bb >> 23) == 0xffu) continue;
+    float a, b;
+    memcpy(&a, &ba, sizeof a);
+    memcpy(&b, &bb, sizeof b);
+    const double got = vrc::m64::exact_product(a, b), want = (double)a * (double)b;
+    prod_off += memcmp(&got, &want, sizeof got) != 0;
+    ++n_prod;
+  }
+  printf("exact product: %ld pairs, %ld differ from the float64 product\n", n_prod, prod_off);
   printf("rcp: %ld floats, worst %.3f ulp, %ld differ from the rounded quotient\n", n_rcp, worst_rcp,
          rcp_off);
   printf("checked %ld: worst exp %.3f ulp at y=%.17g, worst expm1 %.3f ulp at y=%.17g; "
          "below-range failures %ld; exact at 0: %d; tiny: %d\n",
          n_checked, worst_ey, at_ey, worst_em, at_em, n_bad_range, exact0, tiny);
   return (worst_ey <= 0.6 && worst_em <= 2.0 && n_bad_range == 0 && exact0 && tiny &&
-          worst_rcp <= 0.51) ? 0 : 1;
+          worst_rcp <= 0.51 && prod_off == 0) ? 0 : 1;
 }
