@@ -322,14 +322,20 @@ int vrc_moments_fold(vrc_ctx *c, void *cuda_stream);
  * sized by an upper bound of its segments; the records are sorted into
  * buckets of consecutive bins, and per bucket the scores of each (history,
  * bin) are summed in shared memory and folded into S1/S2.  Device scratch,
- * kept for later calls: two pair buffers of 16 B per bound segment (about
- * 3 GB each for 2^20 rays crossing 256^3 cells), 12 B per ray, the bucket
- * table, and the sorted copy of the rays and of their ids (36 B per ray);
- * VRC_ERR_OOM when it does not fit or when the call's bound passes 2^32 - 1
- * segments (split the call).  The call waits for that bound (one small
- * device-to-host read); the cast and the fold into S1/S2 are then queued on
- * cuda_stream (NULL = the context's stream).  Host arrays may be reused on
- * return; device arrays must stay valid until the stream passes the call. */
+ * kept for later calls: two pair buffers, 12 B per ray, the bucket table,
+ * and the sorted copy of the rays and of their ids (36 B per ray).  With
+ * device inputs the pair buffers are sized for every ray's largest bound,
+ * 16 B x n x (nx + ny + nz + 10) each (13 GB for 2^20 rays in a 256^3
+ * mesh), when both fit in a quarter of the free device memory: the call
+ * then never waits on the device (it synchronises the stream only when it
+ * grows them).  Otherwise, and always with host inputs, the call waits for
+ * the sum of its rays' bounds (one small device-to-host read) and sizes the
+ * buffers to 16 B per bound segment (about 3 GB each for 2^20 rays crossing
+ * 256^3 cells); VRC_ERR_OOM when they do not fit or when that bound passes
+ * 2^32 - 1 segments (split the call).  The cast and the fold into S1/S2 are
+ * queued on cuda_stream (NULL = the context's stream).  Host arrays may be
+ * reused on return; device arrays must stay valid until the stream passes
+ * the call. */
 int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, int64_t n_histories,
                        void *cuda_stream);
 

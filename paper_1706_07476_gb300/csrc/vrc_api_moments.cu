@@ -89,61 +89,97 @@ int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, i
     if (rc) return rc;
     hist = sorted;
   }
-  // room of each ray in the pair buffer (an upper bound of its segments),
-  // and each ray's first pair; one small read of the total sizes the buffers
-  BoundGeom G;
-  for (int k = 0; k < 3; ++k) {
-    G.lo[k] = c->org[k];
-    G.h[k] = c->h[k];
-    G.n[k] = c->n[k];
-    G.e[k] = c->rect ? static_cast<const double *>(c->rectD.p) + c->rect_off[k] : nullptr;
-  }
   const size_t nr = (size_t)rp.n;
-  VRC_CUDA(c->rayCap.ensure(sizeof(uint32_t) * nr), "allocating per-ray pair room");
-  VRC_CUDA(c->rayOff.ensure(sizeof(uint32_t) * nr), "allocating per-ray pair room");
-  VRC_CUDA(c->rayCnt.ensure(sizeof(uint32_t) * nr), "allocating per-ray pair room");
+  VRC_CUDA(c->rayCnt.ensure(sizeof(uint32_t) * nr), "allocating per-ray pair counts");
   const int tile = scan_tile_elems();
-  // buckets of 2^shift consecutive bins, at most 16,384 of them
+  // buckets of 2^shift consecutive bins, at most kPairMaxBuckets of them
   const int64_t n_bins = c->ncells * c->n_groups;
   int shift = 0;
-  while (((n_bins - 1) >> shift) + 1 > 16384) ++shift;
+  while (((n_bins - 1) >> shift) + 1 > kPairMaxBuckets) ++shift;
   const int n_buckets = (int)(((n_bins - 1) >> shift) + 1);
   const int64_t tiles = std::max<int64_t>(((int64_t)n_buckets + tile) / tile, ((int64_t)nr + tile - 1) / tile);
   VRC_CUDA(c->pairBoff.ensure(sizeof(uint32_t) * 2 * (size_t)(n_buckets + 1)), "allocating the pair sort table");
   VRC_CUDA(c->pairTiles.ensure(sizeof(uint32_t) * (size_t)tiles), "allocating the pair sort table");
-  uint32_t *cap = static_cast<uint32_t *>(c->rayCap.p), *off = static_cast<uint32_t *>(c->rayOff.p);
-  VRC_CUDA(launch_ray_caps(G, rp, cap, c->num_sms, s), "launching the pair room");
-  VRC_CUDA(launch_exclusive_scan(cap, rp.n, off, static_cast<uint32_t *>(c->pairTiles.p), s),
-           "launching the pair room scan");
-  VRC_CUDA(c->histBound.ensure(2 * sizeof(uint32_t)), "allocating the pair count");
-  uint32_t *d_last = static_cast<uint32_t *>(c->histBound.p);
-  VRC_CUDA(cudaMemcpyAsync(d_last, cap + nr - 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s), "reading the pair room");
-  VRC_CUDA(cudaMemcpyAsync(d_last + 1, off + nr - 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s), "reading the pair room");
-  uint32_t last[2] = {0, 0};
-  VRC_CUDA(cudaMemcpyAsync(last, d_last, sizeof last, cudaMemcpyDeviceToHost, s), "reading the pair room");
-  VRC_CUDA(cudaStreamSynchronize(s), "waiting for the pair room");  // host arrays are free from here
-  const unsigned long long total = (unsigned long long)last[0] + last[1];
-  if (total >= 0xffffffffull)
-    return fail(VRC_ERR_OOM, "this call's rays may cross up to %llu cells, more than 2^32 - 1; split the call",
-                total);
-  const size_t pair_bytes = 16ull * std::max<unsigned long long>(total, 1);
-  if (pair_bytes > c->pairBuf.bytes || pair_bytes > c->pairSorted.bytes) {
-    c->pairBuf.release();
-    c->pairSorted.release();
-    size_t free_b = 0, total_b = 0;
-    VRC_CUDA(cudaMemGetInfo(&free_b, &total_b), "querying device memory");
-    if (2 * pair_bytes > free_b / 10 * 9)
-      return fail(VRC_ERR_OOM, "this call's histories need %.1f GB of pair buffers (%.1f GB free); split the call",
-                  2 * pair_bytes / 1e9, free_b / 1e9);
-    VRC_CUDA(c->pairBuf.ensure(pair_bytes), "allocating the pair buffer");
-    VRC_CUDA(c->pairSorted.ensure(pair_bytes), "allocating the pair buffer");
+
+  // Each ray's stretch of the pair buffer.  With device inputs, a fixed
+  // stretch of nx + ny + nz + 10 pairs per ray (more than any walk's
+  // segments) when two such buffers fit in a quarter of the free device
+  // memory: no per-ray bound is needed and the call never waits on the
+  // device (it synchronises the stream only when it grows the buffers).
+  // Otherwise (or with host inputs, which must be free on return) each
+  // ray's room is an upper bound of its segments, the stretches follow by a
+  // scan, and the call reads the total back to size the buffers.
+  const uint32_t stride = (uint32_t)(c->n[0] + c->n[1] + c->n[2] + 10);
+  const unsigned long long worst = (unsigned long long)nr * stride;
+  bool fixed = false;
+  if (r->on_device && worst < 0xffffffffull) {
+    const size_t wbytes = 16ull * worst;
+    if (wbytes <= c->pairBuf.bytes && wbytes <= c->pairSorted.bytes) {
+      fixed = true;
+    } else {
+      size_t free_b = 0, total_b = 0;
+      VRC_CUDA(cudaStreamSynchronize(s), "waiting for earlier work on the pair buffers");
+      VRC_CUDA(cudaMemGetInfo(&free_b, &total_b), "querying device memory");
+      if (2 * wbytes <= (free_b + c->pairBuf.bytes + c->pairSorted.bytes) / 4) {
+        c->pairBuf.release();
+        c->pairSorted.release();
+        VRC_CUDA(c->pairBuf.ensure(wbytes), "allocating the pair buffer");
+        VRC_CUDA(c->pairSorted.ensure(wbytes), "allocating the pair buffer");
+        fixed = true;
+      }
+    }
+  }
+  uint32_t *cap = nullptr, *off = nullptr;
+  if (!fixed) {
+    BoundGeom G;
+    for (int k = 0; k < 3; ++k) {
+      G.lo[k] = c->org[k];
+      G.h[k] = c->h[k];
+      G.n[k] = c->n[k];
+      G.e[k] = c->rect ? static_cast<const double *>(c->rectD.p) + c->rect_off[k] : nullptr;
+    }
+    VRC_CUDA(c->rayCap.ensure(sizeof(uint32_t) * nr), "allocating per-ray pair room");
+    VRC_CUDA(c->rayOff.ensure(sizeof(uint32_t) * nr), "allocating per-ray pair room");
+    cap = static_cast<uint32_t *>(c->rayCap.p);
+    off = static_cast<uint32_t *>(c->rayOff.p);
+    VRC_CUDA(launch_ray_caps(G, rp, cap, c->num_sms, s), "launching the pair room");
+    VRC_CUDA(launch_exclusive_scan(cap, rp.n, off, static_cast<uint32_t *>(c->pairTiles.p), s),
+             "launching the pair room scan");
+    VRC_CUDA(c->histBound.ensure(2 * sizeof(uint32_t)), "allocating the pair count");
+    uint32_t *d_last = static_cast<uint32_t *>(c->histBound.p);
+    VRC_CUDA(cudaMemcpyAsync(d_last, cap + nr - 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s), "reading the pair room");
+    VRC_CUDA(cudaMemcpyAsync(d_last + 1, off + nr - 1, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s), "reading the pair room");
+    uint32_t last[2] = {0, 0};
+    VRC_CUDA(cudaMemcpyAsync(last, d_last, sizeof last, cudaMemcpyDeviceToHost, s), "reading the pair room");
+    VRC_CUDA(cudaStreamSynchronize(s), "waiting for the pair room");  // host arrays are free from here
+    const unsigned long long total = (unsigned long long)last[0] + last[1];
+    if (total >= 0xffffffffull)
+      return fail(VRC_ERR_OOM, "this call's rays may cross up to %llu cells, more than 2^32 - 1; split the call",
+                  total);
+    const size_t pair_bytes = 16ull * std::max<unsigned long long>(total, 1);
+    if (pair_bytes > c->pairBuf.bytes || pair_bytes > c->pairSorted.bytes) {
+      c->pairBuf.release();
+      c->pairSorted.release();
+      size_t free_b = 0, total_b = 0;
+      VRC_CUDA(cudaMemGetInfo(&free_b, &total_b), "querying device memory");
+      if (2 * pair_bytes > free_b / 10 * 9)
+        return fail(VRC_ERR_OOM, "this call's histories need %.1f GB of pair buffers (%.1f GB free); split the call",
+                    2 * pair_bytes / 1e9, free_b / 1e9);
+      VRC_CUDA(c->pairBuf.ensure(pair_bytes), "allocating the pair buffer");
+      VRC_CUDA(c->pairSorted.ensure(pair_bytes), "allocating the pair buffer");
+    }
   }
   CastArgs a = make_args(c, rp);
   a.hist = hist;
   a.pout.pairs = static_cast<ulonglong2 *>(c->pairBuf.p);
   a.pout.off = off;
   a.pout.cap = cap;
+  a.pout.stride = fixed ? stride : 0u;
   a.pout.cnt = static_cast<uint32_t *>(c->rayCnt.p);
+  uint32_t *bcount = static_cast<uint32_t *>(c->pairBoff.p), *bbase = bcount + (n_buckets + 1);
+  a.pout.bcount = bcount;
+  a.pout.bshift = shift;
+  VRC_CUDA(cudaMemsetAsync(bcount, 0, sizeof(uint32_t) * (size_t)(n_buckets + 1), s), "zeroing the bucket counts");
   // rays the cast rejects write no count
   VRC_CUDA(cudaMemsetAsync(a.pout.cnt, 0, sizeof(uint32_t) * nr, s), "zeroing the pair counts");
   const int form = c->opt.form;
@@ -157,8 +193,7 @@ int vrc_cast_histories(vrc_ctx *c, const vrc_rays *r, const uint32_t *history, i
   if (a.rays_per_warp > 0)
     VRC_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s), "zeroing the ray counter");
   VRC_CUDA(launch_cast_hist(form, a, grid, block, s), "launching the per-history cast");
-  uint32_t *bcount = static_cast<uint32_t *>(c->pairBoff.p), *bbase = bcount + (n_buckets + 1);
-  VRC_CUDA(launch_pair_fold(a.pout, rp.n, shift, n_buckets, bcount, bbase, static_cast<uint32_t *>(c->pairTiles.p),
+  VRC_CUDA(launch_pair_fold(a.pout, rp.n, n_buckets, bbase, static_cast<uint32_t *>(c->pairTiles.p),
                             static_cast<ulonglong2 *>(c->pairSorted.p), static_cast<double2 *>(c->mom.p),
                             c->d_status, c->num_sms, s),
            "launching the per-history fold");

@@ -281,22 +281,34 @@ struct TallySink {
 };
 
 // Per-history cast: each score goes out as one (key, value) pair with a plain
-// store into the ray's own stretch of the pair buffer (no atomics, nothing
-// to wait for); the pairs are summed per (history, bin) after the cast.  A
-// ray that would write more pairs than its room (an upper bound of its
-// segments) sets kStatusTableFull and drops the rest.
+// store into the ray's own stretch of the pair buffer (nothing to wait
+// for); the pairs are summed per (history, bin) after the cast.  The sink
+// also counts the pairs of each bucket of 2^bshift consecutive bins for the
+// bucket sort that follows, with one fire-and-forget reduction per run of
+// the ray's pairs in one bucket.  A ray that would write more pairs than
+// its room (an upper bound of its segments) sets kStatusTableFull and drops
+// the rest.  The bucket table, shift and status come from the cast's
+// arguments (kernel parameters), not from registers.
 struct PairSink {
   ulonglong2 *out;            // this ray's stretch
   unsigned long long kbase;   // (group * ncells) << 32 | history id
   uint32_t cap;
-  unsigned int *status;
-  mutable uint32_t n;
+  const CastArgs &a;
+  mutable uint32_t n, bcur, brun;  // pairs written; the current bucket run
   __device__ __forceinline__ void add(int cell, double v) const {
-    if (n < cap)
+    if (n < cap) {
       out[n] = make_ulonglong2(kbase + ((unsigned long long)(unsigned)cell << 32),
                                (unsigned long long)__double_as_longlong(v));
-    else
-      atomicOr(status, kStatusTableFull);
+      const uint32_t b = ((uint32_t)(kbase >> 32) + (uint32_t)cell) >> a.pout.bshift;
+      if (b != bcur) {
+        if (brun) atomicAdd(a.pout.bcount + bcur, brun);
+        bcur = b;
+        brun = 0;
+      }
+      ++brun;
+    } else {
+      atomicOr(a.status, kStatusTableFull);
+    }
     ++n;
   }
 };
@@ -313,12 +325,13 @@ struct TallyMaker {
 };
 struct PairMaker {
   __device__ __forceinline__ static PairSink make(const CastArgs &a, int64_t r, int g) {
-    return {a.pout.pairs + __ldg(a.pout.off + r),
+    return {a.pout.pairs + pair_off(a.pout, r),
             (((unsigned long long)g * (unsigned long long)a.mesh.ncells) << 32) | __ldg(a.hist + r),
-            __ldg(a.pout.cap + r), a.status, 0u};
+            pair_cap(a.pout, r), a, 0u, 0xffffffffu, 0u};
   }
   __device__ __forceinline__ static void finish(const CastArgs &a, int64_t r, const PairSink &s) {
     a.pout.cnt[r] = s.n < s.cap ? s.n : s.cap;
+    if (s.brun) atomicAdd(a.pout.bcount + s.bcur, s.brun);
   }
 };
 

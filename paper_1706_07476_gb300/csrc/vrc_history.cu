@@ -124,39 +124,41 @@ __global__ void k_ray_caps(BoundGeom G, RayPtrs R, uint32_t *cap) {
 // by consecutive lanes); then one block per bucket sums the scores of equal
 // keys (history, bin) in a shared-memory hash table and adds (x, x^2) to the
 // bin's moments.  A bucket's bins are a contiguous stretch of the moment
-// array, so those reductions stay in L2.  A bucket with more keys than half
-// the table is folded in several passes, each over the keys whose hash falls
-// in that pass.
+// array, so those reductions stay in L2.  A bucket with more keys than 0.7
+// of the table is folded in several passes, each over the keys whose hash
+// falls in that pass.
 constexpr int kFoldThreads = 256;
-constexpr int kFoldSlots = 4096;  // shared-memory hash table of the fold: 64 KiB, 3 blocks per SM
-constexpr int kFoldBlockThreads = 512;
+// The fold's shared-memory hash table (16 bytes a slot), threads and blocks
+// per SM.  Small blocks, many per SM, each on a small bucket (kPairMaxBuckets
+// of them: about 150 keys each for 2^20 slab256 rays, filling 60 % of a
+// table) measured fastest: a block waits at its barriers for 2 warps only.
+constexpr int kFoldSlots = 256;
+constexpr int kFoldBlockThreads = 64;
+constexpr int kFoldBlocksPerSm = 32;
 constexpr int kFoldPassKeys = kFoldSlots * 7 / 10;  // keys per pass: load factor at most 0.7
 constexpr unsigned long long kEmptyKey = ~0ull;  // bin 2^32 - 1 never occurs
 
-// Each warp takes 32 consecutive rays at a time and spreads their pairs
-// over its lanes: lane l handles pairs base + l of the 32 rays' pairs in a
-// row (the ray of a pair found by a binary search over the warp's prefix
-// sums of the counts), so consecutive lanes read consecutive pairs.
-// Each warp takes 32 consecutive rays at a time (a grid-stride loop over
-// groups of 32) and spreads their pairs over its lanes: lane l handles pairs
-// j + l of the group's pairs in a row (the ray of a pair found by a binary
-// search over the warp's prefix sums of the counts), so consecutive lanes
-// read consecutive pairs; four such rounds are loaded before any is used.
-// Count pass: count[b] += pairs of bucket b.  Scatter pass: each pair goes
-// to cursor[b]++ (cursor[b] starts at the bucket's first slot).  Lanes of a
-// warp with the same bucket (mostly consecutive pairs of one ray) share one
-// global atomic.
-template <bool SCATTER>
-__global__ void __launch_bounds__(kFoldThreads) k_pair_bucket(PairOut P, int64_t n_rays, int shift,
-                                                              uint32_t *count, ulonglong2 *sorted) {
+// Scatter of the pairs into buckets: each pair goes to cursor[b]++, where
+// cursor[b] starts at bucket b's first slot (the scan of the counts the cast
+// took).  Each warp takes 32 consecutive rays at a time (a grid-stride loop
+// over groups of 32) and spreads their pairs over its lanes: lane l handles
+// pairs j + l of the group's pairs in a row (the ray of a pair found by a
+// binary search over the warp's prefix sums of the counts), so consecutive
+// lanes read consecutive pairs; four such rounds are loaded before any is
+// used.  A run of consecutive lanes with the same bucket (mostly
+// consecutive pairs of one ray) shares one global atomic, taken by the
+// run's first lane (a lane whose bucket differs from the lane before it).
+__global__ void __launch_bounds__(kFoldThreads) k_pair_scatter(PairOut P, int64_t n_rays, uint32_t *cursor,
+                                                               ulonglong2 *sorted) {
   const unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const int shift = P.bshift;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < n_rays;
        r0 += 32 * warps) {
     const int64_t r = r0 + lane;
     const uint32_t n = r < n_rays ? P.cnt[r] : 0u;
-    const uint32_t o = r < n_rays ? P.off[r] : 0u;
+    const uint32_t o = r < n_rays ? pair_off(P, r) : 0u;
     uint32_t incl = n;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -183,14 +185,17 @@ __global__ void __launch_bounds__(kFoldThreads) k_pair_bucket(PairOut P, int64_t
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const uint32_t b = valid[u] ? (uint32_t)(q[u].x >> 32) >> shift : 0xffffffffu;
-        const unsigned peers = __match_any_sync(kAll, b);
-        const int leader = __ffs(peers) - 1;
+        const uint32_t prev = __shfl_up_sync(kAll, b, 1);
+        const unsigned heads = __ballot_sync(kAll, lane == 0 || b != prev);
+        // this lane's run: from its head (the last head at or below it) to
+        // the lane before the next head
+        const int head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        const unsigned above = heads & ~(0xffffffffu >> (31 - lane));
+        const int next = above ? __ffs(above) - 1 : 32;
         uint32_t first = 0;
-        if (valid[u] && lane == leader) first = atomicAdd(count + b, (uint32_t)__popc(peers));
-        if (SCATTER) {
-          first = __shfl_sync(kAll, first, leader);
-          if (valid[u]) sorted[first + __popc(peers & ((1u << lane) - 1u))] = q[u];
-        }
+        if (valid[u] && lane == head) first = atomicAdd(cursor + b, (uint32_t)(next - head));
+        first = __shfl_sync(kAll, first, head);
+        if (valid[u]) sorted[first + (uint32_t)(lane - head)] = q[u];
       }
     }
   }
@@ -204,7 +209,7 @@ __device__ __forceinline__ uint32_t key_hash(unsigned long long k) {
   return h ^ (h >> 13);
 }
 
-__global__ void __launch_bounds__(kFoldBlockThreads, 3) k_pair_fold(const ulonglong2 *__restrict__ sorted,
+__global__ void __launch_bounds__(kFoldBlockThreads, kFoldBlocksPerSm) k_pair_fold(const ulonglong2 *__restrict__ sorted,
                                                                     const uint32_t *__restrict__ base,
                                                                     int n_buckets, double2 *__restrict__ mom,
                                                                     unsigned int *status) {
@@ -310,24 +315,22 @@ cudaError_t launch_ray_caps(const BoundGeom &g, const RayPtrs &rays, uint32_t *c
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair_fold(const PairOut &p, int64_t n_rays, int shift, int n_buckets, uint32_t *count,
-                             uint32_t *base, uint32_t *tiles, ulonglong2 *sorted, double2 *mom,
-                             unsigned int *status, int num_sms, cudaStream_t s) {
+cudaError_t launch_pair_fold(const PairOut &p, int64_t n_rays, int n_buckets, uint32_t *base, uint32_t *tiles,
+                             ulonglong2 *sorted, double2 *mom, unsigned int *status, int num_sms,
+                             cudaStream_t s) {
   if (n_rays <= 0) return cudaSuccess;
   cudaError_t e;
   const int grid = (int)std::min<int64_t>((n_rays + 255) / 256, (int64_t)num_sms * 8);
-  // count[n_buckets] stays 0, so base[n_buckets] is the number of pairs
-  if ((e = cudaMemsetAsync(count, 0, sizeof(uint32_t) * (size_t)(n_buckets + 1), s)) != cudaSuccess) return e;
-  k_pair_bucket<false><<<grid, kFoldThreads, 0, s>>>(p, n_rays, shift, count, nullptr);
-  note_launches(1);
-  if ((e = launch_exclusive_scan(count, (int64_t)n_buckets + 1, base, tiles, s)) != cudaSuccess) return e;
-  // the scatter's cursors start at the bases
-  if ((e = cudaMemcpyAsync(count, base, sizeof(uint32_t) * (size_t)n_buckets, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+  // p.bcount[n_buckets] stays 0, so base[n_buckets] is the number of pairs
+  if ((e = launch_exclusive_scan(p.bcount, (int64_t)n_buckets + 1, base, tiles, s)) != cudaSuccess) return e;
+  // the scatter's cursors (in the count array) start at the bases
+  if ((e = cudaMemcpyAsync(p.bcount, base, sizeof(uint32_t) * (size_t)n_buckets, cudaMemcpyDeviceToDevice, s)) !=
+      cudaSuccess)
     return e;
-  k_pair_bucket<true><<<grid, kFoldThreads, 0, s>>>(p, n_rays, shift, count, sorted);
+  k_pair_scatter<<<grid, kFoldThreads, 0, s>>>(p, n_rays, p.bcount, sorted);
   const int fold_smem = 2 * 8 * kFoldSlots;
   if ((e = cudaFuncSetAttribute(k_pair_fold, cudaFuncAttributeMaxDynamicSharedMemorySize, fold_smem)) != cudaSuccess) return e;
-  const int fgrid = (int)std::min<int64_t>(n_buckets, (int64_t)num_sms * 3);
+  const int fgrid = (int)std::min<int64_t>(n_buckets, (int64_t)num_sms * kFoldBlocksPerSm);
   k_pair_fold<<<fgrid, kFoldBlockThreads, fold_smem, s>>>(sorted, base, n_buckets, mom, status);
   note_launches(2);
   return cudaGetLastError();

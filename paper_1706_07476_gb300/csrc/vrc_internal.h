@@ -66,13 +66,35 @@ struct RayPtrs {
 // Output of a per-history cast: ray r writes its scores, in walk order, to
 // pairs[off[r]] .. pairs[off[r] + cap[r] - 1] as (key, float64 bits), key =
 // bin << 32 | history id, bin = group * ncells + cell, and the number
-// written to cnt[r] (cap[r] is an upper bound of the ray's segments).
+// written to cnt[r] (cap[r] is an upper bound of the ray's segments).  With
+// stride != 0, off[r] = r * stride and cap[r] = stride (off, cap unused).
+// The cast also counts the pairs it writes per bucket of 2^bshift
+// consecutive bins into bcount (zeroed before the cast), one reduction per
+// run of a ray's pairs in one bucket.
 struct PairOut {
   ulonglong2 *pairs;
   const uint32_t *off;
   const uint32_t *cap;
   uint32_t *cnt;
+  uint32_t stride;
+  uint32_t *bcount;
+  int32_t bshift;
 };
+
+__host__ __device__ __forceinline__ uint32_t pair_off(const PairOut &p, int64_t r) {
+#ifdef __CUDA_ARCH__
+  return p.stride ? (uint32_t)r * p.stride : __ldg(p.off + r);
+#else
+  return p.stride ? (uint32_t)r * p.stride : p.off[r];
+#endif
+}
+__host__ __device__ __forceinline__ uint32_t pair_cap(const PairOut &p, int64_t r) {
+#ifdef __CUDA_ARCH__
+  return p.stride ? p.stride : __ldg(p.cap + r);
+#else
+  return p.stride ? p.stride : p.cap[r];
+#endif
+}
 
 struct CastArgs {
   MeshDev mesh;
@@ -151,12 +173,14 @@ cudaError_t launch_ray_caps(const BoundGeom &g, const RayPtrs &rays, uint32_t *c
 cudaError_t launch_cast_hist(int form, const CastArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t cast_hist_occupancy(int form, const CastArgs &a, int block, int *blocks_per_sm);
 // Bucket sort and fold of the pairs of n_rays rays (PairOut with pairs,
-// off and cnt set) into mom: count and base hold n_buckets + 1 values;
-// tiles is scan scratch; sorted receives the pairs bucket by bucket; status
-// gets kStatusTableFull if a bucket's shared-memory table overflows.
-cudaError_t launch_pair_fold(const PairOut &p, int64_t n_rays, int shift, int n_buckets, uint32_t *count,
-                             uint32_t *base, uint32_t *tiles, ulonglong2 *sorted, double2 *mom,
-                             unsigned int *status, int num_sms, cudaStream_t s);
+// off or stride, cnt, and bcount / bshift counted by the cast) into mom:
+// p.bcount and base hold n_buckets + 1 values (bcount[n_buckets] = 0); tiles
+// is scan scratch; sorted receives the pairs bucket by bucket; status gets
+// kStatusTableFull if a bucket's shared-memory table overflows.
+constexpr int kPairMaxBuckets = 262144;  // buckets of the pair sort, at most
+cudaError_t launch_pair_fold(const PairOut &p, int64_t n_rays, int n_buckets, uint32_t *base, uint32_t *tiles,
+                             ulonglong2 *sorted, double2 *mom, unsigned int *status, int num_sms,
+                             cudaStream_t s);
 // total[i] = S1; sigma[i] = sqrt(B/(B-1) (S2 - S1^2/B)) if sigma is not null.
 cudaError_t launch_moment_read(const double2 *mom, double *total, double *sigma, int64_t n, double B,
                                cudaStream_t s);
