@@ -564,16 +564,14 @@ def run_stream(args, rank, world, local):
 
 # --------------------------------------------------------------------------- per-history moments
 
-def run_history(args, rank, world, local):
+def measure_history(args, torch, vrc, local, prob, stream, steps, warmup):
     """Per-history moments: every step casts the slab256 rays in 16 calls of
-    2^20 rays through vrc_cast_histories (segment bound, sort of the rays
-    with their history ids, cast into the history table, fold into S1/S2),
-    FP32 form, timed with CUDA events on the calling stream; the plain tally
-    cast of the same calls (sorted too) is timed beside it."""
-    import torch
-    from paper_1706_07476_gb300 import vrc
-    torch.cuda.set_device(local)
-    prob = workload(args)
+    2^20 rays through vrc_cast_histories (sort of the rays with their
+    history ids, cast into per-ray pair records with bucket counts, bucket
+    scatter, fold into S1/S2), FP32 form, device inputs, timed with CUDA
+    events on the calling stream; the plain tally cast of the same calls
+    (sorted too) is timed beside it.  Returns the history figures, both
+    modes and the launch count."""
     rng = np.random.default_rng(6)
     lengths = rng.integers(1, 16, size=prob.n_rays // 4)
     hist = np.repeat(np.arange(lengths.size, dtype=np.uint32), lengths)[:prob.n_rays]
@@ -592,8 +590,6 @@ def run_history(args, rank, world, local):
     parts = [({k: v[a:b] for k, v in dev.items()}, hdev[a:b], int(hist[b - 1]) - int(hist[a]) + 1)
              for a, b in zip(cuts[:-1], cuts[1:])]
     ctx = vrc.context_for(prob, vrc.vrc_default_options(form=vrc.VRC_FORM_FP32, device=local))
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
 
     def step_hist():
         for r, h, nh in parts:
@@ -606,18 +602,18 @@ def run_history(args, rank, world, local):
     out = {}
     for name, fn, mode in (("tally", step_tally, vrc.VRC_MOMENTS_OFF), ("history", step_hist, vrc.VRC_MOMENTS_HISTORY)):
         vrc.vrc_moments_enable(ctx, mode)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             fn()
         stream.synchronize()
         vrc.vrc_reset_tally(ctx, stream)
         vrc.vrc_moments_enable(ctx, mode)
         torch.cuda.synchronize()
-        steps = max(1, min(args.steps, 10))
+        n = max(1, min(steps, 10))
         l0 = vrc.vrc_launch_count()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
         e0.record(stream)
-        for _ in range(steps):
+        for _ in range(n):
             fn()
         e1.record(stream)
         e1.synchronize()
@@ -625,22 +621,44 @@ def run_history(args, rank, world, local):
         rc, st = vrc.vrc_sync(ctx, stream)
         assert rc == vrc.VRC_OK and st["overflow"] == 0, (rc, st)
         dt = e0.elapsed_time(e1) / 1e3
-        out[name] = {"segments_per_s": st["segments"] / dt, "ms_per_step": 1e3 * dt / steps,
-                     "wall_ms_per_step": 1e3 * wall / steps, "segments_per_step": st["segments"] / steps,
-                     "steps": steps, "launches": vrc.vrc_launch_count() - l0}
+        out[name] = {"segments_per_s": st["segments"] / dt, "ms_per_step": 1e3 * dt / n,
+                     "wall_ms_per_step": 1e3 * wall / n, "segments_per_step": st["segments"] / n,
+                     "steps": n, "launches": vrc.vrc_launch_count() - l0}
     _, _, samples = vrc.vrc_moments_read(ctx)
-    H = out["history"]
-    line = {
-        "metric": "per-history moments: ray-cell segments/s", "value": H["segments_per_s"],
-        "unit": UNIT, "n_gpus": world, "steps": H["steps"], "warmup": args.warmup,
-        "ms_per_step": H["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": HISTORY, "rays_per_step": prob.n_rays, "calls_per_step": len(parts),
-                   "histories_per_step": int(hist[-1]) + 1, "form": "fp32", "sort": "auto (each call)"},
-        "history_over_tally_time": H["ms_per_step"] / out["tally"]["ms_per_step"],
-        "modes": out, "histories_folded": samples, "gpu_launches": H["launches"],
-    }
     ctx.close()
+    n_calls = len(parts)
+    del dev, hdev, parts
+    torch.cuda.empty_cache()
+    H = out["history"]
+    return {"workload": HISTORY, "form": "fp32", "value": H["segments_per_s"], "unit": UNIT,
+            "ms_per_step": H["ms_per_step"], "segments_per_step": H["segments_per_step"],
+            "rays_per_step": prob.n_rays, "calls_per_step": n_calls,
+            "histories_per_step": int(hist[-1]) + 1, "steps": H["steps"],
+            "history_over_tally_time": H["ms_per_step"] / out["tally"]["ms_per_step"],
+            "modes": out, "histories_folded": samples, "gpu_launches": H["launches"],
+            "parity": "tests/test_history_moments_gpu.py (the oracle's per-history moments are "
+                      "per-history full casts, too slow at this size)"}
+
+
+def run_history(args, rank, world, local):
+    """The per-history workload on its own (measure_history), one JSON line."""
+    import torch
+    from paper_1706_07476_gb300 import vrc
+    torch.cuda.set_device(local)
+    prob = workload(args)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    m = measure_history(args, torch, vrc, local, prob, stream, args.steps, args.warmup)
+    line = {
+        "metric": "per-history moments: ray-cell segments/s", "value": m["value"],
+        "unit": UNIT, "n_gpus": world, "steps": m["steps"], "warmup": args.warmup,
+        "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": HISTORY, "rays_per_step": prob.n_rays, "calls_per_step": m["calls_per_step"],
+                   "histories_per_step": m["histories_per_step"], "form": "fp32", "sort": "auto (each call)"},
+        "history_over_tally_time": m["history_over_tally_time"],
+        "modes": m["modes"], "histories_folded": m["histories_folded"], "gpu_launches": m["gpu_launches"],
+    }
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1046,6 +1064,7 @@ def main():
         m["workload"] = BATCHED
         configs["batched1024"] = m
         configs["surrogate32"] = measure_surrogate(args, torch, vrc, local, stream, cs, cw, oracle)
+        configs["history"] = measure_history(args, torch, vrc, local, prob, stream, cs, cw)
         line["configs"] = configs
     if rank == 0:
         print(json.dumps(line), flush=True)
