@@ -86,7 +86,8 @@ typedef struct {
                              one grid further); R > 0, a multiple of 32 up to 65,536: each warp
                              takes R consecutive (sorted) rays at a time from a device counter,
                              so warps that finish early take more work; 0 auto (default:
-                             32 in the plain form, interleaved in the FP32 form) */
+                             32 in the plain form and for FP32 casts of 2^23 rays or more,
+                             interleaved for smaller FP32 casts) */
 } vrc_options;
 
 /* A uniform 3-D Cartesian mesh (Sec. 3: 3-D Cartesian mesh geometry).

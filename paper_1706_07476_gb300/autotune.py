@@ -37,7 +37,7 @@ CAST_SPACE = {
     "block": [128, 256],
     "rays_per_warp": [-1, 32, 128, 512, 2048],
 }
-CAST_DEFAULT = {"sort_len_buckets": 64, "block": 256, "rays_per_warp": -1}
+CAST_DEFAULT = {"sort_len_buckets": 64, "block": 256, "rays_per_warp": 32}
 
 
 def _gpu_name(torch) -> str:

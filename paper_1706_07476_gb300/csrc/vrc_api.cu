@@ -146,12 +146,19 @@ CastArgs make_args(const vrc_ctx *c, const RayPtrs &rays) {
   a.rays = rays;
   a.tally = c->d_tally;
   a.stop_zero = c->opt.stop_at_zero;
-  // auto: warps take 32 sorted rays at a time from the counter in the plain
-  // form (2 % faster on slab256: warps of the FP64-bound walk finish at
-  // different times), interleaved in the FP32 form (chunks lose the tally
-  // slice's L2 locality there)
+  // auto: in the plain form, and in the FP32 form for casts of 2^23 rays or
+  // more, warps take 32 sorted rays at a time from the counter.  The warps
+  // then work on one contiguous window of the sorted order, whose group's
+  // tally slice stays in L2, and warps that finish early take more rays.
+  // Smaller FP32 casts use interleaved rounds, whose warps have too few
+  // rounds to drift apart.  Measured (FP32 cast, one box): 2^24 slab256
+  // rays 15.9 against 17.1 ms interleaved (18.3 ms for chunks of 64),
+  // graded 42.3 against 51.1 ms, pin lattice 33.1 against 38.3 ms; 2^22
+  // rays 4.50 against 4.36 ms, 2^20 rays 1.29 against 1.21 ms.  Plain form:
+  // 2 % faster than interleaved at 2^24 rays.
   a.rays_per_warp = c->opt.rays_per_warp > 0 ? c->opt.rays_per_warp
-                    : (c->opt.rays_per_warp == 0 && c->opt.form == VRC_FORM_PLAIN ? 32 : 0);
+                    : (c->opt.rays_per_warp == 0 &&
+                       (c->opt.form == VRC_FORM_PLAIN || rays.n >= kAutoChunkMinRays) ? 32 : 0);
   a.queue = c->d_queue;
   a.counters = c->d_counters;
   a.status = c->d_status;

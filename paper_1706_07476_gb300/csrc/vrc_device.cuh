@@ -79,6 +79,13 @@ __device__ __forceinline__ float df_diff(df a, df b) {
   return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
 }
 
+// |(u, v, w)| in float32 with the products and sums in a fixed order (u^2
+// rounded, then two fused multiply-adds), so that every inlined copy of the
+// walk, whatever the compiler would otherwise contract, gets the same bits.
+__device__ __forceinline__ float norm3(float u, float v, float w) {
+  return sqrtf(__fmaf_rn(w, w, __fmaf_rn(v, v, __fmul_rn(u, u))));
+}
+
 // floor(a) clamped to [0, n-1].
 __device__ __forceinline__ int df_floor_clamp(df a, int n) {
   float f = floorf(a.hi);
@@ -785,7 +792,7 @@ __device__ __forceinline__ bool ray_setup(const CastArgs &a, int64_t r, const in
   load_ray(a.rays, r, f);
   const float x = f[0], y = f[1], z = f[2], u = f[3], v = f[4], w = f[5], E = f[6], wt = f[7];
   ++c.rays;
-  const float dn = sqrtf(u * u + v * v + w * w);
+  const float dn = norm3(u, v, w);
   if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(u) && isfinite(v) && isfinite(w) &&
         isfinite(E) && isfinite(wt) && E > 0.f && dn > 0.f && isfinite(dn))) {
     ++c.rej;
@@ -892,7 +899,7 @@ __device__ __forceinline__ df optical_depth(const MeshDev &M, const float p[3], 
                                             const float *sg, int stride, float tau_zero,
                                             bool *overflow) {
   const float d[3] = {q[0] - p[0], q[1] - p[1], q[2] - p[2]};
-  const float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  const float dn = norm3(d[0], d[1], d[2]);
   const df inf = {INFINITY, 0.f};
   df tau = {0.f, 0.f};
   df D[3], R[3];

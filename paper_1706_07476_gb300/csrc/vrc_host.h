@@ -233,6 +233,9 @@ int status_code(unsigned st);
 int sync_streams(vrc_ctx *c, void *stream);
 // Batches of at least this many rays are sorted when options.sort is -1.
 constexpr int64_t kAutoSortMin = 65536;
+// FP32 casts of at least this many rays hand rays to warps in chunks of 32
+// from a counter when options.rays_per_warp is 0 (auto).
+constexpr int64_t kAutoChunkMinRays = (int64_t)1 << 23;
 // Sorts the batch into context scratch and points rp at the sorted copy.
 // When carry_out is set, carry_in[i] (one uint32 per ray) goes to the sorted
 // position of ray i.

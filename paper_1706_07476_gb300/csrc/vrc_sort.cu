@@ -63,7 +63,7 @@ __device__ __forceinline__ uint32_t ray_key(const SortKeyArgs &P, const double *
   float f[8];
   load_ray(R, r, f);
   const float x = f[0], y = f[1], z = f[2], u = f[3], v = f[4], w = f[5], E = f[6], wt = f[7];
-  const float dn = sqrtf(u * u + v * v + w * w);
+  const float dn = norm3(u, v, w);
   const uint32_t reject = (uint32_t)(P.n_keys - 1);
   if (P.blocks_axis > 0) {  // point events: position, energy and weight only
     if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(E) && isfinite(wt) && E > 0.f)) return reject;
