@@ -72,7 +72,7 @@ typedef struct {
                              crossed) before the cast: 0 off, 1 on, -1 auto (on for batches
                              of 65,536 rays or more; default) */
   int32_t sort_len_buckets; /* crossed-cell buckets per group in the sort key, 1..256;
-                               -1 auto (64, fewer when groups x buckets would pass 16,384) */
+                               -1 auto (256, fewer when groups x buckets would pass 16,384) */
   int32_t block;          /* threads per block of the cast kernel; 0 auto */
   int32_t blocks_per_sm;  /* resident blocks per SM for the cast grid; 0 auto */
   int32_t device;         /* CUDA device ordinal for this context; -1 = current device */

@@ -33,11 +33,11 @@ BATCH_SPACE = {
 # rays_per_warp: -1 interleaved assignment; R > 0, each warp takes R
 # consecutive sorted rays at a time from a device counter
 CAST_SPACE = {
-    "sort_len_buckets": [8, 32, 64, 128],
+    "sort_len_buckets": [8, 32, 64, 128, 256],
     "block": [128, 256],
-    "rays_per_warp": [-1, 32, 128, 512, 2048],
+    "rays_per_warp": [-1, 32, 64, 128, 512, 2048],
 }
-CAST_DEFAULT = {"sort_len_buckets": 64, "block": 256, "rays_per_warp": 32}
+CAST_DEFAULT = {"sort_len_buckets": 256, "block": 256, "rays_per_warp": 32}
 
 
 def _gpu_name(torch) -> str:

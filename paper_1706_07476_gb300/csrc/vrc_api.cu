@@ -197,7 +197,7 @@ int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in,
     P.n[k] = c->n[k];
   }
   P.n_groups = c->n_groups;
-  int nl = c->opt.sort_len_buckets > 0 ? c->opt.sort_len_buckets : 64;
+  int nl = c->opt.sort_len_buckets > 0 ? c->opt.sort_len_buckets : kAutoLenBuckets;
   while (nl > 1 && (int64_t)c->n_groups * nl + 1 > 16384) nl >>= 1;
   P.n_len = nl;
   const int max_cells = c->n[0] + c->n[1] + c->n[2] + 1;
@@ -762,7 +762,7 @@ int vrc::ctx_sort_args(const vrc_ctx *c, SortKeyArgs *P, const double **edges, i
     P->n[k] = c->n[k];
   }
   P->n_groups = c->n_groups;
-  int nl = c->opt.sort_len_buckets > 0 ? c->opt.sort_len_buckets : 64;
+  int nl = c->opt.sort_len_buckets > 0 ? c->opt.sort_len_buckets : kAutoLenBuckets;
   while (nl > 1 && (int64_t)c->n_groups * nl + 1 > 16384) nl >>= 1;
   P->n_len = nl;
   const int max_cells = c->n[0] + c->n[1] + c->n[2] + 1;

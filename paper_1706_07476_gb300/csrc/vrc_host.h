@@ -233,6 +233,11 @@ int status_code(unsigned st);
 int sync_streams(vrc_ctx *c, void *stream);
 // Batches of at least this many rays are sorted when options.sort is -1.
 constexpr int64_t kAutoSortMin = 65536;
+// Crossed-cell buckets per group of the sort key when options.sort_len_buckets
+// is -1 (halved while groups x buckets + 1 would pass the key limit).
+// slab256, chunks of 32 rays per warp: 256 buckets 16.9 ms (FP32) and 44.7 ms
+// (plain) per sort and cast, 64 buckets 17.0 and 45.0 ms.
+constexpr int kAutoLenBuckets = 256;
 // FP32 casts of at least this many rays hand rays to warps in chunks of 32
 // from a counter when options.rays_per_warp is 0 (auto).
 constexpr int64_t kAutoChunkMinRays = (int64_t)1 << 23;
