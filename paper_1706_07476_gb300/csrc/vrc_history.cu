@@ -120,14 +120,14 @@ __global__ void k_ray_caps(BoundGeom G, RayPtrs R, uint32_t *cap) {
 
 // ---- fold of the per-history pairs ------------------------------------------
 // A counting sort puts the pairs into buckets of 2^shift consecutive bins
-// (block c takes rays c * kPairChunkRays .., one warp per ray, its pairs read
-// by consecutive lanes); then one block per bucket sums the scores of equal
-// keys (history, bin) in a shared-memory hash table and adds (x, x^2) to the
-// bin's moments.  A bucket's bins are a contiguous stretch of the moment
+// (the cast counts each bucket's pairs; a scan gives the buckets' first
+// slots; k_pair_scatter moves the pairs); then one block per bucket sums
+// the scores of equal keys (history, bin) in a shared-memory hash table and
+// adds (x, x^2) to the bin's moments.  A bucket's bins are a contiguous stretch of the moment
 // array, so those reductions stay in L2.  A bucket with more keys than 0.7
 // of the table is folded in several passes, each over the keys whose hash
 // falls in that pass.
-constexpr int kFoldThreads = 256;
+constexpr int kFoldThreads = 256;  // threads per block of the scatter
 // The fold's shared-memory hash table (16 bytes a slot), threads and blocks
 // per SM.  Small blocks, many per SM, each on a small bucket (kPairMaxBuckets
 // of them: about 150 keys each for 2^20 slab256 rays, filling 60 % of a

@@ -157,10 +157,11 @@ cudaError_t launch_per_volume_rect(const double *src, double *dst, int64_t n, in
                                    const double *wz, cudaStream_t s);
 // Tally moments (vrc_history.cu): mom[bin] = (S1, S2), the sums of the
 // samples and of their squares per (group, cell).  Batch moments: the fold
-// mom += (t, t^2), t = 0.  Per-history moments: an upper bound of each
-// ray's segments (cap), the cast that writes each ray's (key, score) pairs
-// (vrc_cast.cu), a counting sort of the pairs into buckets of 2^shift
-// consecutive bins, and per bucket the sum x of every (history, bin) and
+// mom += (t, t^2), t = 0.  Per-history moments: each ray's room in the pair
+// buffer (a fixed stretch, or an upper bound of its segments, cap), the cast
+// that writes each ray's (key, score) pairs and counts them per bucket of
+// 2^shift consecutive bins (vrc_cast.cu), the scatter of the pairs into
+// their buckets, and per bucket the sum x of every (history, bin) and
 // mom[bin] += (x, x^2).
 cudaError_t launch_fold_moments(double *tally, double2 *mom, int64_t n, cudaStream_t s);
 struct BoundGeom {

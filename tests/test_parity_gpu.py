@@ -288,6 +288,26 @@ def test_sort_on_off_same_tally(vrc, torch_cuda, slab_small, form):
     assert_parity(want, b)
 
 
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_ray_assignment_same_tally(vrc, torch_cuda, slab_small, form):
+    """How the cast hands rays to warps (interleaved rounds, or chunks of 32,
+    64 or 2048 sorted rays from a counter) changes only the float64
+    summation order: every ray's scores are the same bits in each loop, so
+    the tallies agree to rounding of the sums and the segment counts
+    exactly."""
+    prob, want, st = slab_small
+    out = {}
+    for rpw in (-1, 32, 64, 2048):
+        t, rc, sx = run_gpu(vrc, torch_cuda, prob, FORMS[form],
+                            options=vrc.vrc_default_options(form=FORMS[form], sort=1, rays_per_warp=rpw))
+        assert rc == vrc.VRC_OK
+        assert sx["segments"] == st["segments"] and sx["rays"] == prob.n_rays
+        out[rpw] = t
+    for rpw in (32, 64, 2048):
+        np.testing.assert_allclose(out[rpw], out[-1], rtol=1e-12, atol=1e-300)
+    assert_parity(want, out[32])
+
+
 def test_sort_with_rejected_and_out_of_group_rays(vrc, torch_cuda):
     """Rejected rays and rays outside every group land in the last key and are
     still reported; a ragged count that is not a multiple of the chunk."""
