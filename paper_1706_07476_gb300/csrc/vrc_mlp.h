@@ -17,8 +17,10 @@
 // lo = bf16(v - hi), two products into one accumulator, so the activations
 // keep about 16 significant bits (a single bfloat16 rounding, 2^-9, puts
 // about 1e-3 of noise on log sigma, the accepted error of the surrogate).
-// The 128 -> 16 output layer runs in float32 on the CUDA cores, W3 and h2 in
-// float32 (2,048 FMAs per ray).
+// The 128 -> 16 output layer: in training, float32 on the CUDA cores; in the
+// forward pass (vrc_mlp_tc.cu), on the tensor cores with h2 as a bfloat16
+// pair and W3 as three bfloat16 parts (hi, mid, lo; about 24 bits), five
+// products into one float32 accumulator.
 #pragma once
 
 #include <cuda_runtime.h>

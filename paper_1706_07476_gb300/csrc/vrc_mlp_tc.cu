@@ -2,11 +2,17 @@
 // fifth-generation tensor cores (tcgen05, accumulators in tensor memory).
 //
 // One persistent block per SM holds the bfloat16 weights once and runs two
-// independent groups of 128 threads (four warps each), each on its own tiles
+// independent groups of 512 threads (16 warps each), each on its own tiles
 // of 128 rays with its own operand buffer, mbarrier, named barrier and 128
-// tensor-memory columns.  Thread t of a group owns ray t of the tile, which
-// is row t of every matrix and lane t of the tensor memory (warp j of the
-// group reads lane quarter j).  Every activation enters the tensor cores as
+// tensor-memory columns.  Threads t, t + 128, t + 256 and t + 384 of a group
+// own ray t of the tile, which is row t of every matrix and lane t of the
+// tensor memory (warps j, j + 4, j + 8 and j + 12 of the group read lane
+// quarter j); each takes a quarter of the row's columns (features,
+// activations, outputs).  Eight warps per scheduler hide the latency of the
+// per-element work (sines, SiLU, the hi/lo splits); with one thread per row
+// (two warps per scheduler) it was exposed: 5.8 ms per 2^24 rays, against
+// 4.6 ms with two threads per row and 4.4 ms with four.
+// Every activation enters the tensor cores as
 // a pair of bfloat16 matrices, hi = bf16(v) and lo = bf16(v - hi), whose two
 // products go into one accumulator (about 16 significant bits per value).
 // Per tile:
@@ -18,9 +24,14 @@
 //      row's hi and lo parts to A1hi, A1lo;
 //   4. D = A1hi W2^T + A1lo W2^T (K = 128, eight steps each) into the same
 //      columns;
-//   5. each thread loads its row, h2 = SiLU(D + b2) in float32, and forms the
-//      float32 128 -> 16 output layer on the CUDA cores (2,048 FMAs), adds the
-//      1/v prior and writes log sigma or sigma.
+//   5. each thread loads its row, h2 = SiLU(D + b2), and writes its hi and lo
+//      parts to A2hi, A2lo (A1's bytes: the layer-2 MMAs have completed);
+//   6. D3 = A2 W3^T (M = 128, N = 16, K = 128) with W3 held as three
+//      bfloat16 parts (hi, mid, lo: about 24 significant bits): the five
+//      products A2hi W3hi, A2hi W3mid, A2hi W3lo, A2lo W3hi, A2lo W3mid into
+//      the group's first 16 columns;
+//   7. each thread loads its 16 outputs, adds b3 and the 1/v prior and writes
+//      log sigma or sigma.
 // Operands live in shared memory in the canonical K-major layout without
 // swizzle: 8-row x 16-byte core matrices, consecutive along K 128 bytes
 // apart (leading byte offset) and along rows K*16 bytes apart (stride byte
@@ -41,25 +52,28 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int kTile = 128;            // rays per tile: the MMA's M and the tensor-memory lanes
 constexpr int kGroups = 2;            // independent groups of 128 threads per block
-constexpr int kTcThreads = 128 * kGroups;
+constexpr int kHalves = 4;             // threads per ray row: each takes a quarter of the row's columns
+constexpr int kGroupThreads = 128 * kHalves;
+constexpr int kTcThreads = kGroupThreads * kGroups;
 constexpr uint32_t kTmemCols = 256;   // allocated once per block; group g uses columns 128 g ..
 constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before a wait gives up
 
 // shared memory (bytes from the block's base)
 constexpr uint32_t kSW1 = 0;          // W1 [128][64] bfloat16, 16 KiB
 constexpr uint32_t kSW2 = 16384;      // W2 [128][128], 32 KiB
-constexpr uint32_t kSW3 = 49152;      // W3 transposed, [128][16] float32, 8 KiB
-constexpr uint32_t kSB = 57344;       // b1, b2, b3, then the prior C [16][2] (float32, 304 values)
-constexpr uint32_t kSBar = 58624;     // per group an mbarrier (8 B); then the tensor-memory address
+constexpr uint32_t kSW3 = 49152;      // W3 [16][128] as bfloat16 hi, mid, lo: 3 x 4 KiB
+constexpr uint32_t kW3Part = 4096;
+constexpr uint32_t kSB = 61440;       // b1, b2, b3, then the prior C [16][2] (float32, 304 values)
+constexpr uint32_t kSBar = 62720;     // per group an mbarrier (8 B); then the tensor-memory address
 // Per group one 64 KiB operand buffer: A1hi [128][128] at 0 and A1lo at
 // 32 KiB; A0hi [128][64] at 0 and A0lo at 16 KiB share A1hi's bytes (A0 is
 // read only by the layer-1 MMAs, which have completed before A1 is written;
 // A1 is read only by the layer-2 MMAs, which have completed before the next
 // tile's A0 is written).
-constexpr uint32_t kSGroup = 59392;
+constexpr uint32_t kSGroup = 63488;
 constexpr uint32_t kGroupBytes = 65536;
 constexpr uint32_t kA0Lo = 16384, kA1Lo = 32768;
-constexpr uint32_t kSmemTc = kSGroup + kGroups * kGroupBytes;  // 190,464
+constexpr uint32_t kSmemTc = kSGroup + kGroups * kGroupBytes;  // 194,560
 
 // Byte offset of element (r, k) of a K-column matrix in the core-matrix layout.
 __device__ __forceinline__ uint32_t cm_off(int r, int k, int K) {
@@ -94,12 +108,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 // and B (bits 7-9 and 10-12 = 1), both K-major, N / 8 at bits 17-22, M / 16
 // at bits 24-28.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdesc16 = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16_tc(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16_tc(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate,
+                                            uint32_t idesc = kIdesc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      :: "r"(tmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      :: "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -139,6 +155,50 @@ __device__ __forceinline__ void tmem_ld32(uint32_t (&r)[32], uint32_t taddr) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// N = 4 or 8 consecutive float32 columns of this thread's lane.
+template <int N>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t (&r)[N], uint32_t taddr);
+template <>
+__device__ __forceinline__ void tmem_ld_cols<8>(uint32_t (&r)[8], uint32_t taddr) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_ld_cols<4>(uint32_t (&r)[4], uint32_t taddr) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Stages W3 [16][128] (float32) as three bfloat16 parts w = hi + mid + lo
+// (hi = bf16(w), mid = bf16(w - hi), lo = bf16(w - hi - mid)), each in core
+// matrices of K = 128 columns.
+__device__ __forceinline__ void stage_w3(unsigned char *smem, const float *W) {
+  for (int i = threadIdx.x; i < kOut * kHid / 8; i += blockDim.x) {
+    const int r = i / (kHid / 8), k = (i % (kHid / 8)) * 8;
+    uint32_t h[4], m[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float w0 = W[r * kHid + k + 2 * e], w1 = W[r * kHid + k + 2 * e + 1];
+      const __nv_bfloat162 hb = __floats2bfloat162_rn(w0, w1);
+      const float2 hf = __bfloat1622float2(hb);
+      const float r0 = w0 - hf.x, r1 = w1 - hf.y;  // exact
+      const __nv_bfloat162 mb = __floats2bfloat162_rn(r0, r1);
+      const float2 mf = __bfloat1622float2(mb);
+      h[e] = *reinterpret_cast<const uint32_t *>(&hb);
+      m[e] = *reinterpret_cast<const uint32_t *>(&mb);
+      l[e] = pack2(r0 - mf.x, r1 - mf.y);
+    }
+    const uint32_t o = kSW3 + cm_off(r, k, kHid);
+    *reinterpret_cast<uint4 *>(smem + o) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(smem + o + kW3Part) = make_uint4(m[0], m[1], m[2], m[3]);
+    *reinterpret_cast<uint4 *>(smem + o + 2 * kW3Part) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
 // Stages a [128][K] float32 weight block as bfloat16 core matrices.
 __device__ __forceinline__ void stage_weights(unsigned char *smem, uint32_t off, const float *W, int K) {
   const int chunks = kTile * K / 8;
@@ -150,31 +210,32 @@ __device__ __forceinline__ void stage_weights(unsigned char *smem, uint32_t off,
   }
 }
 
-// Barrier of the 128 threads of one group (named barrier 1 + g); returns
+// Barrier of the threads of one group (named barrier 1 + g); returns
 // nonzero in every thread of the group if any thread passed nonzero.
 __device__ __forceinline__ uint32_t group_sync_or(int g, uint32_t v) {
   uint32_t any;
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t"
-      "bar.red.popc.u32 %0, %1, 128, p;\n\t}"
-      : "=r"(any) : "r"(1 + g), "r"(v) : "memory");
+      "bar.red.popc.u32 %0, %1, %3, p;\n\t}"
+      : "=r"(any) : "r"(1 + g), "r"(v), "r"(kGroupThreads) : "memory");
   return any;
 }
 
 __device__ __forceinline__ void group_sync(int g) {
-  asm volatile("bar.sync %0, 128;" :: "r"(1 + g) : "memory");
+  asm volatile("bar.sync %0, %1;" :: "r"(1 + g), "r"(kGroupThreads) : "memory");
 }
 
-__global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_apply_tc(ApplyArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int g = tid >> 7, gt = tid & 127;  // group, thread (= row) within the group
+  const int g = tid / kGroupThreads, gt = tid % kGroupThreads;  // group, thread within the group
+  const int rt = gt & 127, half = gt >> 7;
+  static_assert(kHalves == 2 || kHalves == 4, "a row is split into 2 or 4 parts");  // the thread's row in the tile; its part of the columns
   // rows to evaluate: all n, or the device count (e.g. the accepted rays of a cast)
   const int64_t n = a.n_limit ? min(a.n, (int64_t)*a.n_limit) : a.n;
   const int64_t tiles = (n + kTile - 1) / kTile;
   if ((int64_t)blockIdx.x * kGroups >= tiles) return;  // the whole block has no tile
 
-  float *W3f = reinterpret_cast<float *>(smem + kSW3);
   float *bs = reinterpret_cast<float *>(smem + kSB);
   const uint32_t bar = smem_u32(smem + kSBar + 8 * g);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + kSBar + 8 * kGroups);
@@ -184,8 +245,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
 
   stage_weights(smem, kSW1, P + kOffW1, kEmb);
   stage_weights(smem, kSW2, P + kOffW2, kHid);
-  for (int i = tid; i < kOut * kHid; i += kTcThreads)  // W3[m][k] -> W3f[k][m], float32
-    W3f[(i % kHid) * kOut + i / kHid] = P[kOffW3 + i];
+  stage_w3(smem, P + kOffW3);
   for (int i = tid; i < kHid; i += kTcThreads) { bs[i] = P[kOffB1 + i]; bs[kHid + i] = P[kOffB2 + i]; }
   if (tid < kOut) bs[2 * kHid + tid] = P[kOffB3 + tid];
   if (tid < 2 * kOut) bs[2 * kHid + kOut + tid] = P[kOffC + tid];
@@ -202,17 +262,18 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
   const uint32_t tmem = *tslot + 128u * (uint32_t)g;                     // the group's columns
   const uint32_t tmem_row = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lane quarter
   const uint32_t sA0 = smem_u32(A0), sA1 = smem_u32(A1);
-  const uint32_t sW1 = smem_u32(smem + kSW1), sW2 = smem_u32(smem + kSW2);
+  const uint32_t sW1 = smem_u32(smem + kSW1), sW2 = smem_u32(smem + kSW2), sW3 = smem_u32(smem + kSW3);
   const float *C = bs + 2 * kHid + kOut;  // prior (a_m, b_m)
+  uint32_t phase = 0;  // parity of the group's next mbarrier phase (three commits per tile)
 
   for (int64_t tile = (int64_t)blockIdx.x * kGroups + g; tile < tiles; tile += (int64_t)gridDim.x * kGroups) {
-    const int64_t row = tile * kTile + gt;
+    const int64_t row = tile * kTile + rt;
     const float E = row < n ? (a.aos ? __ldg(a.aos + 2 * row + 1).z : a.E[row]) : 1.0f;
 
     // 1. embedding row: features 2f, 2f + 1 = sin, cos of pi f_f x, as hi and lo
     const float x = embed_x(a.emb, E);
 #pragma unroll
-    for (int kc = 0; kc < kEmb / 8; ++kc) {
+    for (int kc = half * (kEmb / 8 / kHalves); kc < (half + 1) * (kEmb / 8 / kHalves); ++kc) {
       uint32_t wh[4], wl[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -220,7 +281,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
         embed_pair_x(a.emb, x, kc * 4 + q, &sn, &cs);
         split2(sn, cs, wh[q], wl[q]);
       }
-      const uint32_t o = cm_off(gt, kc * 8, kEmb);
+      const uint32_t o = cm_off(rt, kc * 8, kEmb);
       *reinterpret_cast<uint4 *>(A0 + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
       *reinterpret_cast<uint4 *>(A0 + kA0Lo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
     }
@@ -241,15 +302,16 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
                     smem_desc(sW1 + kk * 256, 128, kEmb * 16), 1);
       mma_commit(bar);
     }
-    if (group_sync_or(g, !wait_phase(bar, 0))) {
+    if (group_sync_or(g, !wait_phase(bar, phase))) {
       if (gt == 0 && a.status) atomicOr(a.status, kStatusTimeout);
       break;
     }
+    phase ^= 1u;
     fence_after();
 
     // 3. h1 = SiLU(D + b1) as hi and lo bfloat16 into A1hi, A1lo
 #pragma unroll
-    for (int c = 0; c < kHid / 32; ++c) {
+    for (int c = half * (kHid / 32 / kHalves); c < (half + 1) * (kHid / 32 / kHalves); ++c) {
       uint32_t r[32];
       tmem_ld32(r, tmem_row + c * 32);
 #pragma unroll
@@ -260,7 +322,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
           const int j = q * 8 + 2 * e, k = c * 32 + j;
           split2(silu(__uint_as_float(r[j]) + bs[k]), silu(__uint_as_float(r[j + 1]) + bs[k + 1]), wh[e], wl[e]);
         }
-        const uint32_t o = cm_off(gt, c * 32 + q * 8, kHid);
+        const uint32_t o = cm_off(rt, c * 32 + q * 8, kHid);
         *reinterpret_cast<uint4 *>(A1 + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
         *reinterpret_cast<uint4 *>(A1 + kA1Lo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
       }
@@ -282,34 +344,65 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
                     smem_desc(sW2 + kk * 256, 128, kHid * 16), 1);
       mma_commit(bar);
     }
-    if (group_sync_or(g, !wait_phase(bar, 1))) {
+    if (group_sync_or(g, !wait_phase(bar, phase))) {
       if (gt == 0 && a.status) atomicOr(a.status, kStatusTimeout);
       break;
     }
+    phase ^= 1u;
     fence_after();
 
-    // 5. h2 = SiLU(D + b2) in float32, W3 h2 + b3 on the CUDA cores
-    float p[kOut];
+    // 5. h2 = SiLU(D + b2) as hi and lo bfloat16 into A2hi, A2lo (A1's bytes)
 #pragma unroll
-    for (int m = 0; m < kOut; ++m) p[m] = bs[2 * kHid + m];
-#pragma unroll
-    for (int c = 0; c < kHid / 32; ++c) {
+    for (int c = half * (kHid / 32 / kHalves); c < (half + 1) * (kHid / 32 / kHalves); ++c) {
       uint32_t r[32];
       tmem_ld32(r, tmem_row + c * 32);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int k = c * 32 + j;
-        const float h = silu(__uint_as_float(r[j]) + bs[kHid + k]);
-        const float4 *w = reinterpret_cast<const float4 *>(W3f + k * kOut);  // 16 weights, 4 loads
+      for (int q = 0; q < 4; ++q) {
+        uint32_t wh[4], wl[4];
 #pragma unroll
-        for (int q = 0; q < kOut / 4; ++q) {
-          const float4 wq = w[q];
-          p[4 * q] = fmaf(wq.x, h, p[4 * q]);
-          p[4 * q + 1] = fmaf(wq.y, h, p[4 * q + 1]);
-          p[4 * q + 2] = fmaf(wq.z, h, p[4 * q + 2]);
-          p[4 * q + 3] = fmaf(wq.w, h, p[4 * q + 3]);
+        for (int e = 0; e < 4; ++e) {
+          const int j = q * 8 + 2 * e, k = c * 32 + j;
+          split2(silu(__uint_as_float(r[j]) + bs[kHid + k]), silu(__uint_as_float(r[j + 1]) + bs[kHid + k + 1]),
+                 wh[e], wl[e]);
         }
+        const uint32_t o = cm_off(rt, c * 32 + q * 8, kHid);
+        *reinterpret_cast<uint4 *>(A1 + o) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+        *reinterpret_cast<uint4 *>(A1 + kA1Lo + o) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
       }
+    }
+    fence_async_smem();
+    fence_before();
+    group_sync(g);
+
+    // 6. D3 = A2 W3^T (N = 16): A2hi (W3hi + W3mid + W3lo) + A2lo (W3hi + W3mid)
+    if (gt == 0) {
+      fence_after();
+#pragma unroll 1
+      for (int part = 0; part < 5; ++part) {
+        const uint32_t sa = sA1 + (part < 3 ? 0u : kA1Lo);
+        const uint32_t sb = sW3 + (uint32_t)(part < 3 ? part : part - 3) * kW3Part;
+#pragma unroll
+        for (int kk = 0; kk < kHid / 16; ++kk)
+          mma_bf16_tc(tmem, smem_desc(sa + kk * 256, 128, kHid * 16), smem_desc(sb + kk * 256, 128, kHid * 16),
+                      part > 0 || kk > 0, kIdesc16);
+      }
+      mma_commit(bar);
+    }
+    if (group_sync_or(g, !wait_phase(bar, phase))) {
+      if (gt == 0 && a.status) atomicOr(a.status, kStatusTimeout);
+      break;
+    }
+    phase ^= 1u;
+    fence_after();
+
+    // 7. this thread's kPer of the 16 outputs (part h: outputs kPer h ..) plus b3
+    constexpr int kPer = kOut / kHalves;
+    float p[kPer];
+    {
+      uint32_t r[kPer];
+      tmem_ld_cols<kPer>(r, tmem_row + (uint32_t)(half * kPer));
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) p[j] = __uint_as_float(r[j]) + bs[2 * kHid + half * kPer + j];
     }
     fence_before();
 
@@ -317,7 +410,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
       const float rs = rsqrtf(E);
       if (a.mode == 1) {
         bool flagged = false;
-        if (a.flags) {
+        if (a.flags && half == 0) {
           const double e = (double)E;
           if (!(e >= a.e_first && e <= a.e_last)) {
             flagged = true;
@@ -328,16 +421,21 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_apply_tc(ApplyArgs a) {
           }
         }
 #pragma unroll
-        for (int m = 0; m < kOut; ++m)
-          p[m] = ((a.mat_mask >> m) & 1u) ? fmaf(C[2 * m + 1], rs, C[2 * m]) * expf(p[m]) : 0.f;
-        if (flagged) p[0] = __int_as_float(0x7fc00000);
+        for (int j = 0; j < kPer; ++j) {
+          const int m = half * kPer + j;
+          p[j] = ((a.mat_mask >> m) & 1u) ? fmaf(C[2 * m + 1], rs, C[2 * m]) * expf(p[j]) : 0.f;
+        }
+        if (flagged) p[0] = __int_as_float(0x7fc00000);  // output 0 (half 0) marks a flagged bin
       } else {
 #pragma unroll
-        for (int m = 0; m < kOut; ++m) p[m] += logf(fmaf(C[2 * m + 1], rs, C[2 * m]));
+        for (int j = 0; j < kPer; ++j) {
+          const int m = half * kPer + j;
+          p[j] += logf(fmaf(C[2 * m + 1], rs, C[2 * m]));
+        }
       }
-      float4 *o = reinterpret_cast<float4 *>(a.out + row * kOut);
+      float4 *o = reinterpret_cast<float4 *>(a.out + row * kOut + half * kPer);
 #pragma unroll
-      for (int q = 0; q < kOut / 4; ++q) o[q] = make_float4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+      for (int q = 0; q < kPer / 4; ++q) o[q] = make_float4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
     }
   }
   // every tensor-memory read has completed (tcgen05.wait::ld) before the barrier
