@@ -21,6 +21,7 @@ namespace vrc {
 namespace {
 
 constexpr int kSortBlock = 256;
+constexpr int kSortUnroll = 4;  // rays each sort thread handles at a time
 
 __device__ __forceinline__ int floor_clamp_f(float c, int n) {
   float f = floorf(c);
@@ -112,10 +113,20 @@ __global__ void __launch_bounds__(kSortBlock) k_sort_count(RayPtrs R, SortKeyArg
   const double *edges = edges_g ? edges_s : nullptr;
   const int64_t begin = (int64_t)blockIdx.x * P.chunk;
   const int64_t end = min(begin + P.chunk, R.n);
-  for (int64_t r = begin + threadIdx.x; r < end; r += blockDim.x) {
-    uint32_t k = ray_key(P, edges, R, r);
-    keys[r] = k;
-    atomicAdd(&hist[k], 1u);
+  for (int64_t r0 = begin + threadIdx.x; r0 < end; r0 += (int64_t)kSortUnroll * blockDim.x) {
+    uint32_t k[kSortUnroll];
+#pragma unroll
+    for (int u = 0; u < kSortUnroll; ++u) {
+      const int64_t r = r0 + (int64_t)u * blockDim.x;
+      if (r < end) k[u] = ray_key(P, edges, R, r);
+    }
+#pragma unroll
+    for (int u = 0; u < kSortUnroll; ++u) {
+      const int64_t r = r0 + (int64_t)u * blockDim.x;
+      if (r >= end) break;
+      keys[r] = k[u];
+      atomicAdd(&hist[k[u]], 1u);
+    }
   }
   __syncthreads();
   const int nb = gridDim.x;
@@ -214,18 +225,31 @@ __global__ void __launch_bounds__(kSortBlock) k_sort_scatter(RayPtrs R, SortKeyA
   __syncthreads();
   const int64_t begin = (int64_t)blockIdx.x * P.chunk;
   const int64_t end = min(begin + P.chunk, R.n);
-  for (int64_t r = begin + threadIdx.x; r < end; r += blockDim.x) {
-    const uint32_t pos = atomicAdd(&cursor[keys[r]], 1u);
-    float f[8];
-    load_ray(R, r, f);
-    if (O.aos) {
-      O.aos[2 * (int64_t)pos] = make_float4(f[0], f[1], f[2], f[3]);
-      O.aos[2 * (int64_t)pos + 1] = make_float4(f[4], f[5], f[6], f[7]);
-    } else {
-      O.x[pos] = f[0]; O.y[pos] = f[1]; O.z[pos] = f[2]; O.u[pos] = f[3];
-      O.v[pos] = f[4]; O.w[pos] = f[5]; O.E[pos] = f[6]; O.wt[pos] = f[7];
+  // kSortUnroll rays per thread at a time: their keys and fields are loaded
+  // before any is placed
+  for (int64_t r0 = begin + threadIdx.x; r0 < end; r0 += (int64_t)kSortUnroll * blockDim.x) {
+    uint32_t key[kSortUnroll];
+    float f[kSortUnroll][8];
+#pragma unroll
+    for (int u = 0; u < kSortUnroll; ++u) {
+      const int64_t r = r0 + (int64_t)u * blockDim.x;
+      key[u] = r < end ? keys[r] : 0u;
+      if (r < end) load_ray(R, r, f[u]);
     }
-    if (O.carry_out) O.carry_out[pos] = O.carry_in[r];
+#pragma unroll
+    for (int u = 0; u < kSortUnroll; ++u) {
+      const int64_t r = r0 + (int64_t)u * blockDim.x;
+      if (r >= end) break;
+      const uint32_t pos = atomicAdd(&cursor[key[u]], 1u);
+      if (O.aos) {
+        O.aos[2 * (int64_t)pos] = make_float4(f[u][0], f[u][1], f[u][2], f[u][3]);
+        O.aos[2 * (int64_t)pos + 1] = make_float4(f[u][4], f[u][5], f[u][6], f[u][7]);
+      } else {
+        O.x[pos] = f[u][0]; O.y[pos] = f[u][1]; O.z[pos] = f[u][2]; O.u[pos] = f[u][3];
+        O.v[pos] = f[u][4]; O.w[pos] = f[u][5]; O.E[pos] = f[u][6]; O.wt[pos] = f[u][7];
+      }
+      if (O.carry_out) O.carry_out[pos] = O.carry_in[r];
+    }
   }
 }
 
