@@ -51,9 +51,9 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 constexpr int kTile = 128;            // rays per tile: the MMA's M and the tensor-memory lanes
-constexpr int kGroups = 2;            // independent groups of 128 threads per block
-constexpr int kHalves = 4;             // threads per ray row: each takes a quarter of the row's columns
-constexpr int kGroupThreads = 128 * kHalves;
+constexpr int kGroups = 2;            // independent groups of kGroupThreads threads per block
+constexpr int kRowParts = 4;          // threads per ray row: each takes a quarter of the row's columns
+constexpr int kGroupThreads = 128 * kRowParts;
 constexpr int kTcThreads = kGroupThreads * kGroups;
 constexpr uint32_t kTmemCols = 256;   // allocated once per block; group g uses columns 128 g ..
 constexpr int kWaitLimit = 1 << 22;   // mbarrier polls before a wait gives up
@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_apply_tc(ApplyArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int g = tid / kGroupThreads, gt = tid % kGroupThreads;  // group, thread within the group
-  const int rt = gt & 127, half = gt >> 7;
-  static_assert(kHalves == 2 || kHalves == 4, "a row is split into 2 or 4 parts");  // the thread's row in the tile; its part of the columns
+  const int rt = gt & 127, part = gt >> 7;  // the thread's row in the tile; its part of the columns
+  static_assert(kRowParts == 2 || kRowParts == 4, "a row is split into 2 or 4 parts");
   // rows to evaluate: all n, or the device count (e.g. the accepted rays of a cast)
   const int64_t n = a.n_limit ? min(a.n, (int64_t)*a.n_limit) : a.n;
   const int64_t tiles = (n + kTile - 1) / kTile;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_apply_tc(ApplyArgs a) {
     // 1. embedding row: features 2f, 2f + 1 = sin, cos of pi f_f x, as hi and lo
     const float x = embed_x(a.emb, E);
 #pragma unroll
-    for (int kc = half * (kEmb / 8 / kHalves); kc < (half + 1) * (kEmb / 8 / kHalves); ++kc) {
+    for (int kc = part * (kEmb / 8 / kRowParts); kc < (part + 1) * (kEmb / 8 / kRowParts); ++kc) {
       uint32_t wh[4], wl[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_apply_tc(ApplyArgs a) {
 
     // 3. h1 = SiLU(D + b1) as hi and lo bfloat16 into A1hi, A1lo
 #pragma unroll
-    for (int c = half * (kHid / 32 / kHalves); c < (half + 1) * (kHid / 32 / kHalves); ++c) {
+    for (int c = part * (kHid / 32 / kRowParts); c < (part + 1) * (kHid / 32 / kRowParts); ++c) {
       uint32_t r[32];
       tmem_ld32(r, tmem_row + c * 32);
 #pragma unroll
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_apply_tc(ApplyArgs a) {
 
     // 5. h2 = SiLU(D + b2) as hi and lo bfloat16 into A2hi, A2lo (A1's bytes)
 #pragma unroll
-    for (int c = half * (kHid / 32 / kHalves); c < (half + 1) * (kHid / 32 / kHalves); ++c) {
+    for (int c = part * (kHid / 32 / kRowParts); c < (part + 1) * (kHid / 32 / kRowParts); ++c) {
       uint32_t r[32];
       tmem_ld32(r, tmem_row + c * 32);
 #pragma unroll
@@ -396,13 +396,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_apply_tc(ApplyArgs a) {
     fence_after();
 
     // 7. this thread's kPer of the 16 outputs (part h: outputs kPer h ..) plus b3
-    constexpr int kPer = kOut / kHalves;
+    constexpr int kPer = kOut / kRowParts;
     float p[kPer];
     {
       uint32_t r[kPer];
-      tmem_ld_cols<kPer>(r, tmem_row + (uint32_t)(half * kPer));
+      tmem_ld_cols<kPer>(r, tmem_row + (uint32_t)(part * kPer));
 #pragma unroll
-      for (int j = 0; j < kPer; ++j) p[j] = __uint_as_float(r[j]) + bs[2 * kHid + half * kPer + j];
+      for (int j = 0; j < kPer; ++j) p[j] = __uint_as_float(r[j]) + bs[2 * kHid + part * kPer + j];
     }
     fence_before();
 
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_apply_tc(ApplyArgs a) {
       const float rs = rsqrtf(E);
       if (a.mode == 1) {
         bool flagged = false;
-        if (a.flags && half == 0) {
+        if (a.flags && part == 0) {
           const double e = (double)E;
           if (!(e >= a.e_first && e <= a.e_last)) {
             flagged = true;
@@ -422,18 +422,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_apply_tc(ApplyArgs a) {
         }
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-          const int m = half * kPer + j;
+          const int m = part * kPer + j;
           p[j] = ((a.mat_mask >> m) & 1u) ? fmaf(C[2 * m + 1], rs, C[2 * m]) * expf(p[j]) : 0.f;
         }
-        if (flagged) p[0] = __int_as_float(0x7fc00000);  // output 0 (half 0) marks a flagged bin
+        if (flagged) p[0] = __int_as_float(0x7fc00000);  // output 0 (part 0) marks a flagged bin
       } else {
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-          const int m = half * kPer + j;
+          const int m = part * kPer + j;
           p[j] += logf(fmaf(C[2 * m + 1], rs, C[2 * m]));
         }
       }
-      float4 *o = reinterpret_cast<float4 *>(a.out + row * kOut + half * kPer);
+      float4 *o = reinterpret_cast<float4 *>(a.out + row * kOut + part * kPer);
 #pragma unroll
       for (int q = 0; q < kPer / 4; ++q) o[q] = make_float4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
     }
