@@ -487,6 +487,11 @@ typedef struct {
   int32_t sort_len_buckets; /* 0: no sort; 1..256: sort each problem's rays by (group,
                                crossed cells) into this many buckets first; -1 auto (16) */
   int32_t use_graph;        /* 1 (default): capture the sequence in a CUDA graph once */
+  int32_t rays_per_warp;    /* how a block hands a work item's rays to its warps: 0 (default)
+                               interleaved (warp w takes rays w*32 + lane, then one block
+                               further); R > 0, a multiple of 32 up to 8,192: each warp takes R
+                               consecutive rays at a time from the item's counter in shared
+                               memory, so warps that finish early take more of the item */
 } vrc_batch_options;
 
 void vrc_default_batch_options(vrc_batch_options *opt);

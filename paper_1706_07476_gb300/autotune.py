@@ -25,10 +25,13 @@ def cache_path() -> str:
     return os.environ.get("VRC_AUTOTUNE_CACHE",
                           os.path.join(os.path.expanduser("~"), ".cache", "vrc_autotune.json"))
 
+# rays_per_warp (batched): 0 interleaved within a work item; R > 0, each
+# warp takes R rays at a time from the item's shared counter
 BATCH_SPACE = {
     "sort_len_buckets": [0, 8, 16, 32],
     "chunk": [1024, 2048, 4096, 8192],
     "block": [128, 256],
+    "rays_per_warp": [0, 32, 128],
 }
 # rays_per_warp: -1 interleaved assignment; R > 0, each warp takes R
 # consecutive sorted rays at a time from a device counter
@@ -136,8 +139,8 @@ def tune_batched(torch, problems, ctxs, rays_list, form: int, reps: int = 2, use
                 stream.synchronize()
             batch.close()
 
-    best, ms, table = _descend(BATCH_SPACE, {"sort_len_buckets": 16, "chunk": 2048, "block": 256},
-                               measure)
+    best, ms, table = _descend(BATCH_SPACE, {"sort_len_buckets": 16, "chunk": 2048, "block": 256,
+                                             "rays_per_warp": 0}, measure)
     _store(key, {"options": best, "ms": ms, "when": time.time()})
     return best, ms, table
 

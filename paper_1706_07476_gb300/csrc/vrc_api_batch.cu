@@ -60,6 +60,8 @@ int check_batch_options(const vrc_batch_options *o) {
   if (o->blocks_per_sm < 0) return fail(VRC_ERR_ARG, "batch blocks_per_sm must be >= 0");
   if (o->chunk != 0 && (o->chunk < 64 || o->chunk > 65536))
     return fail(VRC_ERR_ARG, "batch chunk must be 0 or 64..65536");
+  if (o->rays_per_warp < 0 || o->rays_per_warp > 8192 || (o->rays_per_warp % 32) != 0)
+    return fail(VRC_ERR_ARG, "batch rays_per_warp must be 0 or a multiple of 32 up to 8192");
   if (o->sort_len_buckets < -1 || o->sort_len_buckets > 256)
     return fail(VRC_ERR_ARG, "batch sort_len_buckets must be -1, 0 or 1..256");
   return VRC_OK;
@@ -78,7 +80,7 @@ cudaError_t enqueue_batch(vrc_batch *b, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   return launch_batched_cast(b->form, b->d_probs, b->d_items, b->n_items, b->d_queue, b->shape,
-                             b->grid, b->block, s);
+                             b->grid, b->block, b->opt.rays_per_warp, s);
 }
 
 template <typename T>
@@ -100,6 +102,7 @@ void vrc_default_batch_options(vrc_batch_options *opt) {
   opt->chunk = 0;
   opt->sort_len_buckets = -1;
   opt->use_graph = 1;
+  opt->rays_per_warp = 0;
 }
 
 int vrc_batch_create(vrc_ctx *const *ctxs, const vrc_rays *rays, int32_t n_problems,

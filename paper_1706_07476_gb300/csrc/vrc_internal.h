@@ -131,9 +131,11 @@ struct BatchShape {
 
 size_t batched_smem_bytes(int form, const BatchShape &sh, int block);
 cudaError_t batched_occupancy(int form, const BatchShape &sh, int block, int *blocks_per_sm);
+// rays_per_warp 0: a block's warps take an item's rays interleaved; R > 0:
+// R at a time from the item's counter in shared memory.
 cudaError_t launch_batched_cast(int form, const CastArgs *probs, const BatchItem *items, int n_items,
                                 unsigned int *queue, const BatchShape &sh, int grid, int block,
-                                cudaStream_t s);
+                                int rays_per_warp, cudaStream_t s);
 
 // Next-event estimator (vrc_detect.cu): adds every ray's flux at n_det
 // detector points (float [n_det][3]) to out [n_det][n_groups] (device).

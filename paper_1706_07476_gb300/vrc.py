@@ -477,7 +477,7 @@ class RayStream:
 
 class vrc_batch_options(C.Structure):
     _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("chunk", C.c_int32),
-                ("sort_len_buckets", C.c_int32), ("use_graph", C.c_int32)]
+                ("sort_len_buckets", C.c_int32), ("use_graph", C.c_int32), ("rays_per_warp", C.c_int32)]
 
 
 def vrc_default_batch_options(**kw) -> vrc_batch_options:

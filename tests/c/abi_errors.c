@@ -91,6 +91,8 @@ int main(void) {
   EXPECT(vrc_batch_create(none, &r, 1, &bb, &bt) == VRC_ERR_ARG);
   bb = bo; bb.block = 48;
   EXPECT(vrc_batch_create(none, &r, 1, &bb, &bt) == VRC_ERR_ARG);
+  bb = bo; bb.rays_per_warp = 48;
+  EXPECT(vrc_batch_create(none, &r, 1, &bb, &bt) == VRC_ERR_ARG);
   EXPECT(vrc_batch_launch(NULL, NULL) == VRC_ERR_ARG);
   vrc_batch_destroy(NULL);
   EXPECT(vrc_cast_batched(NULL, &r, 1, NULL) == VRC_ERR_ARG);

@@ -124,7 +124,7 @@ def test_batched_descent_with_planted_minimum(monkeypatch, tmp_path):
     fake = FakeVrc()
     monkeypatch.setattr(autotune, "vrc", fake)
     monkeypatch.setenv("VRC_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
-    plant = {"sort_len_buckets": 8, "chunk": 4096, "block": 128}
+    plant = {"sort_len_buckets": 8, "chunk": 4096, "block": 128, "rays_per_warp": 32}
 
     def timer(fn):
         fn()

@@ -51,12 +51,15 @@ def _run(vrc, torch, probs, form, bopts, launches=1):
 
 
 @pytest.mark.parametrize("form", [0, 1], ids=["plain", "fp32"])
-@pytest.mark.parametrize("sort,graph,chunk", [(16, 1, 0), (0, 1, 512), (4, 0, 128)],
-                         ids=["sorted-graph", "unsorted-graph", "sorted-nograph"])
-def test_batched_problems_vs_oracle(vrc, small_batch, form, sort, graph, chunk):
+@pytest.mark.parametrize("sort,graph,chunk,rpw", [(16, 1, 0, 0), (0, 1, 512, 0), (4, 0, 128, 0),
+                                                   (16, 1, 0, 32), (0, 0, 512, 128)],
+                         ids=["sorted-graph", "unsorted-graph", "sorted-nograph", "sorted-graph-warp32",
+                              "unsorted-nograph-warp128"])
+def test_batched_problems_vs_oracle(vrc, small_batch, form, sort, graph, chunk, rpw):
     import torch
     probs, want = small_batch
-    opts = vrc.vrc_default_batch_options(sort_len_buckets=sort, use_graph=graph, chunk=chunk)
+    opts = vrc.vrc_default_batch_options(sort_len_buckets=sort, use_graph=graph, chunk=chunk,
+                                         rays_per_warp=rpw)
     res = _run(vrc, torch, probs, form, opts)
     for p, (prob, (wt, st), (got, rc, stats)) in enumerate(zip(probs, want, res)):
         assert stats["rays"] == prob.n_rays, p
