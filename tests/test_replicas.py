@@ -1,7 +1,8 @@
-"""The N > 1 path on CPU: two gloo ranks each cast (with the oracle, on the
-host) their shard of a batch and sum their tallies; the result equals the
-one-rank tally of the whole batch.  Also checks the benchmark's cross-rank
-timing reduction (max of the ranks' times, sum of their segments)."""
+"""The N > 1 path: two gloo ranks each cast their shard of a batch and sum
+their tallies; the result equals the one-rank tally of the whole batch.  On
+CPU the ranks cast with the oracle (and the benchmark's cross-rank timing
+reduction is checked: max of the ranks' times, sum of their segments); on
+the GPU two replica processes share the one GPU and cast with libvrc."""
 from __future__ import annotations
 
 import os
@@ -86,3 +87,69 @@ def test_device_tally_view_and_single_rank_reduce(vrc):
         np.testing.assert_array_equal(dev.cpu().numpy(), host)
     finally:
         ctx.close()
+
+
+def _gpu_worker(rank, world, port, out, form):
+    """One replica: casts its shard through libvrc on cuda:0, reads its tally
+    to the host and sums it with the other ranks' over gloo."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from paper_1706_07476_gb300 import vrc
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        prob = _gpu_problem()
+        part = W.take_rays(prob, shard(prob.n_rays, rank, world))
+        ctx = vrc.context_for(prob, vrc.vrc_default_options(form=form))
+        try:
+            dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in part.rays.items()}
+            vrc.vrc_cast_rays(ctx, dev)
+            rc, st = vrc.vrc_sync(ctx)
+            host, _ = vrc.vrc_read_tally(ctx)
+        finally:
+            ctx.close()
+        t = torch.from_numpy(host)
+        allreduce_tally(t)
+        seg = torch.tensor([float(st["segments"]), float(rc != vrc.VRC_OK)], dtype=torch.float64)
+        dist.all_reduce(seg, op=dist.ReduceOp.SUM)
+        if rank == 0:
+            np.save(out, t.numpy())
+            np.save(out + ".meta.npy", seg.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def _gpu_problem():
+    return W.slab_room(seed=5, n=32, n_rays=1 << 16, n_points=500, n_resonances=8, n_groups=2)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form", [0, 1], ids=["plain", "fp32"])
+def test_two_replicas_through_libvrc_sum_to_the_whole_batch(vrc, tmp_path, form):
+    """Two processes on the one GPU, each a replica that casts its shard with
+    the library (their kernels never wait on each other: the only exchange
+    is the host-side gloo sum after both casts), reproduce the single cast
+    of the whole batch to float64 summation order and the oracle to 1e-4."""
+    out = str(tmp_path / "tally.npy")
+    port = _free_port()
+    mp.start_processes(_gpu_worker, args=(2, port, out, form), nprocs=2, join=True, start_method="spawn")
+    got = np.load(out)
+    seg, bad = np.load(out + ".meta.npy")
+    prob = _gpu_problem()
+    ctx = vrc.context_for(prob, vrc.vrc_default_options(form=form))
+    try:
+        vrc.vrc_cast_rays(ctx, {k: torch.from_numpy(v).cuda() for k, v in prob.rays.items()})
+        rc, st = vrc.vrc_sync(ctx)
+        whole, _ = vrc.vrc_read_tally(ctx)
+    finally:
+        ctx.close()
+    assert bad == 0 and rc == vrc.VRC_OK
+    assert seg == st["segments"]
+    np.testing.assert_allclose(got, whole, rtol=1e-12, atol=1e-300)
+    want, sto = oracle.cast(prob)
+    assert st["segments"] == sto["segments"]
+    sel = want >= 1e-30
+    assert np.max(np.abs(got[sel] - want[sel]) / want[sel]) <= 1e-4
