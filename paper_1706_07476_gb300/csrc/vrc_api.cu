@@ -27,9 +27,43 @@ int fail(int code, const char *fmt, ...) {
 }
 
 int cuda_fail(cudaError_t e, const char *what) {
-  if (e == cudaErrorMemoryAllocation)
+  if (e == cudaErrorMemoryAllocation) {
+    // a failed allocation also sits in the runtime's last-error slot, where
+    // the next launch check (cudaGetLastError) would take it for its own
+    (void)cudaGetLastError();
     return fail(VRC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  }
   return fail(VRC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Allocations still to succeed before the armed failure (-1: none armed).
+std::atomic<long long> g_fail_countdown{-1};
+
+namespace {
+bool injected_failure() {
+  long long left = g_fail_countdown.load(std::memory_order_relaxed);
+  while (left >= 0) {
+    if (g_fail_countdown.compare_exchange_weak(left, left - 1, std::memory_order_relaxed))
+      return left == 0;  // this allocation is the armed one (the hook disarms itself)
+  }
+  return false;
+}
+}  // namespace
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t pinned_alloc(void **p, size_t bytes) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaHostAlloc(p, bytes, cudaHostAllocDefault);
 }
 
 int check_options(const vrc_options *o) {
@@ -487,14 +521,14 @@ int vrc_create_mesh(const vrc_mesh_desc *d, const vrc_options *opt, vrc_ctx **ou
   if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(e, "creating the context stream"));
   const size_t tally_bytes = sizeof(double) * (size_t)ncells * d->n_groups;
-  if ((e = cudaMalloc((void **)&c->d_mat, (size_t)ncells)) != cudaSuccess ||
-      (e = cudaMalloc((void **)&c->d_tally, tally_bytes)) != cudaSuccess ||
-      (e = cudaMalloc((void **)&c->d_counters, sizeof(unsigned long long) * kNumCounters)) != cudaSuccess ||
-      (e = cudaMalloc((void **)&c->d_status, sizeof(unsigned))) != cudaSuccess ||
-      (e = cudaMalloc((void **)&c->d_queue, sizeof(unsigned long long))) != cudaSuccess)
+  if ((e = dev_malloc((void **)&c->d_mat, (size_t)ncells)) != cudaSuccess ||
+      (e = dev_malloc((void **)&c->d_tally, tally_bytes)) != cudaSuccess ||
+      (e = dev_malloc((void **)&c->d_counters, sizeof(unsigned long long) * kNumCounters)) != cudaSuccess ||
+      (e = dev_malloc((void **)&c->d_status, sizeof(unsigned))) != cudaSuccess ||
+      (e = dev_malloc((void **)&c->d_queue, sizeof(unsigned long long))) != cudaSuccess)
     return bail(cuda_fail(e, "allocating the mesh and tally"));
   if (d->group_edges &&
-      (e = cudaMalloc((void **)&c->d_edges, sizeof(double) * (d->n_groups + 1))) != cudaSuccess)
+      (e = dev_malloc((void **)&c->d_edges, sizeof(double) * (d->n_groups + 1))) != cudaSuccess)
     return bail(cuda_fail(e, "allocating the group edges"));
   if ((e = cudaMemcpy(c->d_mat, d->material, (size_t)ncells, cudaMemcpyHostToDevice)) != cudaSuccess)
     return bail(cuda_fail(e, "uploading the mesh"));
@@ -746,6 +780,11 @@ int vrc_get_timing(vrc_ctx *c, void *cuda_stream, double *cast_ms, double *sort_
 }
 
 int64_t vrc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int vrc_debug_fail_alloc(int64_t n) {
+  g_fail_countdown.store(n < 0 ? -1 : (long long)n, std::memory_order_relaxed);
+  return VRC_OK;
+}
 
 }  // extern "C"
 

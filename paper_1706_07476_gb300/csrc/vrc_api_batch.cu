@@ -85,7 +85,7 @@ cudaError_t enqueue_batch(vrc_batch *b, cudaStream_t s) {
 
 template <typename T>
 cudaError_t upload(T **dst, const std::vector<T> &src) {
-  cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(src.size(), 1));
+  cudaError_t e = dev_malloc((void **)dst, sizeof(T) * std::max<size_t>(src.size(), 1));
   if (e != cudaSuccess) return e;
   if (src.empty()) return cudaSuccess;
   return cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
@@ -211,11 +211,11 @@ int vrc_batch_create(vrc_ctx *const *ctxs, const vrc_rays *rays, int32_t n_probl
     b->bplan.max_keys = max_keys;
     b->bplan.total_rays = total;
     if ((e = upload(&b->d_bprobs, bp)) != cudaSuccess || (e = upload(&b->d_chunk_problem, chunk_problem)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&b->d_keys, sizeof(uint32_t) * T)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&b->d_table, sizeof(uint32_t) * std::max<int64_t>(table, 1))) != cudaSuccess ||
-        (e = cudaMalloc((void **)&b->d_offsets, sizeof(uint32_t) * std::max<int64_t>(table, 1))) != cudaSuccess ||
-        (e = cudaMalloc((void **)&b->d_tiles, sizeof(uint32_t) * std::max(b->bplan.n_tiles, 1))) != cudaSuccess ||
-        (e = cudaMalloc((void **)&b->d_sorted, 8 * sizeof(float) * T)) != cudaSuccess)
+        (e = dev_malloc((void **)&b->d_keys, sizeof(uint32_t) * T)) != cudaSuccess ||
+        (e = dev_malloc((void **)&b->d_table, sizeof(uint32_t) * std::max<int64_t>(table, 1))) != cudaSuccess ||
+        (e = dev_malloc((void **)&b->d_offsets, sizeof(uint32_t) * std::max<int64_t>(table, 1))) != cudaSuccess ||
+        (e = dev_malloc((void **)&b->d_tiles, sizeof(uint32_t) * std::max(b->bplan.n_tiles, 1))) != cudaSuccess ||
+        (e = dev_malloc((void **)&b->d_sorted, 8 * sizeof(float) * T)) != cudaSuccess)
       return bail(cuda_fail(e, "allocating the batch sort"));
     if ((e = prepare_batched_sort(b->bplan)) != cudaSuccess) return bail(cuda_fail(e, "preparing the batch sort"));
   }
@@ -255,7 +255,7 @@ int vrc_batch_create(vrc_ctx *const *ctxs, const vrc_rays *rays, int32_t n_probl
   if (items.size() >= ((size_t)1 << 31)) return bail(fail(VRC_ERR_ARG, "too many work items"));
   b->n_items = (int)items.size();
   if ((e = upload(&b->d_probs, probs)) != cudaSuccess || (e = upload(&b->d_items, items)) != cudaSuccess ||
-      (e = cudaMalloc((void **)&b->d_queue, sizeof(unsigned int))) != cudaSuccess)
+      (e = dev_malloc((void **)&b->d_queue, sizeof(unsigned int))) != cudaSuccess)
     return bail(cuda_fail(e, "allocating the batch plan"));
 
   b->block = o.block > 0 ? o.block : 256;

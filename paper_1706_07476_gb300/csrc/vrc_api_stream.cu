@@ -58,9 +58,9 @@ int vrc_stream_create(vrc_ctx *c, int64_t capacity, int32_t n_buffers, vrc_strea
   if ((e = cudaStreamCreateWithFlags(&st->copy, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(e, "creating the copy stream");
   for (int i = 0; i < n_buffers; ++i) {
-    if ((e = cudaHostAlloc((void **)&st->host[i], bytes, cudaHostAllocDefault)) != cudaSuccess)
+    if ((e = pinned_alloc((void **)&st->host[i], bytes)) != cudaSuccess)
       return bail(e, "allocating a pinned ray buffer");
-    if ((e = cudaMalloc(&st->dev[i], bytes)) != cudaSuccess) return bail(e, "allocating a device ray buffer");
+    if ((e = dev_malloc(&st->dev[i], bytes)) != cudaSuccess) return bail(e, "allocating a device ray buffer");
     if ((e = cudaEventCreateWithFlags(&st->copied[i], cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&st->cast[i], cudaEventDisableTiming)) != cudaSuccess)
       return bail(e, "creating stream events");

@@ -30,7 +30,7 @@ uint64_t host_mix64(uint64_t x) {
 struct TmpDev {  // device buffers freed at scope exit
   std::vector<void *> ptrs;
   cudaError_t alloc(void **p, size_t bytes) {
-    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    cudaError_t e = dev_malloc(p, std::max<size_t>(bytes, 16));
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   }

@@ -29,6 +29,13 @@ int cuda_fail(cudaError_t e, const char *what);
 // Process-wide count of launched kernels (vrc_launch_count).
 extern std::atomic<long long> g_launches;
 
+// Every device and pinned-host allocation of the library goes through these
+// two, so that vrc_debug_fail_alloc can make a chosen one fail (with
+// cudaErrorMemoryAllocation, before the driver is asked) and tests can walk
+// each failure path without exhausting a GPU.
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t pinned_alloc(void **p, size_t bytes);
+
 #define VRC_CUDA(call, what)                            \
   do {                                                  \
     cudaError_t e_ = (call);                            \
@@ -58,7 +65,7 @@ struct DevBuf {
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
-    cudaError_t e = cudaMalloc(&p, want);
+    cudaError_t e = dev_malloc(&p, want);
     if (e == cudaSuccess) bytes = want;
     return e;
   }

@@ -93,6 +93,7 @@ def _load():
         "vrc_enable_timing": ([P, I32], C.c_int),
         "vrc_get_timing": ([P, P, P, P, P, I32], C.c_int),
         "vrc_launch_count": ([], C.c_int64),
+        "vrc_debug_fail_alloc": ([I64], C.c_int),
         "vrc_sort_rays_static": ([P, P, P, P], C.c_int),
         "vrc_detector_flux": ([P, P, P, I32, P, P], C.c_int),
         "vrc_moments_enable": ([P, I32], C.c_int),
@@ -599,6 +600,11 @@ def vrc_get_timing(ctx: Context, stream=None, reset: bool = False):
 
 def vrc_launch_count() -> int:
     return int(_lib.vrc_launch_count())
+
+
+def vrc_debug_fail_alloc(n: int):
+    """Test hook: the allocation after the next n fails as out of memory (n < 0 disarms)."""
+    _check(_lib.vrc_debug_fail_alloc(int(n)))
 
 
 def vrc_destroy(ctx: Context):

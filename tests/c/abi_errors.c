@@ -120,6 +120,9 @@ int main(void) {
   EXPECT(vrc_moments_fold(NULL, NULL) == VRC_ERR_ARG);
   EXPECT(vrc_cast_histories(NULL, &r, hist, 1, NULL) == VRC_ERR_ARG);
   EXPECT(vrc_context_stream(NULL) == NULL);
+  /* the allocation-failure hook touches no GPU */
+  EXPECT(vrc_debug_fail_alloc(3) == VRC_OK);
+  EXPECT(vrc_debug_fail_alloc(-1) == VRC_OK);
   EXPECT(vrc_version() == VRC_VERSION);
   EXPECT(vrc_device_count() >= 0);
 
