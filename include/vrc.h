@@ -538,10 +538,9 @@ int64_t vrc_launch_count(void);
  * any thread) succeed and the one after fails as if the device were out of
  * memory, without asking the driver; the hook then disarms itself.  n < 0
  * disarms it.  The failing call returns VRC_ERR_OOM: a create call then
- * returns NULL and leaks nothing; a cast of device rays, or of at most 2^22
- * host rays, adds nothing to the tally (a larger host batch is cast in
- * chunks, and the chunks cast before the failing allocation stay added).
- * Touches no GPU; always returns VRC_OK. */
+ * returns NULL and leaks nothing, and a cast adds nothing to the tally (a
+ * cast takes all its buffers before it launches anything, also a large host
+ * batch cast in chunks).  Touches no GPU; always returns VRC_OK. */
 int vrc_debug_fail_alloc(int64_t n);
 
 /* Number of CUDA devices visible (0 when none or on failure). */

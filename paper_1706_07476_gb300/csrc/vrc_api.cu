@@ -220,8 +220,9 @@ int sync_streams(vrc_ctx *c, void *stream) {
 }
 
 
-int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in, uint32_t *carry_out,
-              bool spatial, const uint32_t **n_accepted) {
+// The sort key's layout for this context: (group, crossed-cell bucket),
+// accepted-bin rays first when `accepted`, or (group, spatial block).
+int sort_key_args(const vrc_ctx *c, bool spatial, bool accepted, SortKeyArgs *out) {
   SortKeyArgs P;
   std::memset(&P, 0, sizeof P);
   for (int k = 0; k < 3; ++k) {
@@ -237,7 +238,7 @@ int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in,
   const int max_cells = c->n[0] + c->n[1] + c->n[2] + 1;
   P.len_width = std::max(1, (max_cells + nl - 1) / nl);
   P.n_keys = c->n_groups * nl + 1;
-  if (n_accepted) {  // accepted-bin rays first: twice the keys
+  if (accepted) {  // accepted-bin rays first: twice the keys
     while (nl > 1 && 2 * (int64_t)c->n_groups * nl + 1 > 16384) nl >>= 1;
     if (2 * (int64_t)c->n_groups * nl + 1 > 16384)
       return fail(VRC_ERR_ARG, "too many energy groups for the surrogate's sort");
@@ -257,12 +258,32 @@ int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in,
     P.blocks_axis = nb;
     P.n_keys = c->n_groups * nb * nb * nb + 1;
   }
-  SortPlan plan = make_sort_plan(rp.n, P.n_keys);
+  *out = P;
+  return VRC_OK;
+}
+
+// Sort scratch for a batch of n rays (grow-only buffers).
+int reserve_sort(vrc_ctx *c, const SortPlan &plan) {
   VRC_CUDA(c->sortKeys.ensure(plan.bytes_keys), "allocating sort scratch");
   VRC_CUDA(c->sortTable.ensure(plan.bytes_table), "allocating sort scratch");
   VRC_CUDA(c->sortOffsets.ensure(plan.bytes_table), "allocating sort scratch");
   VRC_CUDA(c->sortTiles.ensure(plan.bytes_tiles), "allocating sort scratch");
   VRC_CUDA(c->sortRays.ensure(plan.bytes_rays), "allocating sort scratch");
+  return VRC_OK;
+}
+
+int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in, uint32_t *carry_out,
+              bool spatial, const uint32_t **n_accepted) {
+  SortKeyArgs P;
+  {
+    int rc = sort_key_args(c, spatial, n_accepted != nullptr, &P);
+    if (rc) return rc;
+  }
+  SortPlan plan = make_sort_plan(rp.n, P.n_keys);
+  {
+    int rc = reserve_sort(c, plan);
+    if (rc) return rc;
+  }
   RayOut out;
   std::memset(&out, 0, sizeof out);
   out.aos = static_cast<float4 *>(c->sortRays.p);  // sorted copy as 32-byte records
@@ -292,12 +313,33 @@ int sort_rays(vrc_ctx *c, RayPtrs &rp, cudaStream_t s, const uint32_t *carry_in,
   return VRC_OK;
 }
 
+// With the learned surrogate the rays are always sorted: those in accepted
+// energy bins first, so the network runs on exactly that leading range.
+bool cast_uses_surrogate(const vrc_ctx *c) { return c->xs_mode == VRC_XS_SURROGATE && c->mlp_ready; }
+bool cast_sorts(const vrc_ctx *c, int64_t n) {
+  return cast_uses_surrogate(c) || c->opt.sort == 1 || (c->opt.sort == -1 && n >= kAutoSortMin);
+}
+
+// Sizes the scratch that cast_device takes for a batch of n rays (sort
+// scratch, the surrogate's cross sections), so that casts of up to n rays
+// that follow allocate nothing.
+int reserve_cast(vrc_ctx *c, int64_t n) {
+  const bool surr = cast_uses_surrogate(c);
+  if (cast_sorts(c, n)) {
+    SortKeyArgs P;
+    int rc = sort_key_args(c, false, surr, &P);
+    if (rc) return rc;
+    rc = reserve_sort(c, make_sort_plan(n, P.n_keys));
+    if (rc) return rc;
+  }
+  if (surr) VRC_CUDA(c->sigBuf.ensure(sizeof(float) * 16 * (size_t)n), "allocating surrogate scratch");
+  return VRC_OK;
+}
+
 // Sort (optional), surrogate (optional) and cast of a device batch on stream s.
 int cast_device(vrc_ctx *c, RayPtrs rp, cudaStream_t s) {
-  // with the learned surrogate the rays are always sorted: those in accepted
-  // energy bins first, so the network runs on exactly that leading range
-  const bool surr = c->xs_mode == VRC_XS_SURROGATE && c->mlp_ready;
-  const bool do_sort = surr || c->opt.sort == 1 || (c->opt.sort == -1 && rp.n >= kAutoSortMin);
+  const bool surr = cast_uses_surrogate(c);
+  const bool do_sort = cast_sorts(c, rp.n);
   const uint32_t *n_acc = nullptr;
   if (do_sort) {
     int rc = sort_rays(c, rp, s, nullptr, nullptr, false, surr ? &n_acc : nullptr);
@@ -405,6 +447,13 @@ int cast_host_pipelined(vrc_ctx *c, const vrc_rays *r, cudaStream_t s) {
   }
   const size_t slot_bytes = 8 * sizeof(float) * (size_t)kUploadChunk;
   for (int i = 0; i < 2; ++i) VRC_CUDA(c->up_slot[i].ensure(slot_bytes), "allocating upload slots");
+  // every buffer the chunks' casts need, before the first of them is
+  // launched: an allocation failure then leaves the tally untouched
+  {
+    const int64_t largest = std::min(kUploadChunk, std::max(kFirstChunk, r->n - kFirstChunk));
+    int rc = reserve_cast(c, largest);
+    if (rc) return rc;
+  }
   const float *src[8] = {r->x, r->y, r->z, r->u, r->v, r->w, r->E, r->wt};
   int last = 0;
   for (int64_t off = 0, i = 0, m = 0; off < r->n; off += m, ++i) {

@@ -74,14 +74,17 @@ def test_create_mesh_fails_cleanly_at_every_allocation(vrc):
     assert free0 - _free(torch) <= LEAK_TOL
 
 
-@pytest.mark.parametrize("on_device", [True, False])
-def test_failed_cast_adds_nothing(vrc, on_device):
+@pytest.mark.parametrize("where", ["device", "host", "host_chunked"])
+def test_failed_cast_adds_nothing(vrc, where):
     """A cast whose allocation fails (cross-section tables, sort scratch, ray
-    staging) adds nothing; the next identical cast gives the oracle's tally."""
+    staging, upload slots) adds nothing; the next identical cast gives the
+    oracle's tally.  host_chunked is a host batch above 2^22 rays, uploaded
+    and cast in chunks: every buffer of every chunk is sized before the
+    first chunk is cast."""
     import torch
-    prob = _problem()
+    prob = _problem(n_rays=(1 << 22) + 4096 if where == "host_chunked" else 20000)
     want, st = oracle.cast(prob)
-    rays = ({k: torch.from_numpy(v).cuda() for k, v in prob.rays.items()} if on_device
+    rays = ({k: torch.from_numpy(v).cuda() for k, v in prob.rays.items()} if where == "device"
             else prob.rays)
     ctx = vrc.context_for(prob, vrc.vrc_default_options(form=vrc.VRC_FORM_FP32, sort=1))
     try:
