@@ -185,3 +185,31 @@ def test_genuine_out_of_memory_then_small_cast(vrc):
         got, _ = vrc.vrc_read_tally(ctx)
     assert rc == vrc.VRC_OK and stats["segments"] == st["segments"]
     assert H.rel_err_report(want, got)["max_rel"] <= 1e-4
+
+
+def test_history_moments_and_detectors_fail_cleanly(vrc):
+    """Per-history moments and point detectors with every allocation of a
+    first call failing in turn: a failed call folds nothing into the moments
+    and counts none of its histories; the call that succeeds gives the
+    oracle's per-history totals and detector flux."""
+    prob = W.slab_room(seed=9, n=16, n_rays=6000, n_points=400, n_resonances=6, n_groups=3)
+    rng = np.random.default_rng(10)
+    N = 2000
+    hist = rng.integers(0, N, size=prob.n_rays).astype(np.uint32)
+    want_total, _, _ = oracle.history_moments(prob, hist, N)
+    det = np.array([[8.3, 7.7, 9.1], [2.0, 3.0, 4.0]])
+    want_flux = oracle.point_detector(prob, det)
+    ctx = vrc.context_for(prob, vrc.vrc_default_options(form=vrc.VRC_FORM_FP32, sort=1))
+    try:
+        vrc.vrc_moments_enable(ctx, vrc.VRC_MOMENTS_HISTORY)
+        fails, _ = _walk(vrc, lambda: vrc.vrc_cast_histories(ctx, prob.rays, hist, N))
+        assert fails >= 1, fails
+        total, _, samples = vrc.vrc_moments_read(ctx)
+        assert samples == N
+        assert H.rel_err_report(want_total, total)["max_rel"] <= 1e-4
+        fails, got = _walk(vrc, lambda: vrc.vrc_detector_flux(ctx, prob.rays, det))
+        assert fails >= 1, fails
+        sel = want_flux > 0
+        assert (np.abs(got[sel] - want_flux[sel]) / want_flux[sel]).max() <= 1e-4
+    finally:
+        ctx.close()
