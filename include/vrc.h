@@ -194,7 +194,9 @@ int vrc_load_xs(vrc_ctx *c, int32_t material, const double *E_eV, const double *
  * nothing and are reported by the next vrc_sync / vrc_read_tally as
  * VRC_ERR_NONFINITE.  n == 0 is a no-op.
  * Errors: VRC_ERR_ARG, VRC_ERR_STATE (a material used by the mesh has no
- * table), VRC_ERR_OOM, VRC_ERR_CUDA. */
+ * table), VRC_ERR_OOM (a scratch buffer could not be allocated; the call
+ * takes every buffer before it launches a kernel, so it has added nothing),
+ * VRC_ERR_CUDA. */
 int vrc_cast_rays(vrc_ctx *c, const vrc_rays *r, void *cuda_stream);
 
 /* Sorts a device batch of rays the way vrc_cast_rays does before its cast
