@@ -767,7 +767,7 @@ def measure_surrogate(args, torch, vrc, local, stream, steps, warmup, oracle=Non
                      "median_rel_err": rep["median_rel_err"], "smooth_fraction": rep["smooth_fraction"],
                      "final_loss": rep["final_loss"]},
         "mlp_forward": {"ms": 1e3 * dt_mlp, "rays_per_s": prob.n_rays / dt_mlp,
-                        "kernel": "k_mlp_apply_tc (tcgen05.mma kind::f16, M = 128, N = 128 and 16)"},
+                        "kernel": "k_mlp_apply_tc (tcgen05.mma kind::f16, M = 128, N = 128, 48 and 32)"},
         "roofline": {"bound": "tensor", "achieved": tensor_flop / dt_mlp / 1e12, "peak": peak,
                      "unit": "TFLOP/s", "frac": tensor_flop / dt_mlp / 1e12 / peak, "traffic": None,
                      "peak_source": f"{src} bf16_tflops (cuBLAS bf16 GEMM, burst)",

@@ -26,12 +26,13 @@
 //      columns;
 //   5. each thread loads its row, h2 = SiLU(D + b2), and writes its hi and lo
 //      parts to A2hi, A2lo (A1's bytes: the layer-2 MMAs have completed);
-//   6. D3 = A2 W3^T (M = 128, N = 16, K = 128) with W3 held as three
-//      bfloat16 parts (hi, mid, lo: about 24 significant bits): the five
-//      products A2hi W3hi, A2hi W3mid, A2hi W3lo, A2lo W3hi, A2lo W3mid into
-//      the group's first 16 columns;
-//   7. each thread loads its 16 outputs, adds b3 and the 1/v prior and writes
-//      log sigma or sigma.
+//   6. D3 = A2 W3^T (M = 128, K = 128) with W3 held as three bfloat16 parts
+//      (hi, mid, lo: about 24 significant bits) stacked as one [48][128]
+//      matrix: A2hi [W3hi; W3mid; W3lo] (N = 48) and A2lo [W3hi; W3mid]
+//      (N = 32) into two column ranges of the group;
+//   7. each thread loads its outputs' five products (hi hi, hi mid, hi lo,
+//      lo hi, lo mid), sums them, adds b3 and the 1/v prior and writes log
+//      sigma or sigma.
 // Operands live in shared memory in the canonical K-major layout without
 // swizzle: 8-row x 16-byte core matrices, consecutive along K 128 bytes
 // apart (leading byte offset) and along rows K*16 bytes apart (stride byte
@@ -108,7 +109,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 // and B (bits 7-9 and 10-12 = 1), both K-major, N / 8 at bits 17-22, M / 16
 // at bits 24-28.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-constexpr uint32_t kIdesc16 = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdesc48 = (1u << 4) | (1u << 7) | (1u << 10) | ((48u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdesc32 = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// Output-layer accumulators within the group's columns: A2hi [W3hi; W3mid;
+// W3lo] (N = 48) at 0, A2lo [W3hi; W3mid] (N = 32) at kD3Lo.
+constexpr uint32_t kD3Lo = 64;
 
 __device__ __forceinline__ void mma_bf16_tc(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate,
                                             uint32_t idesc = kIdesc) {
@@ -155,23 +160,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t (&r)[32], uint32_t taddr) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// N = 4 or 8 consecutive float32 columns of this thread's lane.
+// N = 4 or 8 consecutive float32 columns of this thread's lane, without
+// waiting: several loads are issued before one tmem_wait_ld.
 template <int N>
-__device__ __forceinline__ void tmem_ld_cols(uint32_t (&r)[N], uint32_t taddr);
+__device__ __forceinline__ void tmem_ld_cols_async(uint32_t (&r)[N], uint32_t taddr);
 template <>
-__device__ __forceinline__ void tmem_ld_cols<8>(uint32_t (&r)[8], uint32_t taddr) {
+__device__ __forceinline__ void tmem_ld_cols_async<8>(uint32_t (&r)[8], uint32_t taddr) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 template <>
-__device__ __forceinline__ void tmem_ld_cols<4>(uint32_t (&r)[4], uint32_t taddr) {
+__device__ __forceinline__ void tmem_ld_cols_async<4>(uint32_t (&r)[4], uint32_t taddr) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Stages W3 [16][128] (float32) as three bfloat16 parts w = hi + mid + lo
 // (hi = bf16(w), mid = bf16(w - hi), lo = bf16(w - hi - mid)), each in core
@@ -398,18 +403,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_apply_tc(ApplyArgs a) {
     fence_before();
     group_sync(g);
 
-    // 6. D3 = A2 W3^T (N = 16): A2hi (W3hi + W3mid + W3lo) + A2lo (W3hi + W3mid)
+    // 6. D3 = A2 W3^T with W3 as three bfloat16 parts, whose [16][128]
+    // blocks lie back to back as one [48][128] matrix: A2hi [W3hi; W3mid;
+    // W3lo] (N = 48) and A2lo [W3hi; W3mid] (N = 32), 16 MMAs in place of
+    // 40 with N = 16; the five 16-column products are summed in step 7
     if (gt == 0) {
       fence_after();
-#pragma unroll 1
-      for (int part = 0; part < 5; ++part) {
-        const uint32_t sa = sA1 + (part < 3 ? 0u : kA1Lo);
-        const uint32_t sb = sW3 + (uint32_t)(part < 3 ? part : part - 3) * kW3Part;
 #pragma unroll
-        for (int kk = 0; kk < kHid / 16; ++kk)
-          mma_bf16_tc(tmem, smem_desc(sa + kk * 256, 128, kHid * 16), smem_desc(sb + kk * 256, 128, kHid * 16),
-                      part > 0 || kk > 0, kIdesc16);
-      }
+      for (int kk = 0; kk < kHid / 16; ++kk)
+        mma_bf16_tc(tmem, smem_desc(sA1 + kk * 256, 128, kHid * 16), smem_desc(sW3 + kk * 256, 128, kHid * 16),
+                    kk > 0, kIdesc48);
+#pragma unroll
+      for (int kk = 0; kk < kHid / 16; ++kk)
+        mma_bf16_tc(tmem + kD3Lo, smem_desc(sA1 + kA1Lo + kk * 256, 128, kHid * 16),
+                    smem_desc(sW3 + kk * 256, 128, kHid * 16), kk > 0, kIdesc32);
       mma_commit(bar);
     }
     if (group_sync_or(g, !wait_phase(bar, phase))) {
@@ -419,14 +426,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_apply_tc(ApplyArgs a) {
     phase ^= 1u;
     fence_after();
 
-    // 7. this thread's kPer of the 16 outputs (part h: outputs kPer h ..) plus b3
+    // 7. this thread's kPer of the 16 outputs (part h: outputs kPer h ..):
+    // the five products (hi hi, hi mid, hi lo, lo hi, lo mid) plus b3
     constexpr int kPer = kOut / kRowParts;
     float p[kPer];
     {
-      uint32_t r[kPer];
-      tmem_ld_cols<kPer>(r, tmem_row + (uint32_t)(part * kPer));
+      uint32_t hh[kPer], hm[kPer], hl[kPer], lh[kPer], lm[kPer];
+      const uint32_t c0 = tmem_row + (uint32_t)(part * kPer);
+      tmem_ld_cols_async<kPer>(hh, c0);
+      tmem_ld_cols_async<kPer>(hm, c0 + 16);
+      tmem_ld_cols_async<kPer>(hl, c0 + 32);
+      tmem_ld_cols_async<kPer>(lh, c0 + kD3Lo);
+      tmem_ld_cols_async<kPer>(lm, c0 + kD3Lo + 16);
+      tmem_wait_ld();
 #pragma unroll
-      for (int j = 0; j < kPer; ++j) p[j] = __uint_as_float(r[j]) + bs[2 * kHid + part * kPer + j];
+      for (int j = 0; j < kPer; ++j) {
+        const float small = (__uint_as_float(hl[j]) + __uint_as_float(lm[j])) +
+                            (__uint_as_float(hm[j]) + __uint_as_float(lh[j]));
+        p[j] = (__uint_as_float(hh[j]) + small) + bs[2 * kHid + part * kPer + j];
+      }
     }
     fence_before();
 
