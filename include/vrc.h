@@ -548,11 +548,12 @@ int vrc_debug_fail_alloc(int64_t n);
 /* Number of CUDA devices visible (0 when none or on failure). */
 int vrc_device_count(void);
 
-/* Library version as major*10000 + minor*100 + patch (0.3.0: vrc_options
+/* Library version as major*10000 + minor*100 + patch (0.4.0: the
+ * allocation-failure hook vrc_debug_fail_alloc; 0.3.0: vrc_options
  * gained rays_per_warp and vrc_stats gained live; 0.2.0: vrc_options gained
  * stop_at_zero; rectilinear meshes, per-history moments, the next-event
  * estimator and streaming buffers were added). */
-#define VRC_VERSION 300
+#define VRC_VERSION 400
 int vrc_version(void);
 
 #ifdef __cplusplus
